@@ -1,0 +1,255 @@
+"""Pins of the oracle's filters against closed forms, invariants and two
+independent constructions of the scaling function (cascade, Fourier product).
+All CPU."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.filters as F
+import scaling_function as S
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+JS = np.arange(F.J_LO, F.J_HI + 1)
+LS = np.arange(-F.KIN_HALF, F.KIN_HALF + 1)
+
+
+# --------------------------------------------------------------------- h, g
+def test_h_sum_and_orthonormality():
+    """Eq. (refinement) with orthonormal phi: sum h = sqrt2,
+    sum_j h_j h_{j+2k} = delta_k."""
+    h = F.h()
+    assert abs(h.sum() - math.sqrt(2.0)) < 4e-16
+    for k in range(F.M_VANISH):
+        v = np.dot(h[: F.NTAP - 2 * k], h[2 * k:])
+        assert abs(v - (1.0 if k == 0 else 0.0)) < 1e-15, (k, v)
+
+
+def test_g_definition_and_vanishing_moments():
+    """g_j = (-1)^j h_{1-j} (printed after Eq. refinement); a Daubechies
+    wavelet of order 2M has M vanishing moments: sum_j j^p g_j = 0, p < 8."""
+    h, g = F.h(), F.g()
+    for t, j in enumerate(JS):
+        assert g[t] == (-1) ** (j % 2) * h[(1 - j) - F.J_LO]
+    for p in range(F.M_VANISH):
+        terms = JS.astype(np.float64) ** p * g
+        assert abs(terms.sum()) < 1e-13 * max(1.0, np.abs(terms).sum()), p
+    # the 9th moment does not vanish (the order is exactly 8)
+    terms = JS.astype(np.float64) ** 8 * g
+    assert abs(terms.sum()) > 1e-3 * np.abs(terms).sum()
+    # h and g are orthogonal at every even shift
+    for k in range(-7, 8):
+        v = sum(h[i] * g[i + 2 * k] for i in range(16) if 0 <= i + 2 * k < 16)
+        assert abs(v) < 1e-15
+
+
+def test_h_spectral_factor_closed_form():
+    """|m0(xi)|^2 = cos^16(xi/2) P(sin^2(xi/2)), P(y) = sum_k C(7+k,k) y^k."""
+    h = F.h()
+    xi = np.linspace(0.0, np.pi, 257)
+    m0 = (h[None, :] * np.exp(-1j * JS[None, :] * xi[:, None])).sum(1) / math.sqrt(2)
+    y = np.sin(xi / 2) ** 2
+    P = sum(math.comb(7 + k, k) * y ** k for k in range(8))
+    ref = np.cos(xi / 2) ** 16 * P
+    assert np.max(np.abs(np.abs(m0) ** 2 - ref)) < 1e-14
+
+
+def test_h_least_asymmetric_choice():
+    """The chosen factor has the smallest phase nonlinearity of the 16
+    spectral factors (ties only between mirror images), and its energy
+    centre is >= 1/2 (the mirror tie-break)."""
+    cands, choice = F.candidates()
+    assert len(cands) == 16
+    crit = dict(cands)
+    best = min(crit.values())
+    assert crit[choice] <= best + 1e-9
+    mirror = tuple(1 - b for b in choice)
+    assert abs(crit[mirror] - crit[choice]) < 1e-9
+    others = [v for c, v in cands if c not in (choice, mirror)]
+    assert min(others) > best + 1e-3
+    h = F.h()
+    assert (JS * h * h).sum() >= 0.5
+
+
+def test_h_matches_high_precision_rounding():
+    hp = F.high_precision()
+    for name, arr in (("hD", F.h()), ("gD", F.g()), ("aD", F.kinetic_a())):
+        assert all(float(v) == a for v, a in zip(hp[name], arr)), name
+
+
+def test_cascade_refinement_identity():
+    """phi built by the cascade satisfies Eq. (refinement) at every dyadic
+    point, has unit integral, and integer translates sum to one."""
+    h = F.h()
+    x, p = S.phi_dyadic(h, 8)
+    dx = 1.0 / 2 ** 8
+    assert abs(p.sum() * dx - 1.0) < 1e-14
+    xi, pi = S.phi_integers(h)
+    # partition of unity at integers and half-integers
+    assert abs(pi.sum() - 1.0) < 1e-14
+    half = p[2 ** 7::2 ** 8]
+    assert abs(half.sum() - 1.0) < 1e-13
+
+
+# --------------------------------------------------------------- moments
+def test_moments_against_cascade_quadrature():
+    """Moment recursion vs trapezoid quadrature on the cascade grid."""
+    h = F.h()
+    x, p = S.phi_dyadic(h, 12)
+    dx = 1.0 / 2 ** 12
+    M = F.moments()
+    for q in range(8):
+        ref = np.sum(x ** q * p) * dx
+        assert abs(M[q] - ref) < 1e-12 * max(1.0, abs(ref)), q
+
+
+# ---------------------------------------------------------------- magic
+def test_magic_sum_and_window():
+    w, k0 = F.magic()
+    assert abs(w.sum() - 1.0) < 1e-15
+    M1 = F.moments()[1]
+    assert k0 == int(round(M1 - 7.5))
+    assert w.size == 16
+
+
+def test_magic_reproduces_polynomials_exactly():
+    """Point values of x^q, q <= 15, from their exact projections
+    s_j = int x^q phi(x - j) dx (moments, binomial expansion in 80 digits)."""
+    from decimal import Decimal, localcontext
+    hp = F.high_precision()
+    wD, k0, M = hp["wD"], hp["k0"], hp["momD"]
+    with localcontext() as ctx:
+        ctx.prec = 60
+        for q in range(16):
+            for I in (-3, 0, 2, 5):
+                acc = Decimal(0)
+                for t, wk in enumerate(wD):
+                    j = I - (k0 + t)
+                    sj = sum(math.comb(q, r) * Decimal(j ** (q - r)) * M[r]
+                             for r in range(q + 1))
+                    acc += wk * sj
+                ref = Decimal(I ** q)
+                assert abs(acc - ref) <= Decimal(10) ** -40 * max(1, abs(ref)), (q, I)
+
+
+def test_magic_polynomials_via_cascade():
+    """Same property, projections computed by quadrature of the cascade phi
+    (independent of the moment recursion), FP64 taps."""
+    h = F.h()
+    w, k0 = F.magic()
+    for q in (0, 1, 2, 5, 9):
+        f = lambda x: (x / 8.0) ** q
+        for I in (0, 3):
+            js = I - (k0 + np.arange(16))
+            s = S.project(h, f, js, level=12)
+            assert abs(np.dot(w, s) - (I / 8.0) ** q) < 1e-11, (q, I)
+
+
+def test_magic_plane_wave_order16():
+    """For f = e^{i kappa x}: s_j = e^{i kappa j} phi^(-kappa), so the magic
+    filter returns f(I) times phi^(-kappa) w^(kappa); the defect falls as
+    kappa^16 (the O(h^16) of Sec. "Application of the local potential")."""
+    h = F.h()
+    w, k0 = F.magic()
+    ks = k0 + np.arange(16)
+    errs = []
+    Ns = (6, 8, 12)
+    for N in Ns:
+        kap = 2 * np.pi / N
+        wh = (w * np.exp(-1j * kap * ks)).sum()
+        errs.append(abs(S.phi_hat(h, -kap) * wh - 1.0))
+    for (N1, e1), (N2, e2) in zip(zip(Ns, errs), zip(Ns[1:], errs[1:])):
+        slope = math.log(e1 / e2) / math.log(N2 / N1)
+        assert 14.0 < slope < 17.5, (N1, N2, slope)
+
+
+def test_magic_window_direction_matters():
+    """A reversed magic filter is much worse: the pin above fails for it."""
+    h = F.h()
+    w, k0 = F.magic()
+    ks = k0 + np.arange(16)
+    kap = 2 * np.pi / 8
+    good = abs(S.phi_hat(h, -kap) * (w * np.exp(-1j * kap * ks)).sum() - 1)
+    bad = abs(S.phi_hat(h, -kap) * (w[::-1] * np.exp(-1j * kap * ks)).sum() - 1)
+    assert bad > 1e3 * good
+
+
+# --------------------------------------------------------------- kinetic
+def test_kinetic_invariants():
+    a = F.kinetic_a()
+    assert np.max(np.abs(a - a[::-1])) < 1e-15 * np.abs(a).max()
+    assert abs(a.sum()) < 1e-14
+    assert abs((LS ** 2 * a).sum() - 2.0) < 1e-14
+    assert a[F.KIN_HALF] < 0          # a_0 = -int phi'^2
+    kap = np.linspace(0, np.pi, 513)
+    sym = (a[None, :] * np.cos(kap[:, None] * LS[None, :])).sum(1)
+    assert np.all(sym <= 1e-14)
+
+
+def test_kinetic_full_refinement_residual():
+    """The solution satisfies every row of a = 4 R a (none dropped)."""
+    from decimal import localcontext
+    hp = F.high_precision()
+    with localcontext() as ctx:
+        ctx.prec = F.PREC
+        rows = F.kinetic_system(hp["hD"])
+        for row in rows:
+            r = sum(c * x for c, x in zip(row, hp["aD"]))
+            assert abs(r) < 1e-50
+
+
+def test_kinetic_plane_wave_order16():
+    """a^(kappa) = -kappa^2 + O(kappa^16): the Galerkin second derivative is
+    exact on polynomials of degree < 16."""
+    a = F.kinetic_a()
+    Ns = (6, 8, 12)
+    errs = []
+    for N in Ns:
+        kap = 2 * np.pi / N
+        errs.append(abs((a * np.cos(kap * LS)).sum() + kap * kap))
+    for (N1, e1), (N2, e2) in zip(zip(Ns, errs), zip(Ns[1:], errs[1:])):
+        slope = math.log(e1 / e2) / math.log(N2 / N1)
+        assert 14.0 < slope < 17.5, (N1, N2, slope)
+
+
+@pytest.mark.parametrize("kap", [0.5, 1.0, 2.0, 3.0])
+def test_kinetic_fourier_form(kap):
+    """a^(kappa) = -sum_n (kappa + 2 pi n)^2 |phi^(kappa + 2 pi n)|^2 with
+    phi^ the infinite product of the refinement symbol."""
+    a = F.kinetic_a()
+    xi = kap + 2 * np.pi * np.arange(-400, 401)
+    ref = -(xi ** 2 * np.abs(S.phi_hat(F.h(), xi)) ** 2).sum()
+    assert abs((a * np.cos(kap * LS)).sum() - ref) < 1e-10 * max(1, abs(ref))
+
+
+def test_kinetic_against_cascade_derivative():
+    """a_1 = int phi(x) phi''(x-1) dx = -int phi'(x) phi'(x-1) dx with phi'
+    from finite differences of the cascade phi (coarse, independent)."""
+    h = F.h()
+    L = 12
+    x, p = S.phi_dyadic(h, L)
+    dx = 1.0 / 2 ** L
+    dp = np.gradient(p, dx)
+    a = F.kinetic_a()
+    for l in (0, 1, 2, 3):
+        sh = l * 2 ** L
+        v = -np.sum(dp[sh:] * dp[: dp.size - sh]) * dx
+        assert abs(v - a[F.KIN_HALF + l]) < 2e-3 * abs(a).max(), l
+
+
+def test_golden_table_reproduced():
+    """tests/golden/filters.txt (written by make_golden.py from the oracle)
+    is reproduced bit for bit on this machine."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "filters.txt")
+    tab = {}
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        k, *vals = line.split()
+        tab[k] = vals
+    w, k0 = F.magic()
+    assert int(tab["k0"][0]) == k0
+    for name, arr in (("h", F.h()), ("g", F.g()), ("w", w), ("a", F.kinetic_a())):
+        assert [float.fromhex(v) for v in tab[name]] == list(arr), name
