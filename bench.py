@@ -1,0 +1,354 @@
+"""Benchmark of the batched FP64 local Hamiltonian (one JSON line on rank 0).
+
+Workload (the configuration the orbital-applications/s metric is quoted on):
+192 orbitals in one autotuned, graph-captured plan -- 64 orbitals on each of
+three periodic cells with coarse grids 56^3, 48^3 and 40^3 (fine 112^3, 96^3,
+80^3), 8 wavelet components per coarse point, FP64, each cell with its own
+Gaussian-sum potential, occupations 2.0.  One step = the whole hot path
+(uncompress, synthesis, magic filter, V psi + density + Epot, transposed
+magic filter, kinetic + Ekin, analysis, compress, reductions) over all 192
+orbitals.  The orbitals (1.43 GB per array) exceed the 129 MB L2, so no
+flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (test infrastructure, plain
+numpy) on a bounded sample of the same workload (one orbital of each cell per
+step) on the host cores.
+
+Multi-GPU (torchrun): every rank runs its own 192 orbitals (weak scaling, no
+data-path collective); value = all ranks' orbitals / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIZES = [(56, 56, 56), (48, 48, 48), (40, 40, 40)]
+PER_CELL = 64
+CFG = 2
+METRIC = "H_loc|psi> orbital-applications/s (FP64, batched uneven cells)"
+UNIT = "orbital-applications/s"
+WORKLOAD = {
+    "workload": "batched FP64 local Hamiltonian + density, 192 orbitals: 64 each on "
+                "periodic coarse 56^3, 48^3, 40^3 cells (fine 112^3, 96^3, 80^3), "
+                "8 components, Gaussian-sum V per cell, occ 2.0; autotuned, graph-captured",
+    "orbitals": 3 * PER_CELL,
+    "fine_points_per_step": sum(PER_CELL * 8 * a * b * c for a, b, c in SIZES),
+    "l2": "inputs larger than L2 (1.43 GB per orbital array), no flush",
+}
+# FP64-pipe operations per fine point of the chain (FMA = 1 op)
+KIN_OPS_PER_POINT_PER_PASS = 29
+FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of GB300 (2 flops per DFMA)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs(rank):
+    from paper_0904_1543_gb300 import inputs
+    cell_of_orb = [c for c in range(3) for _ in range(PER_CELL)]
+    first = rank * len(cell_of_orb)
+    psi = np.concatenate([inputs.orbital(CFG, first + o, SIZES[c])
+                          for o, c in enumerate(cell_of_orb)])
+    Vs = [inputs.gaussian_potential(CFG, c, SIZES[c]) for c in range(3)]
+    occ = np.full(len(cell_of_orb), 2.0)
+    return cell_of_orb, psi, Vs, occ
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------- CPU oracle
+def oracle_sample(cell_of_orb, psi, Vs, occ, offsets, norb_per_cell=1):
+    """Times the oracle on norb_per_cell orbitals of each cell; returns
+    (orbitals, seconds)."""
+    import oracle.wavelet as O
+    t0 = time.perf_counter()
+    done = 0
+    for c in range(3):
+        idx = [o for o, cc in enumerate(cell_of_orb) if cc == c][:norb_per_cell]
+        for o in idx:
+            O.hpsi_local(psi[offsets[o]:offsets[o + 1]], Vs[c], occ[o], SIZES[c])
+            done += 1
+    return done, time.perf_counter() - t0
+
+
+def offsets_of(cell_of_orb):
+    off = [0]
+    for c in cell_of_orb:
+        off.append(off[-1] + 8 * int(np.prod(SIZES[c])))
+    return off
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cell_of_orb, psi, Vs, occ = make_inputs(0)
+    off = offsets_of(cell_of_orb)
+    for _ in range(args.warmup):
+        oracle_sample(cell_of_orb, psi, Vs, occ, off)
+    done, secs = 0, 0.0
+    for _ in range(args.steps):
+        d, s = oracle_sample(cell_of_orb, psi, Vs, occ, off)
+        done += d
+        secs += s
+    value = done / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, sample="one orbital of each cell per step (3 orbitals)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one orbital of each of the 56^3/48^3/40^3 cells per step, "
+                                   "FP64 numpy oracle, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_0904_1543_gb300 as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    # a non-default stream: plan graphs are captured and replayed on it
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        _run_ours(args, W, torch, dist, rank, world, local, dev)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _run_ours(args, W, torch, dist, rank, world, local, dev):
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cell_of_orb, psi_h, Vs_h, occ_h = make_inputs(rank)
+    cells = [W.Grid(s) for s in SIZES]
+    plan = W.Plan(cells, cell_of_orb, prec=W.WVL_F64, graph=True, autotune=True)
+    psi = torch.from_numpy(psi_h).to(dev)
+    V = [torch.from_numpy(v).to(dev) for v in Vs_h]
+    occ = torch.from_numpy(occ_h).to(dev)
+    hp = torch.empty_like(psi)
+    ek = torch.empty(len(cell_of_orb), dtype=torch.float64, device=dev)
+    ep = torch.empty_like(ek)
+    rho = [torch.zeros(c.fine, dtype=torch.float64, device=dev) for c in cells]
+    plan.autotune(psi, V, occ, hpsi=hp, rho=rho)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.hpsi(psi, V, occ, hpsi=hp, rho=rho, ekin=ek, epot=ep)
+
+    # ---- device-resident timed region (graph replay)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    gpu_id = local
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else local
+    except Exception:
+        pass
+    clocks = Clocks(gpu_id)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = W.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = W.kernel_launches() - l0
+
+    # ---- per-stage times of the same steps, traced on the launching stream
+    plan.set_profiling(True)
+    plan.profile()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = plan.profile()
+    plan.set_profiling(False)
+    clk = clocks.stop()
+
+    # ---- end to end through the public API from pinned host memory
+    psi_pin = torch.from_numpy(psi_h).pin_memory()
+    V_pin = [torch.from_numpy(v).pin_memory() for v in Vs_h]
+    occ_pin = torch.from_numpy(occ_h).pin_memory()
+    hp_pin = torch.empty(psi_h.shape, dtype=torch.float64).pin_memory()
+    ek_pin = torch.empty(len(cell_of_orb), dtype=torch.float64).pin_memory()
+    ep_pin = torch.empty_like(ek_pin)
+    rho_pin = [torch.empty(c.fine, dtype=torch.float64).pin_memory() for c in cells]
+    h2d = psi_pin.numel() * 8 + sum(v.numel() * 8 for v in V_pin) + occ_pin.numel() * 8
+    d2h = hp_pin.numel() * 8 + 2 * ek_pin.numel() * 8 + sum(r.numel() * 8 for r in rho_pin)
+
+    def e2e_step():
+        psi.copy_(psi_pin, non_blocking=True)
+        for v, vp in zip(V, V_pin):
+            v.copy_(vp, non_blocking=True)
+        occ.copy_(occ_pin, non_blocking=True)
+        for r in rho:
+            r.zero_()
+        step()
+        hp_pin.copy_(hp, non_blocking=True)
+        ek_pin.copy_(ek, non_blocking=True)
+        ep_pin.copy_(ep, non_blocking=True)
+        for r, rp in zip(rho, rho_pin):
+            rp.copy_(r, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0))
+
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+
+    norb_total = len(cell_of_orb) * world
+    value = norb_total * args.steps / (ms * 1e-3)
+    value_e2e = norb_total * args.steps / (ms_e2e * 1e-3)
+
+    # roofline of the dominant kernel (kinetic pass, 3 launches per step)
+    kin_ms, kin_launches = prof["kinetic"]
+    pts = WORKLOAD["fine_points_per_step"]
+    flops_per_launch = 2.0 * KIN_OPS_PER_POINT_PER_PASS * pts
+    kin_avg_s = kin_ms * 1e-3 / max(kin_launches * 3, 1)
+    achieved = flops_per_launch / kin_avg_s / 1e12 if kin_launches else None
+    traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "traffic": traffic, "kernel": "kinetic 1D pass (FP64 DFMA pipe)",
+                "peak_source": "nominal GB300 FP64 rate from the recipe table (not measured)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": WORKLOAD,
+        "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk,
+        "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        off = offsets_of(cell_of_orb)
+        done, secs = 0, 0.0
+        while secs < 10.0:
+            d, s = oracle_sample(cell_of_orb, psi_h, Vs_h, occ_h, off)
+            done += d
+            secs += s
+        line["cpu_baseline"] = {
+            "value": done / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} orbitals (one of each cell per round), FP64 numpy oracle, "
+                      f"single thread, {secs:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

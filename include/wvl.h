@@ -1,0 +1,211 @@
+/*
+ * wvl.h -- C ABI of the GB300 local-Hamiltonian library for Daubechies-16
+ * wavelets in periodic boundary conditions (Genovese et al., "Density
+ * Functional Theory calculation on many-cores hybrid CPU-GPU architectures").
+ *
+ * Method (paper, Sec. "Full local hamiltonian"): for each orbital
+ *   1) decompression, 2) wavelet synthesis to the fine scaling basis
+ *   (Eq. wavefhigh), 3a) magic filter (Eq. magicfilter), 3b) V*psi,
+ *   3c) transposed magic filter, 4) kinetic convolution (Eqs. kiner, fprod)
+ *   on the output of 2), 5) sum, 6) analysis, 7) compression;
+ * plus the density rho += occ |psi_r|^2 (Eq. density, Sec. "Local density
+ * calculation") and the energies Ekin = <s, -1/2 Lap s>, Epot = sum V psi_r^2.
+ * Every 3D convolution is three 1D periodic "convolve + transpose" passes
+ * (Eqs. 3dconv, 1dconvtrans, kinetic1d).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: coarse n1 x n2 x n3 points (n_d >= 1), fine N_d = 2 n_d, fine spacing
+ *   h'_d (kinetic scale -1/(2 h'_d^2)); P = N1 N2 N3 fine points per orbital.
+ * Arrays are C-ordered with x fastest: fine arrays are [N3][N2][N1].
+ * Compressed coefficients (8 n1 n2 n3 values per orbital): the scaling block
+ *   c^0[i3][i2][i1] followed by the wavelet block c^mu[i3][i2][i1][mu-1],
+ *   mu = a1 + 2 a2 + 4 a3 = 1..7 (a_d = 1 selects the wavelet along axis d).
+ * Orbitals of one call are contiguous, orbital o at offset o * 8 n1 n2 n3
+ *   (compressed) or o * P (fine).
+ * Precision: WVL_F64 -- every array is double.  WVL_F32 -- coefficient, fine
+ *   and potential arrays are float; rho, occ and energies stay double, and
+ *   every reduction (rho over orbitals, Ekin, Epot) is carried at least in
+ *   compensated single (~48-bit) inside a thread and in double above it.
+ * Memory: every data pointer is DEVICE memory owned by the caller and must be
+ *   16-byte aligned; the library allocates nothing on these calls.  Scratch
+ *   space is the caller's workspace `ws` of `ws_bytes` bytes, at least
+ *   wvl_workspace_size(); its contents are clobbered.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream); every
+ *   call only enqueues work and returns without synchronising.  Calls on the
+ *   same stream are ordered; calls sharing a workspace must not overlap.
+ * rho is ACCUMULATED (+=); energies are WRITTEN, one double per orbital.
+ * Errors: arguments are validated on the host before anything is enqueued;
+ *   on error nothing is enqueued, the status is returned and a detail string
+ *   is available from wvl_last_error() (thread-local).  Launch failures are
+ *   returned as WVL_ECUDA.  No call traps, asserts on the device or throws.
+ */
+#ifndef WVL_H
+#define WVL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WVL_OK = 0,
+    WVL_EINVAL = 1,        /* bad argument: null, size, misalignment      */
+    WVL_ENOMEM_WS = 2,     /* workspace smaller than required             */
+    WVL_ECUDA = 3,         /* a CUDA runtime call failed                  */
+    WVL_ETIMEOUT = 4,      /* a bounded device-side wait gave up          */
+    WVL_EUNSUPPORTED = 5   /* size or option outside what is implemented  */
+} wvl_status;
+
+typedef enum { WVL_F64 = 0, WVL_F32 = 1 } wvl_prec;
+
+/* Coarse grid and fine spacing h'_d = h_d / 2 (paper Eq. wavefhigh). */
+typedef struct {
+    int n1, n2, n3;
+    double h1, h2, h3;
+} wvl_grid;
+
+/* Largest fine extent N_d = 2 n_d a 1D pass keeps in shared memory. */
+#define WVL_MAX_FINE 1024
+
+const char* wvl_status_string(int status);
+const char* wvl_last_error(void);
+int wvl_version(void);
+
+/* Number of CUDA devices visible to the library (0 without a GPU); host only. */
+int wvl_device_count(void);
+
+/* Running count of kernels this library has enqueued in this process: direct
+ * launches plus every kernel node of each replayed plan graph. */
+unsigned long long wvl_kernel_launches(void);
+
+/*
+ * Filters derived by the library (host computation, no GPU needed), FP64.
+ *  h[16], g[16]: h_j, g_j for j = -7..8 (Eq. refinement, g_j = (-1)^j h_{1-j});
+ *  w[16], *k0: magic filter w_k for k = k0..k0+15 (Eq. magicfilter);
+ *  a[29]: a_l = int phi phi''(x-l) dx for l = -14..14, so that the 1D
+ *         kinetic filter of Eq. (fprod) along axis d is T_l = -a_l/(2 h'_d^2).
+ * Any pointer may be NULL.
+ */
+wvl_status wvl_filters(double* h, double* g, double* w, int* k0, double* a);
+
+/* Workspace bytes sufficient for every entry point below on `grid` with
+ * `norb` orbitals in precision `prec`. */
+wvl_status wvl_workspace_size(const wvl_grid* grid, int prec, int norb,
+                              size_t* bytes);
+
+/* Steps 1)+2): compressed coefficients -> fine scaling coefficients s
+ * (fast wavelet synthesis, Sec. "Daubechies basis and wavelet
+ * transformation"): psi_c [norb][8 n1 n2 n3] -> s [norb][N3][N2][N1]. */
+wvl_status wvl_synthesis(const wvl_grid* grid, int prec, int norb,
+                         const void* psi_c, void* s,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* Steps 6)+7): the transpose (inverse) of wvl_synthesis:
+ * z [norb][N3][N2][N1] -> psi_c [norb][8 n1 n2 n3]. */
+wvl_status wvl_analysis(const wvl_grid* grid, int prec, int norb,
+                        const void* z, void* psi_c,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* Step 3a), Eq. (3dconv): psi_r(I) = sum_j w_j1 w_j2 w_j3 s(I - j);
+ * s, psi_r: [norb][N3][N2][N1]. */
+wvl_status wvl_magicfilter(const wvl_grid* grid, int prec, int norb,
+                           const void* s, void* psi_r,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/* Step 3c): the transposed magic filter, y(J) = sum_j w w w y_r(J + j). */
+wvl_status wvl_magicfilter_T(const wvl_grid* grid, int prec, int norb,
+                             const void* y_r, void* y,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/* Step 4) (+5) through K_0, Sec. "Kinetic convolution", Eq. (kinetic1d)):
+ * out = K0 + (-1/2 Lap) s, with K0 = 0 when k0 is NULL;
+ * ekin[o] = <s_o, (-1/2 Lap) s_o> when ekin is not NULL (device, double). */
+wvl_status wvl_kinetic(const wvl_grid* grid, int prec, int norb,
+                       const void* s, const void* k0, void* out, double* ekin,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Sec. "Local density calculation": steps 1), 2), 3a) then
+ * rho[N3][N2][N1] += sum_o occ[o] psi_r,o^2 (grid units).  occ: device
+ * double[norb]; rho: device double, accumulated. */
+wvl_status wvl_density(const wvl_grid* grid, int prec, int norb,
+                       const void* psi_c, const double* occ, double* rho,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* The whole local Hamiltonian of Sec. "Full local hamiltonian" for norb
+ * orbitals of one cell: hpsi_c = A^T (M^T V M + K) A psi_c, with the density
+ * of step 3a) accumulated into rho when rho is not NULL, and per-orbital
+ * ekin[o] = <s, -1/2 Lap s>, epot[o] = sum_I V psi_r^2 (device doubles,
+ * written).  V: [N3][N2][N1] in the orbital precision. */
+wvl_status wvl_hpsi_local(const wvl_grid* grid, int prec, int norb,
+                          const void* psi_c, const void* V, const double* occ,
+                          void* hpsi_c, double* rho, double* ekin, double* epot,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* Forward of E_loc = sum_o occ_o (Ekin_o + Epot_o): the energies (and rho
+ * when not NULL) without H psi -- steps 1), 2), 3a), 3b) and 4) only. */
+wvl_status wvl_energy(const wvl_grid* grid, int prec, int norb,
+                      const void* psi_c, const void* V, const double* occ,
+                      double* rho, double* ekin, double* epot,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched plans: many orbitals on cells of different sizes in one enqueue
+ * (the paper's orbital distribution, Sec. "Parallel distribution", inside
+ * one GPU).  Orbital o lives on cell cell_of_orb[o]; orbitals are stored one
+ * after another in the given order, each with its own cell's size.  Runs of
+ * consecutive orbitals on the same cell form one segment of each launch.
+ * ---------------------------------------------------------------------- */
+typedef struct wvl_plan wvl_plan;
+
+#define WVL_PLAN_GRAPH    1u   /* replay a captured CUDA graph when pointers repeat */
+#define WVL_PLAN_AUTOTUNE 2u   /* wvl_plan_autotune may time kernel variants */
+
+/* Host-side; allocates the plan (host memory only).  cells[ncell],
+ * cell_of_orb[norb] are host arrays copied into the plan. */
+wvl_status wvl_plan_create(const wvl_grid* cells, int ncell,
+                           const int* cell_of_orb, int norb, int prec,
+                           unsigned flags, wvl_plan** out);
+wvl_status wvl_plan_destroy(wvl_plan* plan);
+wvl_status wvl_plan_workspace_size(const wvl_plan* plan, size_t* bytes);
+/* Element offset of orbital o in the concatenated compressed array. */
+wvl_status wvl_plan_orbital_offset(const wvl_plan* plan, int o, size_t* offset);
+
+/* Local Hamiltonian of every orbital of the plan.  psi, hpsi: concatenated
+ * compressed orbitals (device); V, rho: HOST arrays of ncell DEVICE pointers
+ * (rho entries may be NULL: no density for that cell); occ, ekin, epot:
+ * device double[norb]. */
+wvl_status wvl_plan_hpsi(wvl_plan* plan, const void* psi,
+                         const void* const* V, const double* occ, void* hpsi,
+                         double* const* rho, double* ekin, double* epot,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* Times the kernel variants of every pass of wvl_plan_hpsi on the given
+ * buffers (their contents are overwritten) and keeps the fastest for later
+ * calls.  Synchronises the stream.  Needs WVL_PLAN_AUTOTUNE. */
+wvl_status wvl_plan_autotune(wvl_plan* plan, const void* psi,
+                             const void* const* V, const double* occ,
+                             void* hpsi, double* const* rho, double* ekin,
+                             double* epot, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/* Human-readable choice of the autotuner (or the defaults), one line per
+ * pass; copies at most len-1 characters. */
+wvl_status wvl_plan_describe(const wvl_plan* plan, char* buf, size_t len);
+
+/* Tracing: when on, every stage of wvl_plan_hpsi is bracketed by CUDA
+ * events on the launching stream (graph replay is then bypassed).
+ * wvl_plan_profile() synchronises those events and returns, per stage, the
+ * summed milliseconds and the launch count since the last read, then
+ * clears them.  Stages: 0 synthesis, 1 magic filter + potential/density,
+ * 2 transposed magic filter, 3 kinetic, 4 analysis, 5 reductions. */
+#define WVL_NSTAGE 6
+wvl_status wvl_plan_set_profiling(wvl_plan* plan, int on);
+wvl_status wvl_plan_profile(wvl_plan* plan, double* ms, int* launches,
+                            int nstage);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WVL_H */

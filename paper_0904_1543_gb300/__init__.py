@@ -1,0 +1,401 @@
+"""Python binding of libwvl (the C ABI in include/wvl.h).
+
+Argument marshalling only: every step of the local Hamiltonian runs in the
+library's CUDA kernels.  PyTorch provides device memory (inputs, outputs and
+the scratch workspace) and the current CUDA stream.  There is no CPU fallback:
+if libwvl.so cannot be loaded the calls raise.
+
+Layouts (see include/wvl.h): compressed orbitals ``(norb, 8 n1 n2 n3)``, fine
+arrays ``(norb, N3, N2, N1)`` with N_d = 2 n_d, potential and density
+``(N3, N2, N1)``.  float64 tensors select the FP64 kernels, float32 tensors
+the FP32 kernels (density, occupations and energies stay float64).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "WvlError", "Grid", "lib", "filters", "workspace_size", "synthesis", "analysis",
+    "magicfilter", "magicfilter_T", "kinetic", "density", "hpsi_local", "energy",
+    "Plan", "ELoc", "device_count",
+]
+
+WVL_F64, WVL_F32 = 0, 1
+WVL_PLAN_GRAPH, WVL_PLAN_AUTOTUNE = 1, 2
+WVL_NSTAGE = 6
+STAGES = ("synthesis", "magicfilter+potential", "magicfilter_T", "kinetic", "analysis",
+          "reductions")
+
+
+class WvlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int),
+                ("h1", ctypes.c_double), ("h2", ctypes.c_double), ("h3", ctypes.c_double)]
+
+
+@dataclass(frozen=True)
+class Grid:
+    """Coarse extents (n1, n2, n3) and fine spacings h' = (h1, h2, h3)."""
+    n: tuple
+    h: tuple = (0.25, 0.25, 0.25)
+
+    @property
+    def fine(self):
+        return (2 * self.n[2], 2 * self.n[1], 2 * self.n[0])   # (N3, N2, N1)
+
+    @property
+    def ncoef(self):
+        return 8 * self.n[0] * self.n[1] * self.n[2]
+
+    def c(self):
+        return _Grid(self.n[0], self.n[1], self.n[2], *map(float, self.h))
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+
+
+def _declare(L):
+    G = ctypes.POINTER(_Grid)
+    sigs = {
+        "wvl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "wvl_last_error": (ctypes.c_char_p, []),
+        "wvl_version": (ctypes.c_int, []),
+        "wvl_device_count": (ctypes.c_int, []),
+        "wvl_kernel_launches": (ctypes.c_ulonglong, []),
+        "wvl_filters": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "wvl_workspace_size": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_sz)]),
+        "wvl_synthesis": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
+        "wvl_analysis": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
+        "wvl_magicfilter": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
+        "wvl_magicfilter_T": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
+        "wvl_kinetic": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+        "wvl_density": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _vp]),
+        "wvl_hpsi_local": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
+                                          _vp, _vp, _vp, _sz, _vp]),
+        "wvl_energy": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
+                                      _vp, _sz, _vp]),
+        "wvl_plan_create": (ctypes.c_int, [G, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_uint, ctypes.POINTER(_vp)]),
+        "wvl_plan_destroy": (ctypes.c_int, [_vp]),
+        "wvl_plan_workspace_size": (ctypes.c_int, [_vp, ctypes.POINTER(_sz)]),
+        "wvl_plan_orbital_offset": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_sz)]),
+        "wvl_plan_hpsi": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+        "wvl_plan_autotune": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+        "wvl_plan_describe": (ctypes.c_int, [_vp, ctypes.c_char_p, _sz]),
+        "wvl_plan_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "wvl_plan_profile": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def lib():
+    """The loaded libwvl.so (built in-tree on first use if nvcc is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB) or not _build.up_to_date():
+                try:
+                    _build.build()
+                except Exception as e:   # no toolkit: only a prebuilt library will do
+                    if not os.path.exists(_build.LIB):
+                        raise RuntimeError(f"libwvl.so is missing and cannot be built: {e}")
+            _lib = _declare(ctypes.CDLL(_build.LIB))
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        L = lib()
+        raise WvlError(status, L.wvl_status_string(status).decode() + ": "
+                       + (L.wvl_last_error() or b"").decode())
+
+
+def device_count():
+    return lib().wvl_device_count()
+
+
+def kernel_launches():
+    """Kernels enqueued by the library so far in this process."""
+    return lib().wvl_kernel_launches()
+
+
+def filters():
+    """The library's own filters: h, g (16), w (16) with k0, a (29)."""
+    import numpy as np
+    h, g, w, a = (np.zeros(16), np.zeros(16), np.zeros(16), np.zeros(29))
+    k0 = ctypes.c_int(0)
+    _check(lib().wvl_filters(h.ctypes.data, g.ctypes.data, w.ctypes.data,
+                             ctypes.addressof(k0), a.ctypes.data))
+    return {"h": h, "g": g, "w": w, "k0": k0.value, "a": a}
+
+
+def _prec(t):
+    if t.dtype == torch.float64:
+        return WVL_F64
+    if t.dtype == torch.float32:
+        return WVL_F32
+    raise TypeError(f"unsupported dtype {t.dtype}: use float64 or float32")
+
+
+def workspace_size(grid: Grid, prec: int, norb: int) -> int:
+    out = _sz(0)
+    _check(lib().wvl_workspace_size(ctypes.byref(grid.c()), prec, norb, ctypes.byref(out)))
+    return out.value
+
+
+_ws_cache = {}
+
+
+def _workspace(nbytes, device, stream):
+    """Per (device, stream) scratch buffer, grown on demand (256-byte aligned)."""
+    key = (device.index, int(stream))
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=device)
+        _ws_cache[key] = buf
+    ptr = buf.data_ptr()
+    off = (-ptr) % 256
+    return ptr + off, buf.numel() - off
+
+
+def _stream(device):
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _dev(t, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _norb(x, per):
+    if x.numel() % per:
+        raise ValueError(f"tensor of {x.numel()} elements is not a whole number of orbitals of {per}")
+    return x.numel() // per
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+def _run(fn, grid, prec, norb, device, *ptrs):
+    st = _stream(device)
+    need = workspace_size(grid, prec, max(norb, 1))
+    ws, wsb = _workspace(need, device, st)
+    _check(fn(ctypes.byref(grid.c()), prec, norb, *ptrs, ws, wsb, st))
+
+
+def synthesis(psi_c, grid: Grid, out=None):
+    """Steps 1)+2): compressed coefficients -> fine scaling coefficients."""
+    norb = _norb(psi_c, grid.ncoef)
+    out = torch.empty((norb, *grid.fine), dtype=psi_c.dtype, device=psi_c.device) if out is None else out
+    _dev(psi_c, "psi_c"), _dev(out, "out")
+    _run(lib().wvl_synthesis, grid, _prec(psi_c), norb, psi_c.device, psi_c.data_ptr(), out.data_ptr())
+    return out
+
+
+def analysis(z, grid: Grid, out=None):
+    """Steps 6)+7): fine -> compressed (transpose of synthesis)."""
+    norb = _norb(z, grid.ncoef)
+    out = torch.empty((norb, grid.ncoef), dtype=z.dtype, device=z.device) if out is None else out
+    _dev(z, "z"), _dev(out, "out")
+    _run(lib().wvl_analysis, grid, _prec(z), norb, z.device, z.data_ptr(), out.data_ptr())
+    return out
+
+
+def magicfilter(s, grid: Grid, out=None):
+    norb = _norb(s, grid.ncoef)
+    out = torch.empty_like(s) if out is None else out
+    _dev(s, "s"), _dev(out, "out")
+    _run(lib().wvl_magicfilter, grid, _prec(s), norb, s.device, s.data_ptr(), out.data_ptr())
+    return out
+
+
+def magicfilter_T(y, grid: Grid, out=None):
+    norb = _norb(y, grid.ncoef)
+    out = torch.empty_like(y) if out is None else out
+    _dev(y, "y"), _dev(out, "out")
+    _run(lib().wvl_magicfilter_T, grid, _prec(y), norb, y.device, y.data_ptr(), out.data_ptr())
+    return out
+
+
+def kinetic(s, grid: Grid, k0=None, out=None, want_ekin=True):
+    """out = K0 + (-1/2 Lap) s and ekin[o] = <s_o, -1/2 Lap s_o>."""
+    norb = _norb(s, grid.ncoef)
+    out = torch.empty_like(s) if out is None else out
+    ek = torch.empty(norb, dtype=torch.float64, device=s.device) if want_ekin else None
+    _dev(s, "s"), _dev(out, "out")
+    if k0 is not None:
+        _dev(k0, "k0")
+    _run(lib().wvl_kinetic, grid, _prec(s), norb, s.device, s.data_ptr(), _p(k0),
+         out.data_ptr(), _p(ek))
+    return out, ek
+
+
+def density(psi_c, occ, grid: Grid, rho=None):
+    """rho += sum_o occ_o |psi_r,o|^2 (float64, (N3, N2, N1))."""
+    norb = _norb(psi_c, grid.ncoef)
+    rho = torch.zeros(grid.fine, dtype=torch.float64, device=psi_c.device) if rho is None else rho
+    _dev(psi_c, "psi_c"), _dev(occ, "occ"), _dev(rho, "rho")
+    _run(lib().wvl_density, grid, _prec(psi_c), norb, psi_c.device, psi_c.data_ptr(),
+         occ.data_ptr(), rho.data_ptr())
+    return rho
+
+
+def hpsi_local(psi_c, V, occ, grid: Grid, rho=None, out=None):
+    """H_loc psi for norb orbitals of one cell; rho += density if given.
+    Returns (hpsi_c, ekin, epot)."""
+    norb = _norb(psi_c, grid.ncoef)
+    out = torch.empty_like(psi_c) if out is None else out
+    ek = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    ep = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    for t, nm in ((psi_c, "psi_c"), (V, "V"), (occ, "occ"), (out, "out")):
+        _dev(t, nm)
+    if rho is not None:
+        _dev(rho, "rho")
+    _run(lib().wvl_hpsi_local, grid, _prec(psi_c), norb, psi_c.device, psi_c.data_ptr(),
+         V.data_ptr(), occ.data_ptr(), out.data_ptr(), _p(rho), ek.data_ptr(), ep.data_ptr())
+    return out, ek, ep
+
+
+def energy(psi_c, V, occ, grid: Grid, rho=None):
+    """Per-orbital (ekin, epot) without H psi; rho += density if given."""
+    norb = _norb(psi_c, grid.ncoef)
+    ek = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    ep = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    for t, nm in ((psi_c, "psi_c"), (V, "V"), (occ, "occ")):
+        _dev(t, nm)
+    if rho is not None:
+        _dev(rho, "rho")
+    _run(lib().wvl_energy, grid, _prec(psi_c), norb, psi_c.device, psi_c.data_ptr(),
+         V.data_ptr(), occ.data_ptr(), _p(rho), ek.data_ptr(), ep.data_ptr())
+    return ek, ep
+
+
+class Plan:
+    """Batched local Hamiltonian for orbitals on cells of different sizes
+    (one enqueue of every pass over all cells; optional graph replay and
+    autotuning)."""
+
+    def __init__(self, cells, cell_of_orb, prec=WVL_F64, graph=True, autotune=False):
+        self.cells = [c if isinstance(c, Grid) else Grid(tuple(c)) for c in cells]
+        self.cell_of_orb = [int(c) for c in cell_of_orb]
+        self.prec = prec
+        arr = (_Grid * len(self.cells))(*[c.c() for c in self.cells])
+        co = (ctypes.c_int * max(1, len(self.cell_of_orb)))(*self.cell_of_orb)
+        flags = (WVL_PLAN_GRAPH if graph else 0) | (WVL_PLAN_AUTOTUNE if autotune else 0)
+        h = _vp()
+        _check(lib().wvl_plan_create(arr, len(self.cells), co, len(self.cell_of_orb), prec,
+                                     flags, ctypes.byref(h)))
+        self._h = h
+        self.norb = len(self.cell_of_orb)
+        sz = _sz(0)
+        _check(lib().wvl_plan_workspace_size(h, ctypes.byref(sz)))
+        self.ws_bytes = sz.value
+        self.offsets = []
+        for o in range(self.norb + 1):
+            _check(lib().wvl_plan_orbital_offset(h, o, ctypes.byref(sz)))
+            self.offsets.append(sz.value)
+        self.total = self.offsets[-1]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.wvl_plan_destroy(h)
+            self._h = None
+
+    def _args(self, psi, V, occ, hpsi, rho, ekin, epot):
+        for t, nm in ((psi, "psi"), (occ, "occ"), (hpsi, "hpsi"), (ekin, "ekin"), (epot, "epot")):
+            _dev(t, nm)
+        if psi.numel() != self.total or hpsi.numel() != self.total:
+            raise ValueError("psi/hpsi must hold the plan's concatenated orbitals")
+        Vp = (_vp * len(self.cells))(*[_dev(v, "V") for v in V])
+        Rp = None
+        if rho is not None:
+            Rp = (_vp * len(self.cells))(*[(None if r is None else _dev(r, "rho")) for r in rho])
+        st = _stream(psi.device)
+        ws, wsb = _workspace(self.ws_bytes, psi.device, st)
+        return (self._h, psi.data_ptr(), Vp, occ.data_ptr(), hpsi.data_ptr(), Rp,
+                ekin.data_ptr(), epot.data_ptr(), ws, wsb, st)
+
+    def hpsi(self, psi, V, occ, hpsi=None, rho=None, ekin=None, epot=None):
+        dev = psi.device
+        hpsi = torch.empty_like(psi) if hpsi is None else hpsi
+        ekin = torch.empty(self.norb, dtype=torch.float64, device=dev) if ekin is None else ekin
+        epot = torch.empty(self.norb, dtype=torch.float64, device=dev) if epot is None else epot
+        _check(lib().wvl_plan_hpsi(*self._args(psi, V, occ, hpsi, rho, ekin, epot)))
+        return hpsi, ekin, epot
+
+    def autotune(self, psi, V, occ, hpsi=None, rho=None):
+        dev = psi.device
+        hpsi = torch.empty_like(psi) if hpsi is None else hpsi
+        ek = torch.empty(self.norb, dtype=torch.float64, device=dev)
+        ep = torch.empty(self.norb, dtype=torch.float64, device=dev)
+        _check(lib().wvl_plan_autotune(*self._args(psi, V, occ, hpsi, rho, ek, ep)))
+
+    def describe(self):
+        buf = ctypes.create_string_buffer(4096)
+        _check(lib().wvl_plan_describe(self._h, buf, 4096))
+        return buf.value.decode()
+
+    def set_profiling(self, on=True):
+        _check(lib().wvl_plan_set_profiling(self._h, int(bool(on))))
+
+    def profile(self):
+        """{stage: (ms, launches)} since the last read."""
+        import numpy as np
+        ms = np.zeros(WVL_NSTAGE)
+        cnt = np.zeros(WVL_NSTAGE, dtype=np.int32)
+        _check(lib().wvl_plan_profile(self._h, ms.ctypes.data, cnt.ctypes.data, WVL_NSTAGE))
+        return {STAGES[k]: (float(ms[k]), int(cnt[k])) for k in range(WVL_NSTAGE)}
+
+
+class ELoc(torch.autograd.Function):
+    """E_loc(psi, V) = sum_o occ_o (Ekin_o + Epot_o) for the orbitals of one
+    cell.  Forward runs steps 1), 2), 3a), 3b) and 4) only (energies, no
+    H psi); backward recomputes the real-space orbitals instead of storing
+    them and applies the full chain: dE/dpsi_o = 2 occ_o H psi_o (the
+    transposed filters are the adjoint kernels), dE/dV = rho."""
+
+    @staticmethod
+    def forward(ctx, psi, V, occ, grid):
+        rho = torch.zeros(grid.fine, dtype=torch.float64, device=psi.device)
+        ek, ep = energy(psi.detach(), V.detach(), occ, grid, rho=rho)
+        ctx.save_for_backward(psi, V, occ, rho)
+        ctx.grid = grid
+        return (occ * (ek + ep)).sum()
+
+    @staticmethod
+    def backward(ctx, g):
+        psi, V, occ, rho = ctx.saved_tensors
+        gpsi = gV = None
+        if ctx.needs_input_grad[0]:
+            hp, _, _ = hpsi_local(psi.detach(), V.detach(), occ, ctx.grid)
+            scale = (2.0 * occ * g).to(hp.dtype).view(-1, *([1] * (hp.dim() - 1)))
+            gpsi = hp * scale
+        if ctx.needs_input_grad[1]:
+            gV = (rho * g).to(V.dtype)
+        return gpsi, gV, None, None

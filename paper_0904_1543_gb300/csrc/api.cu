@@ -1,0 +1,1115 @@
+// Host side of the C ABI declared in include/wvl.h: argument validation,
+// workspace carving, the order of the 1D passes for each operator (paper
+// Sec. "Full local hamiltonian", Sec. "Local density calculation",
+// Sec. "Kinetic convolution"), the second-stage reductions, batched plans
+// (segments of equal-size cells, CUDA-graph replay, autotuning, tracing).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "wvl.h"
+#include "wvl_internal.h"
+
+namespace wvl {
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+static wvl_status fail(wvl_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+static wvl_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(WVL_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------ filters
+KindGeom kind_geom(int kind) {
+    const int k0 = filters().k0;
+    switch (kind) {
+    case K_MF:  return {16, 0, 0, 0, k0 + 15, -k0};
+    case K_MFT: return {16, 0, 0, 0, -k0, k0 + 15};
+    case K_KIN: return {29, 0, 0, 0, 14, 14};
+    case K_SYN: return {16, 0, 1, 1, 8, 8};
+    case K_ANA: return {16, 1, 0, 1, 8, 8};
+    }
+    return {0, 0, 0, 0, 0, 0};
+}
+
+// Tap t of parity e multiplies the input at position i - hl + off_e + t.
+template <typename T>
+void fill_taps(PassParams<T>& p, int kind, double hgrid) {
+    const FilterSet& F = filters();
+    auto H = [&](int j) { return F.h[j + 7]; };   // h_j, j = -7..8
+    auto G = [&](int j) { return F.g[j + 7]; };
+    for (int e = 0; e < 2; ++e)
+        for (int t = 0; t < 32; ++t) p.f[e][t] = T(0);
+    for (int t = 0; t < 16; ++t) {
+        switch (kind) {
+        case K_MF:  // psi_r(I) = sum_k w_k s(I - k), k = k0 + 15 - t
+            p.f[0][t] = p.f[1][t] = T(F.w[15 - t]);
+            break;
+        case K_MFT: // y(J) = sum_k w_k y_r(J + k), k = k0 + t
+            p.f[0][t] = p.f[1][t] = T(F.w[t]);
+            break;
+        case K_SYN: // s_i = sum_j h_{i-2j} c_j + g_{i-2j} d_j (interleaved c, d)
+            p.f[0][t] = T((t % 2 == 0) ? H(8 - t) : G(9 - t));
+            p.f[1][t] = T((t % 2 == 0) ? H(7 - t) : G(8 - t));
+            break;
+        case K_ANA: // c_j = sum_i h_{i-2j} s_i, d_j = sum_i g_{i-2j} s_i
+            p.f[0][t] = T(H(t - 7));
+            p.f[1][t] = T(G(t - 7));
+            break;
+        }
+    }
+    if (kind == K_KIN) {
+        // out(I) = sum_l T_l s(I - l), T_l = -a_l / (2 h'^2), l = 14 - t
+        const double sc = 2.0 * hgrid * hgrid;
+        for (int t = 0; t < 29; ++t) p.f[0][t] = p.f[1][t] = T(-F.a[28 - t] / sc);
+    }
+    p.hl = kind_geom(kind).hl;
+}
+template void fill_taps<double>(PassParams<double>&, int, double);
+template void fill_taps<float>(PassParams<float>&, int, double);
+
+static int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    dev &= 63;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 152;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+// ------------------------------------------------------------------ passes
+struct Tune {
+    int R = 8;
+    int LT = 32;
+};
+
+enum Op { OP_HPSI, OP_ENERGY, OP_DENSITY, OP_SYN, OP_ANA, OP_MF, OP_MFT, OP_KIN };
+enum Stage { ST_SYN = 0, ST_MF = 1, ST_MFT = 2, ST_KIN = 3, ST_ANA = 4, ST_RED = 5 };
+
+constexpr int GMAX = 16;   // orbital groups per cell in the potential pass
+constexpr int LT_MIN = 4;
+
+static void pass_dims(const int Nf[3], int pass, int& n, int& N) {
+    if (pass == 1) { n = Nf[0]; N = Nf[2] * Nf[1]; }
+    else if (pass == 2) { n = Nf[1]; N = Nf[0] * Nf[2]; }
+    else { n = Nf[2]; N = Nf[1] * Nf[0]; }
+}
+
+template <typename T>
+struct SegDesc {
+    Seg<T> s{};
+    int Nf[3] = {0, 0, 0};
+    double hax = 0.0;        // spacing of the pass axis (kinetic)
+    double* user_rho = nullptr;
+    double* rho_part = nullptr;
+    int groups = 1;          // M_POT: groups actually launched
+};
+
+template <typename T>
+struct PassCall {
+    int kind, mode, pass, stage;
+    std::vector<SegDesc<T>> segs;
+};
+
+static int rowlen_of(int n, int R, const KindGeom& g) {
+    int nch = (n + R - 1) / R;
+    int rl = nch * R + g.hl + g.hr;
+    if ((rl & 1) == 0) rl += 1;   // odd stride: conflict-free lane-per-line reads
+    return rl;
+}
+
+template <typename T>
+static bool tune_valid(const PassCall<T>& c, const Tune& t) {
+    const KindGeom g = kind_geom(c.kind);
+    for (const auto& d : c.segs) {
+        int n, N;
+        pass_dims(d.Nf, c.pass, n, N);
+        if ((size_t)t.LT * rowlen_of(n, t.R, g) * sizeof(T) > 200 * 1024) return false;
+        if (c.mode == M_POT) {
+            const int nslots = (NTHREADS / 32) * (32 / t.LT);
+            const int cpt = POT_OUT / t.R;
+            if ((long long)cpt * nslots < (n + t.R - 1) / t.R) return false;
+        }
+    }
+    return true;
+}
+
+template <typename T>
+static long long blocks_of(const PassCall<T>& c, const Tune& t) {
+    long long b = 0;
+    for (const auto& d : c.segs) {
+        int n, N;
+        pass_dims(d.Nf, c.pass, n, N);
+        const long long units = (c.mode == M_POT) ? std::min(d.s.norb, GMAX) : d.s.norb;
+        b += (long long)((N + t.LT - 1) / t.LT) * units;
+    }
+    return b;
+}
+
+template <typename T>
+static Tune default_tune(const PassCall<T>& c) {
+    const long long want = 2LL * num_sms();
+    const int lts[4] = {32, 16, 8, 4};
+    for (int R : {8, 4}) {
+        Tune best;
+        bool have = false;
+        for (int lt : lts) {
+            Tune t;
+            t.R = R;
+            t.LT = lt;
+            if (!tune_valid(c, t)) continue;
+            best = t;
+            have = true;
+            if (blocks_of(c, t) >= want) break;
+        }
+        if (have) return best;
+    }
+    Tune t;
+    t.R = 4;
+    t.LT = LT_MIN;
+    return t;
+}
+
+template <typename T>
+static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
+    const KindGeom g = kind_geom(c.kind);
+    size_t i = 0;
+    while (i < c.segs.size()) {
+        PassParams<T> p;
+        std::memset(&p, 0, sizeof p);
+        const double hax = c.segs[i].hax;
+        fill_taps(p, c.kind, hax);
+        p.LT = tn.LT;
+        long long blk = 0;
+        size_t smem = 0;
+        int k = 0;
+        const size_t first = i;
+        for (; i < c.segs.size() && k < MAXSEG; ++i, ++k) {
+            SegDesc<T>& d = c.segs[i];
+            if (c.kind == K_KIN && i > first && d.hax != hax) break;
+            Seg<T>& s = d.s;
+            pass_dims(d.Nf, c.pass, s.n, s.N);
+            s.tiles = (s.N + tn.LT - 1) / tn.LT;
+            s.rowlen = rowlen_of(s.n, tn.R, g);
+            long long units = s.norb;
+            if (c.mode == M_POT) {
+                const long long want = 4LL * num_sms();
+                int gmax = s.norb;
+                if (d.user_rho) gmax = d.rho_part ? std::min(GMAX, s.norb) : 1;
+                long long G = (want + s.tiles - 1) / s.tiles;
+                G = std::max(1LL, std::min<long long>(G, gmax));
+                s.opg = (int)((s.norb + G - 1) / G);
+                G = (s.norb + s.opg - 1) / s.opg;
+                d.groups = (int)G;
+                units = G;
+                if (d.user_rho == nullptr) {
+                    s.rho = nullptr;
+                    s.rho_gstride = 0;
+                } else if (G == 1) {
+                    s.rho = d.user_rho;
+                    s.rho_gstride = 0;
+                } else {
+                    s.rho = d.rho_part;
+                    s.rho_gstride = s.P;
+                }
+            }
+            s.blk0 = blk;
+            blk += units * s.tiles;
+            smem = std::max(smem, (size_t)tn.LT * s.rowlen * sizeof(T));
+            p.seg[k] = s;
+        }
+        p.nseg = k;
+        cudaError_t e = launch_pass<T>(c.kind, c.mode, tn.R, p, blk, smem, st);
+        if (e != cudaSuccess) return cuda_fail(e, "pass launch");
+    }
+    return WVL_OK;
+}
+
+// ------------------------------------------------------------------ runs
+template <typename T>
+struct CellRun {
+    int n[3];
+    int Nf[3];
+    double hg[3];
+    int norb;
+    long long P;
+    const T* in;       // psi_c (or the op's input)
+    T* out;            // hpsi_c (or the op's output)
+    const T* V;        // potential (OP_HPSI/OP_ENERGY) or K0 (OP_KIN)
+    double* rho;
+    const double* occ;
+    double* ekin;
+    double* epot;
+    T* buf[4];
+    double* epart;
+    double* kpart;
+    double* rpart;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static long long tiles_max(const int Nf[3]) {
+    long long N = (long long)Nf[1] * Nf[0];
+    return (N + LT_MIN - 1) / LT_MIN;
+}
+
+// workspace bytes of one cell run
+static size_t run_ws_bytes(const int Nf[3], int norb, size_t elt) {
+    const long long P = (long long)Nf[0] * Nf[1] * Nf[2];
+    size_t b = 4 * align256((size_t)norb * P * elt);
+    b += 2 * align256((size_t)norb * tiles_max(Nf) * sizeof(double));
+    b += align256((size_t)std::min(GMAX, std::max(norb, 1)) * P * sizeof(double));
+    return b;
+}
+
+template <typename T>
+static void carve(CellRun<T>& r, char* ws) {
+    const size_t fb = align256((size_t)r.norb * r.P * sizeof(T));
+    for (int k = 0; k < 4; ++k) r.buf[k] = reinterpret_cast<T*>(ws + k * fb);
+    char* q = ws + 4 * fb;
+    const size_t pb = align256((size_t)r.norb * tiles_max(r.Nf) * sizeof(double));
+    r.epart = reinterpret_cast<double*>(q);
+    r.kpart = reinterpret_cast<double*>(q + pb);
+    r.rpart = reinterpret_cast<double*>(q + 2 * pb);
+}
+
+template <typename T>
+static SegDesc<T> seg_for(const CellRun<T>& c, const T* in, T* out) {
+    SegDesc<T> d;
+    d.s.in = in;
+    d.s.out = out;
+    d.s.P = c.P;
+    d.s.N1 = c.Nf[0];
+    d.s.N2 = c.Nf[1];
+    d.s.n1 = c.n[0];
+    d.s.n2 = c.n[1];
+    d.s.norb = c.norb;
+    d.s.opg = 1;
+    for (int k = 0; k < 3; ++k) d.Nf[k] = c.Nf[k];
+    return d;
+}
+
+template <typename T>
+static std::vector<PassCall<T>> build_calls(int op, std::vector<CellRun<T>>& runs) {
+    std::vector<PassCall<T>> calls;
+    auto add = [&](int kind, int mode, int pass, int stage, auto&& make) {
+        PassCall<T> c{kind, mode, pass, stage, {}};
+        for (auto& r : runs) c.segs.push_back(make(r));
+        calls.push_back(std::move(c));
+    };
+    auto B = [](CellRun<T>& r, int k) { return r.buf[k]; };
+    const int A_ = 0, B_ = 1, C_ = 2, D_ = 3;
+
+    auto synthesis = [&](bool to_user) {
+        add(K_SYN, M_UNCOMP, 1, ST_SYN, [&](CellRun<T>& r) { return seg_for(r, r.in, B(r, A_)); });
+        add(K_SYN, M_PLAIN, 2, ST_SYN, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
+        add(K_SYN, M_PLAIN, 3, ST_SYN, [&](CellRun<T>& r) {
+            return seg_for<T>(r, B(r, B_), to_user ? r.out : B(r, D_));
+        });
+    };
+    auto mf_pot = [&](bool with_v, bool write_y) {
+        add(K_MF, M_PLAIN, 1, ST_MF, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, D_), B(r, A_)); });
+        add(K_MF, M_PLAIN, 2, ST_MF, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
+        add(K_MF, M_POT, 3, ST_MF, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, B_), write_y ? B(r, A_) : nullptr);
+            d.s.aux = with_v ? r.V : nullptr;
+            d.s.occ = r.occ;
+            d.s.part = r.epart;
+            d.user_rho = r.rho;
+            d.rho_part = r.rpart;
+            return d;
+        });
+    };
+
+    switch (op) {
+    case OP_SYN:
+        synthesis(true);
+        break;
+    case OP_ANA:
+        add(K_ANA, M_PLAIN, 1, ST_ANA, [&](CellRun<T>& r) { return seg_for(r, r.in, B(r, A_)); });
+        add(K_ANA, M_PLAIN, 2, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
+        add(K_ANA, M_COMP, 3, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, B_), r.out); });
+        break;
+    case OP_MF:
+    case OP_MFT: {
+        const int kd = (op == OP_MF) ? K_MF : K_MFT;
+        const int st = (op == OP_MF) ? ST_MF : ST_MFT;
+        add(kd, M_PLAIN, 1, st, [&](CellRun<T>& r) { return seg_for(r, r.in, B(r, A_)); });
+        add(kd, M_PLAIN, 2, st, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
+        add(kd, M_PLAIN, 3, st, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, B_), r.out); });
+        break;
+    }
+    case OP_KIN: {
+        // K_1 = T_x s + K0 -> A, G_1 = s^T -> B; K_2 -> C, G_2 -> D; K_3 -> out
+        add(K_KIN, M_KMID, 1, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for(r, r.in, B(r, A_));
+            d.s.in2 = r.V;
+            d.s.out2 = B(r, B_);
+            d.hax = r.hg[0];
+            return d;
+        });
+        add(K_KIN, M_KMID, 2, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, B_), B(r, C_));
+            d.s.in2 = B(r, A_);
+            d.s.out2 = B(r, D_);
+            d.hax = r.hg[1];
+            return d;
+        });
+        add(K_KIN, M_KLAST, 3, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, D_), r.out);
+            d.s.in2 = B(r, C_);
+            d.s.aux = r.V;
+            d.s.part = r.kpart;
+            d.hax = r.hg[2];
+            return d;
+        });
+        break;
+    }
+    case OP_DENSITY:
+        synthesis(false);
+        mf_pot(false, false);
+        break;
+    case OP_ENERGY:
+        synthesis(false);
+        mf_pot(true, false);
+        // kinetic with K0 = 0 on s (D): K_1 -> A, G_1 -> C, K_2 -> B, G_2 -> D
+        add(K_KIN, M_KMID, 1, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, D_), B(r, A_));
+            d.s.out2 = B(r, C_);
+            d.hax = r.hg[0];
+            return d;
+        });
+        add(K_KIN, M_KMID, 2, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, C_), B(r, B_));
+            d.s.in2 = B(r, A_);
+            d.s.out2 = B(r, D_);
+            d.hax = r.hg[1];
+            return d;
+        });
+        add(K_KIN, M_KLAST, 3, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, D_), nullptr);
+            d.s.in2 = B(r, B_);
+            d.s.part = r.kpart;
+            d.hax = r.hg[2];
+            return d;
+        });
+        break;
+    case OP_HPSI:
+        synthesis(false);                      // s -> D
+        mf_pot(true, true);                    // V psi_r -> A
+        add(K_MFT, M_PLAIN, 1, ST_MFT, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
+        add(K_MFT, M_PLAIN, 2, ST_MFT, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, B_), B(r, A_)); });
+        add(K_MFT, M_PLAIN, 3, ST_MFT, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
+        // kinetic on s (D) with K_0 = y (B), Eq. (kinetic1d) with K_0 != 0
+        add(K_KIN, M_KMID, 1, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, D_), B(r, A_));
+            d.s.in2 = B(r, B_);
+            d.s.out2 = B(r, C_);
+            d.hax = r.hg[0];
+            return d;
+        });
+        add(K_KIN, M_KMID, 2, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, C_), B(r, B_));
+            d.s.in2 = B(r, A_);
+            d.s.out2 = B(r, D_);
+            d.hax = r.hg[1];
+            return d;
+        });
+        // K_3 = z -> A; partials of <s, K_3> = Ekin + Epot
+        add(K_KIN, M_KLAST, 3, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, D_), B(r, A_));
+            d.s.in2 = B(r, B_);
+            d.s.part = r.kpart;
+            d.hax = r.hg[2];
+            return d;
+        });
+        add(K_ANA, M_PLAIN, 1, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
+        add(K_ANA, M_PLAIN, 2, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, B_), B(r, A_)); });
+        add(K_ANA, M_COMP, 3, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), r.out); });
+        break;
+    }
+    return calls;
+}
+
+template <typename T>
+static wvl_status exec_reductions(int op, std::vector<CellRun<T>>& runs,
+                                  std::vector<PassCall<T>>& calls, cudaStream_t st) {
+    const PassCall<T>* pot = nullptr;
+    const PassCall<T>* kl = nullptr;
+    for (auto& c : calls) {
+        if (c.mode == M_POT) pot = &c;
+        if (c.mode == M_KLAST) kl = &c;
+    }
+    for (size_t i = 0; i < runs.size(); ++i) {
+        CellRun<T>& r = runs[i];
+        cudaError_t e = cudaSuccess;
+        if (pot) {
+            const SegDesc<T>& d = pot->segs[i];
+            if (r.rho && d.groups > 1) {
+                e = launch_rho_reduce(r.rpart, r.P, d.groups, r.rho, st);
+                if (e != cudaSuccess) return cuda_fail(e, "density reduction");
+            }
+            if ((op == OP_HPSI || op == OP_ENERGY) && r.epot) {
+                e = launch_reduce_parts(r.epart, nullptr, d.s.tiles, r.norb, r.epot, st);
+                if (e != cudaSuccess) return cuda_fail(e, "epot reduction");
+            }
+        }
+        if (kl && r.ekin) {
+            const SegDesc<T>& d = kl->segs[i];
+            // OP_HPSI accumulates <s, z> = Ekin + Epot; subtract Epot
+            const double* minus = (op == OP_HPSI) ? r.epot : nullptr;
+            e = launch_reduce_parts(r.kpart, minus, d.s.tiles, r.norb, r.ekin, st);
+            if (e != cudaSuccess) return cuda_fail(e, "ekin reduction");
+        }
+    }
+    return WVL_OK;
+}
+
+// --------------------------------------------------------------- tracing
+struct Prof {
+    bool on = false;
+    std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[WVL_NSTAGE] = {0};
+    int cnt[WVL_NSTAGE] = {0};
+
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void flush() {
+        for (auto& t : pending) {
+            float v = 0.f;
+            cudaEventSynchronize(std::get<2>(t));
+            if (cudaEventElapsedTime(&v, std::get<1>(t), std::get<2>(t)) == cudaSuccess) {
+                ms[std::get<0>(t)] += v;
+                cnt[std::get<0>(t)] += 1;
+            }
+            pool.push_back(std::get<1>(t));
+            pool.push_back(std::get<2>(t));
+        }
+        pending.clear();
+    }
+    ~Prof() {
+        for (auto& t : pending) {
+            cudaEventDestroy(std::get<1>(t));
+            cudaEventDestroy(std::get<2>(t));
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+using TuneTable = std::map<int, Tune>;
+static int tune_key(int kind, int mode, int pass) { return kind * 100 + mode * 10 + pass; }
+
+template <typename T>
+static wvl_status run_op(int op, std::vector<CellRun<T>>& runs, const TuneTable* tt,
+                         Prof* prof, cudaStream_t st) {
+    std::vector<PassCall<T>> calls = build_calls<T>(op, runs);
+    int cur_stage = -1;
+    cudaEvent_t ev0 = nullptr;
+    auto stage_begin = [&](int stg) {
+        if (!prof || !prof->on || stg == cur_stage) return;
+        if (cur_stage >= 0) {
+            cudaEvent_t e1 = prof->get();
+            cudaEventRecord(e1, st);
+            prof->pending.emplace_back(cur_stage, ev0, e1);
+        }
+        cur_stage = stg;
+        ev0 = prof->get();
+        cudaEventRecord(ev0, st);
+    };
+    for (auto& c : calls) {
+        stage_begin(c.stage);
+        Tune t = default_tune(c);
+        if (tt) {
+            auto it = tt->find(tune_key(c.kind, c.mode, c.pass));
+            if (it != tt->end() && tune_valid(c, it->second)) t = it->second;
+        }
+        wvl_status s = exec_call(c, t, st);
+        if (s != WVL_OK) return s;
+    }
+    stage_begin(ST_RED);
+    wvl_status s = exec_reductions(op, runs, calls, st);
+    if (prof && prof->on && cur_stage >= 0) {
+        cudaEvent_t e1 = prof->get();
+        cudaEventRecord(e1, st);
+        prof->pending.emplace_back(cur_stage, ev0, e1);
+    }
+    return s;
+}
+
+// ------------------------------------------------------------ validation
+static wvl_status check_prec(int prec) {
+    if (prec != WVL_F64 && prec != WVL_F32) return fail(WVL_EINVAL, "prec must be WVL_F64 or WVL_F32");
+    return WVL_OK;
+}
+static wvl_status check_grid(const wvl_grid* g) {
+    if (!g) return fail(WVL_EINVAL, "grid is NULL");
+    const int n[3] = {g->n1, g->n2, g->n3};
+    const double h[3] = {g->h1, g->h2, g->h3};
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] < 1) return fail(WVL_EINVAL, "grid extent n%d = %d < 1", d + 1, n[d]);
+        if (2LL * n[d] > MAX_FINE)
+            return fail(WVL_EUNSUPPORTED, "fine extent 2*n%d = %lld exceeds %d", d + 1,
+                        2LL * n[d], MAX_FINE);
+        if (!(h[d] > 0.0) || !std::isfinite(h[d]))
+            return fail(WVL_EINVAL, "fine spacing h%d must be positive and finite", d + 1);
+    }
+    const long long P = 8LL * n[0] * n[1] * n[2];
+    if (P > (1LL << 40)) return fail(WVL_EUNSUPPORTED, "grid too large");
+    return WVL_OK;
+}
+static wvl_status check_ptr(const void* p, const char* name, bool required) {
+    if (!p) return required ? fail(WVL_EINVAL, "%s is NULL", name) : WVL_OK;
+    if (reinterpret_cast<uintptr_t>(p) & 15) return fail(WVL_EINVAL, "%s is not 16-byte aligned", name);
+    return WVL_OK;
+}
+
+#define WVL_TRY(x)                          \
+    do {                                    \
+        wvl_status _s = (x);                \
+        if (_s != WVL_OK) return _s;        \
+    } while (0)
+
+static void grid_dims(const wvl_grid* g, int n[3], int Nf[3], double hg[3], long long& P) {
+    n[0] = g->n1; n[1] = g->n2; n[2] = g->n3;
+    hg[0] = g->h1; hg[1] = g->h2; hg[2] = g->h3;
+    for (int d = 0; d < 3; ++d) Nf[d] = 2 * n[d];
+    P = (long long)Nf[0] * Nf[1] * Nf[2];
+}
+
+template <typename T>
+static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void* in,
+                              void* out, const void* V, const double* occ, double* rho,
+                              double* ekin, double* epot, void* ws, size_t ws_bytes,
+                              void* stream) {
+    CellRun<T> r;
+    grid_dims(grid, r.n, r.Nf, r.hg, r.P);
+    r.norb = norb;
+    r.in = static_cast<const T*>(in);
+    r.out = static_cast<T*>(out);
+    r.V = static_cast<const T*>(V);
+    r.rho = rho;
+    r.occ = occ;
+    r.ekin = ekin;
+    r.epot = epot;
+    const size_t need = run_ws_bytes(r.Nf, norb, sizeof(T));
+    if (!ws) return fail(WVL_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(WVL_EINVAL, "workspace is not 256-byte aligned");
+    if (ws_bytes < need)
+        return fail(WVL_ENOMEM_WS, "workspace has %zu bytes, %zu needed", ws_bytes, need);
+    carve(r, static_cast<char*>(ws));
+    std::vector<CellRun<T>> runs(1, r);
+    return run_op<T>(op, runs, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+static wvl_status dispatch_single(int op, const wvl_grid* grid, int prec, int norb,
+                                  const void* in, void* out, const void* V,
+                                  const double* occ, double* rho, double* ekin,
+                                  double* epot, void* ws, size_t ws_bytes, void* stream) {
+    g_err[0] = 0;
+    if (prec == WVL_F64)
+        return single_cell<double>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
+                                   ws_bytes, stream);
+    return single_cell<float>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
+                              ws_bytes, stream);
+}
+
+}  // namespace wvl
+
+// ==================================================================== C ABI
+using namespace wvl;
+
+struct wvl_plan {
+    int prec = 0;
+    unsigned flags = 0;
+    std::vector<wvl_grid> cells;
+    std::vector<int> cell_of_orb;
+    int norb = 0;
+    std::vector<size_t> orb_off;
+    size_t total = 0;
+    struct Run {
+        int cell, o0, cnt;
+        size_t off, ws_off;
+    };
+    std::vector<Run> runs;
+    size_t ws_bytes = 0;
+    TuneTable tune;
+    bool tuned = false;
+    Prof prof;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void*> gkey;
+    size_t gnodes = 0;
+    std::mutex mu;
+    ~wvl_plan() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+extern "C" {
+
+const char* wvl_status_string(int s) {
+    switch (s) {
+    case WVL_OK: return "WVL_OK";
+    case WVL_EINVAL: return "WVL_EINVAL: invalid argument";
+    case WVL_ENOMEM_WS: return "WVL_ENOMEM_WS: workspace too small";
+    case WVL_ECUDA: return "WVL_ECUDA: CUDA runtime error";
+    case WVL_ETIMEOUT: return "WVL_ETIMEOUT: bounded device wait expired";
+    case WVL_EUNSUPPORTED: return "WVL_EUNSUPPORTED: unsupported size or option";
+    }
+    return "unknown wvl status";
+}
+
+const char* wvl_last_error(void) { return g_err; }
+
+int wvl_version(void) { return 10000; }
+
+unsigned long long wvl_kernel_launches(void) { return g_launches.load(); }
+
+int wvl_device_count(void) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+wvl_status wvl_filters(double* h, double* g, double* w, int* k0, double* a) {
+    const FilterSet& F = filters();
+    if (h) std::memcpy(h, F.h, sizeof F.h);
+    if (g) std::memcpy(g, F.g, sizeof F.g);
+    if (w) std::memcpy(w, F.w, sizeof F.w);
+    if (k0) *k0 = F.k0;
+    if (a) std::memcpy(a, F.a, sizeof F.a);
+    return WVL_OK;
+}
+
+wvl_status wvl_workspace_size(const wvl_grid* grid, int prec, int norb, size_t* bytes) {
+    g_err[0] = 0;
+    WVL_TRY(check_grid(grid));
+    WVL_TRY(check_prec(prec));
+    if (norb < 0) return fail(WVL_EINVAL, "norb < 0");
+    if (!bytes) return fail(WVL_EINVAL, "bytes is NULL");
+    int n[3], Nf[3];
+    double hg[3];
+    long long P;
+    grid_dims(grid, n, Nf, hg, P);
+    *bytes = run_ws_bytes(Nf, std::max(norb, 1), prec == WVL_F64 ? 8 : 4);
+    return WVL_OK;
+}
+
+#define WVL_COMMON_CHECKS()                        \
+    g_err[0] = 0;                                  \
+    WVL_TRY(check_grid(grid));                     \
+    WVL_TRY(check_prec(prec));                     \
+    if (norb < 0) return fail(WVL_EINVAL, "norb < 0"); \
+    if (norb == 0) return WVL_OK;
+
+wvl_status wvl_synthesis(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                         void* s, void* ws, size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    WVL_TRY(check_ptr(s, "s", true));
+    return dispatch_single(OP_SYN, grid, prec, norb, psi_c, s, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+wvl_status wvl_analysis(const wvl_grid* grid, int prec, int norb, const void* z,
+                        void* psi_c, void* ws, size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_ptr(z, "z", true));
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    return dispatch_single(OP_ANA, grid, prec, norb, z, psi_c, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+wvl_status wvl_magicfilter(const wvl_grid* grid, int prec, int norb, const void* s,
+                           void* psi_r, void* ws, size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_ptr(s, "s", true));
+    WVL_TRY(check_ptr(psi_r, "psi_r", true));
+    return dispatch_single(OP_MF, grid, prec, norb, s, psi_r, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+wvl_status wvl_magicfilter_T(const wvl_grid* grid, int prec, int norb, const void* y_r,
+                             void* y, void* ws, size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_ptr(y_r, "y_r", true));
+    WVL_TRY(check_ptr(y, "y", true));
+    return dispatch_single(OP_MFT, grid, prec, norb, y_r, y, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+wvl_status wvl_kinetic(const wvl_grid* grid, int prec, int norb, const void* s,
+                       const void* k0, void* out, double* ekin, void* ws, size_t ws_bytes,
+                       void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_ptr(s, "s", true));
+    WVL_TRY(check_ptr(k0, "k0", false));
+    WVL_TRY(check_ptr(out, "out", true));
+    WVL_TRY(check_ptr(ekin, "ekin", false));
+    return dispatch_single(OP_KIN, grid, prec, norb, s, out, k0, nullptr, nullptr, ekin,
+                           nullptr, ws, ws_bytes, stream);
+}
+
+wvl_status wvl_density(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                       const double* occ, double* rho, void* ws, size_t ws_bytes,
+                       void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    WVL_TRY(check_ptr(occ, "occ", true));
+    WVL_TRY(check_ptr(rho, "rho", true));
+    return dispatch_single(OP_DENSITY, grid, prec, norb, psi_c, nullptr, nullptr, occ, rho,
+                           nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+wvl_status wvl_hpsi_local(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                          const void* V, const double* occ, void* hpsi_c, double* rho,
+                          double* ekin, double* epot, void* ws, size_t ws_bytes,
+                          void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    WVL_TRY(check_ptr(V, "V", true));
+    WVL_TRY(check_ptr(occ, "occ", true));
+    WVL_TRY(check_ptr(hpsi_c, "hpsi_c", true));
+    WVL_TRY(check_ptr(rho, "rho", false));
+    WVL_TRY(check_ptr(ekin, "ekin", true));
+    WVL_TRY(check_ptr(epot, "epot", true));
+    return dispatch_single(OP_HPSI, grid, prec, norb, psi_c, hpsi_c, V, occ, rho, ekin, epot,
+                           ws, ws_bytes, stream);
+}
+
+wvl_status wvl_energy(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                      const void* V, const double* occ, double* rho, double* ekin,
+                      double* epot, void* ws, size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    WVL_TRY(check_ptr(V, "V", true));
+    WVL_TRY(check_ptr(occ, "occ", true));
+    WVL_TRY(check_ptr(rho, "rho", false));
+    WVL_TRY(check_ptr(ekin, "ekin", true));
+    WVL_TRY(check_ptr(epot, "epot", true));
+    return dispatch_single(OP_ENERGY, grid, prec, norb, psi_c, nullptr, V, occ, rho, ekin,
+                           epot, ws, ws_bytes, stream);
+}
+
+// ----------------------------------------------------------------- plans
+wvl_status wvl_plan_create(const wvl_grid* cells, int ncell, const int* cell_of_orb,
+                           int norb, int prec, unsigned flags, wvl_plan** out) {
+    g_err[0] = 0;
+    if (!out) return fail(WVL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cells || ncell < 1) return fail(WVL_EINVAL, "need at least one cell");
+    if (norb < 0 || (norb > 0 && !cell_of_orb)) return fail(WVL_EINVAL, "bad orbital list");
+    WVL_TRY(check_prec(prec));
+    if (flags & ~(WVL_PLAN_GRAPH | WVL_PLAN_AUTOTUNE)) return fail(WVL_EINVAL, "unknown plan flags");
+    for (int c = 0; c < ncell; ++c) WVL_TRY(check_grid(&cells[c]));
+    for (int o = 0; o < norb; ++o)
+        if (cell_of_orb[o] < 0 || cell_of_orb[o] >= ncell)
+            return fail(WVL_EINVAL, "cell_of_orb[%d] = %d out of range", o, cell_of_orb[o]);
+    wvl_plan* p = new (std::nothrow) wvl_plan;
+    if (!p) return fail(WVL_EINVAL, "host allocation failed");
+    p->prec = prec;
+    p->flags = flags;
+    p->cells.assign(cells, cells + ncell);
+    p->cell_of_orb.assign(cell_of_orb, cell_of_orb + norb);
+    p->norb = norb;
+    const size_t elt = prec == WVL_F64 ? 8 : 4;
+    size_t off = 0, wsoff = 0;
+    for (int o = 0; o < norb;) {
+        const int c = cell_of_orb[o];
+        int e = o;
+        while (e < norb && cell_of_orb[e] == c) ++e;
+        const wvl_grid& g = cells[c];
+        int n[3], Nf[3];
+        double hg[3];
+        long long P;
+        grid_dims(&g, n, Nf, hg, P);
+        wvl_plan::Run r{c, o, e - o, off, wsoff};
+        p->runs.push_back(r);
+        for (int k = o; k < e; ++k) {
+            p->orb_off.push_back(off);
+            off += (size_t)P;
+        }
+        wsoff += align256(run_ws_bytes(Nf, e - o, elt));
+        o = e;
+    }
+    p->total = off;
+    p->ws_bytes = std::max<size_t>(wsoff, 256);
+    *out = p;
+    return WVL_OK;
+}
+
+wvl_status wvl_plan_destroy(wvl_plan* plan) {
+    delete plan;
+    return WVL_OK;
+}
+
+wvl_status wvl_plan_workspace_size(const wvl_plan* plan, size_t* bytes) {
+    if (!plan || !bytes) return fail(WVL_EINVAL, "NULL argument");
+    *bytes = plan->ws_bytes;
+    return WVL_OK;
+}
+
+wvl_status wvl_plan_orbital_offset(const wvl_plan* plan, int o, size_t* offset) {
+    if (!plan || !offset) return fail(WVL_EINVAL, "NULL argument");
+    if (o < 0 || o > plan->norb) return fail(WVL_EINVAL, "orbital index out of range");
+    *offset = (o == plan->norb) ? plan->total : plan->orb_off[o];
+    return WVL_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static wvl_status plan_runs(wvl_plan* plan, const void* psi, const void* const* V,
+                            const double* occ, void* hpsi, double* const* rho, double* ekin,
+                            double* epot, void* ws, std::vector<CellRun<T>>& runs) {
+    for (const auto& pr : plan->runs) {
+        CellRun<T> r;
+        grid_dims(&plan->cells[pr.cell], r.n, r.Nf, r.hg, r.P);
+        r.norb = pr.cnt;
+        r.in = static_cast<const T*>(psi) + pr.off;
+        r.out = static_cast<T*>(hpsi) + pr.off;
+        r.V = static_cast<const T*>(V[pr.cell]);
+        r.rho = rho ? rho[pr.cell] : nullptr;
+        r.occ = occ + pr.o0;
+        r.ekin = ekin + pr.o0;
+        r.epot = epot + pr.o0;
+        carve(r, static_cast<char*>(ws) + pr.ws_off);
+        runs.push_back(r);
+    }
+    return WVL_OK;
+}
+
+static wvl_status plan_check(wvl_plan* plan, const void* psi, const void* const* V,
+                             const double* occ, void* hpsi, double* const* rho, double* ekin,
+                             double* epot, void* ws, size_t ws_bytes) {
+    if (!plan) return fail(WVL_EINVAL, "plan is NULL");
+    WVL_TRY(check_ptr(psi, "psi", true));
+    WVL_TRY(check_ptr(hpsi, "hpsi", true));
+    WVL_TRY(check_ptr(occ, "occ", true));
+    WVL_TRY(check_ptr(ekin, "ekin", true));
+    WVL_TRY(check_ptr(epot, "epot", true));
+    if (!V) return fail(WVL_EINVAL, "V is NULL");
+    for (size_t c = 0; c < plan->cells.size(); ++c) {
+        WVL_TRY(check_ptr(V[c], "V[cell]", true));
+        if (rho) WVL_TRY(check_ptr(rho[c], "rho[cell]", false));
+    }
+    if (!ws) return fail(WVL_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(WVL_EINVAL, "workspace is not 256-byte aligned");
+    if (ws_bytes < plan->ws_bytes)
+        return fail(WVL_ENOMEM_WS, "workspace has %zu bytes, %zu needed", ws_bytes, plan->ws_bytes);
+    return WVL_OK;
+}
+
+template <typename T>
+static wvl_status plan_exec(wvl_plan* plan, const void* psi, const void* const* V,
+                            const double* occ, void* hpsi, double* const* rho, double* ekin,
+                            double* epot, void* ws, cudaStream_t st) {
+    std::vector<CellRun<T>> runs;
+    plan_runs<T>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, runs);
+    const bool graph = (plan->flags & WVL_PLAN_GRAPH) && !plan->prof.on && st != nullptr;
+    if (!graph) return run_op<T>(OP_HPSI, runs, &plan->tune, &plan->prof, st);
+
+    std::vector<const void*> key = {psi, occ, hpsi, ekin, epot, ws};
+    for (size_t c = 0; c < plan->cells.size(); ++c) {
+        key.push_back(V[c]);
+        key.push_back(rho ? rho[c] : nullptr);
+    }
+    if (plan->gexec && key == plan->gkey) {
+        cudaError_t e = cudaGraphLaunch(plan->gexec, st);
+        if (e == cudaSuccess) count_launches(plan->gnodes);
+        return e == cudaSuccess ? WVL_OK : cuda_fail(e, "cudaGraphLaunch");
+    }
+    const unsigned long long before = g_launches.load();
+    // capture the enqueue sequence into a graph; the kernels' shared-memory
+    // attributes are set before capture (host-only calls)
+    cudaError_t e = prepare_pass_kernels<T>();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    wvl_status s = run_op<T>(OP_HPSI, runs, &plan->tune, nullptr, st);
+    e = cudaStreamEndCapture(st, &g);
+    if (s != WVL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    plan->graph = g;
+    plan->gexec = ge;
+    plan->gkey = key;
+    // the capture counted its kernels once; they run now, on the replay
+    plan->gnodes = (size_t)(g_launches.load() - before);
+    e = cudaGraphLaunch(ge, st);
+    return e == cudaSuccess ? WVL_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+extern "C" {
+
+wvl_status wvl_plan_hpsi(wvl_plan* plan, const void* psi, const void* const* V,
+                         const double* occ, void* hpsi, double* const* rho, double* ekin,
+                         double* epot, void* ws, size_t ws_bytes, void* stream) {
+    g_err[0] = 0;
+    WVL_TRY(plan_check(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, ws_bytes));
+    if (plan->norb == 0) return WVL_OK;
+    std::lock_guard<std::mutex> lk(plan->mu);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (plan->prec == WVL_F64) return plan_exec<double>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
+    return plan_exec<float>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
+}
+
+}  // extern "C"
+
+template <typename T>
+static wvl_status plan_tune(wvl_plan* plan, const void* psi, const void* const* V,
+                            const double* occ, void* hpsi, double* const* rho, double* ekin,
+                            double* epot, void* ws, cudaStream_t st) {
+    std::vector<CellRun<T>> runs;
+    plan_runs<T>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, runs);
+    // one full run leaves realistic values in every buffer
+    WVL_TRY(run_op<T>(OP_HPSI, runs, &plan->tune, nullptr, st));
+    std::vector<PassCall<T>> calls = build_calls<T>(OP_HPSI, runs);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    TuneTable best;
+    for (auto& c : calls) {
+        float bt = 1e30f;
+        Tune bv = default_tune(c);
+        for (int R : {4, 8})
+            for (int lt : {32, 16, 8, 4}) {
+                Tune t;
+                t.R = R;
+                t.LT = lt;
+                if (!tune_valid(c, t)) continue;
+                float tot = 0.f;
+                bool ok = true;
+                for (int rep = 0; rep < 3 && ok; ++rep) {
+                    cudaEventRecord(e0, st);
+                    ok = exec_call(c, t, st) == WVL_OK;
+                    cudaEventRecord(e1, st);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) tot += ms;   // first repetition is a warm-up
+                }
+                if (ok && tot < bt) {
+                    bt = tot;
+                    bv = t;
+                }
+            }
+        best[tune_key(c.kind, c.mode, c.pass)] = bv;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan->tune = best;
+    plan->tuned = true;
+    if (plan->gexec) {
+        cudaGraphExecDestroy(plan->gexec);
+        plan->gexec = nullptr;
+    }
+    if (plan->graph) {
+        cudaGraphDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    plan->gkey.clear();
+    cudaError_t e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? WVL_OK : cuda_fail(e, "autotune");
+}
+
+extern "C" {
+
+wvl_status wvl_plan_autotune(wvl_plan* plan, const void* psi, const void* const* V,
+                             const double* occ, void* hpsi, double* const* rho, double* ekin,
+                             double* epot, void* ws, size_t ws_bytes, void* stream) {
+    g_err[0] = 0;
+    WVL_TRY(plan_check(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, ws_bytes));
+    if (!(plan->flags & WVL_PLAN_AUTOTUNE)) return fail(WVL_EINVAL, "plan created without WVL_PLAN_AUTOTUNE");
+    if (plan->norb == 0) return WVL_OK;
+    std::lock_guard<std::mutex> lk(plan->mu);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (plan->prec == WVL_F64) return plan_tune<double>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
+    return plan_tune<float>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
+}
+
+wvl_status wvl_plan_describe(const wvl_plan* plan, char* buf, size_t len) {
+    if (!plan || !buf || len == 0) return fail(WVL_EINVAL, "NULL argument");
+    static const char* kn[] = {"synthesis", "analysis", "magicfilter", "magicfilter_T", "kinetic"};
+    std::string s = plan->tuned ? "autotuned\n" : "defaults\n";
+    for (const auto& kv : plan->tune) {
+        char line[128];
+        snprintf(line, sizeof line, "%s mode %d pass %d: R=%d LT=%d\n", kn[kv.first / 100],
+                 (kv.first / 10) % 10, kv.first % 10, kv.second.R, kv.second.LT);
+        s += line;
+    }
+    std::strncpy(buf, s.c_str(), len - 1);
+    buf[len - 1] = 0;
+    return WVL_OK;
+}
+
+wvl_status wvl_plan_set_profiling(wvl_plan* plan, int on) {
+    if (!plan) return fail(WVL_EINVAL, "plan is NULL");
+    std::lock_guard<std::mutex> lk(plan->mu);
+    plan->prof.on = on != 0;
+    return WVL_OK;
+}
+
+wvl_status wvl_plan_profile(wvl_plan* plan, double* ms, int* launches, int nstage) {
+    if (!plan) return fail(WVL_EINVAL, "plan is NULL");
+    std::lock_guard<std::mutex> lk(plan->mu);
+    plan->prof.flush();
+    for (int k = 0; k < nstage && k < WVL_NSTAGE; ++k) {
+        if (ms) ms[k] = plan->prof.ms[k];
+        if (launches) launches[k] = plan->prof.cnt[k];
+        plan->prof.ms[k] = 0;
+        plan->prof.cnt[k] = 0;
+    }
+    return WVL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Internal declarations shared by the host API and the kernel translation
+// units.  Not part of the public ABI (see include/wvl.h).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime_api.h>
+
+namespace wvl {
+
+// Filters of the method, derived on the host (filters.cpp).
+struct FilterSet {
+    double h[16];   // h_j, j = -7..8         (Eq. refinement)
+    double g[16];   // g_j = (-1)^j h_{1-j}
+    double w[16];   // w_k, k = k0..k0+15     (Eq. magicfilter)
+    double a[29];   // a_l, l = -14..14       (Eqs. kiner, fprod)
+    int k0;
+};
+const FilterSet& filters();
+
+// The five 1D operators.  Each 3D operator is three passes of
+// F(I, a) = sum_t f_t G(a, I - HL + off + t), output written transposed
+// (Eqs. 1dconvtrans and kinetic1d).
+enum Kind { K_SYN = 0, K_ANA = 1, K_MF = 2, K_MFT = 3, K_KIN = 4, NKIND = 5 };
+
+// Load/epilogue variants of a pass.
+enum Mode {
+    M_PLAIN = 0,   // read lines, write transposed
+    M_UNCOMP = 1,  // synthesis pass 1: gather lines from the compressed layout
+    M_COMP = 2,    // analysis pass 3: scatter into the compressed layout
+    M_POT = 3,     // magic-filter pass 3: V*psi, rho += occ psi^2, Epot partials
+    M_KMID = 4,    // kinetic pass 1/2: K_p = T*G + K_{p-1}, G_p = G^T
+    M_KLAST = 5,   // kinetic pass 3: K_3 and sum s*(K_3 - K0) partials
+    NMODE = 6
+};
+
+constexpr int MAXSEG = 8;      // cells (segments) per launch
+constexpr int NTHREADS = 128;  // threads per CTA (4 warps)
+constexpr int POT_OUT = 32;    // register-resident rho outputs per thread (M_POT)
+constexpr int MAX_FINE = 1024; // largest fine extent of one axis
+
+// One cell's orbitals inside one pass launch.  Element offsets are per
+// orbital; orbital o of the segment starts at o * P in every array (P = fine
+// points = compressed length).
+template <typename T>
+struct Seg {
+    const T* in;          // pass input (orbital 0 of the segment)
+    T* out;               // pass output (may be null for reduction-only M_POT/M_KLAST)
+    const T* in2;         // K_{p-1} for M_KMID/M_KLAST (null = 0)
+    T* out2;              // G_p for M_KMID
+    const T* aux;         // M_POT: V (null = no potential);  M_KLAST: K0 (null = 0)
+    double* rho;          // M_POT: density target (null = none)
+    double* part;         // per (orbital, tile) partial sums, [norb][tiles]
+    const double* occ;    // M_POT: occupations of the segment's orbitals
+    long long P;          // elements per orbital
+    long long rho_gstride;// M_POT: 0 -> rho += (direct), else group g writes rho[g*stride]
+    long long blk0;       // first block index of the segment in the launch
+    int n, N;             // line length and line count of this pass
+    int N1, N2;           // fine extents (index decoding)
+    int n1, n2;           // coarse extents (compressed layout)
+    int norb;
+    int tiles;            // ceil(N / LT)
+    int opg;              // M_POT: orbitals per group
+    int rowlen;           // shared-memory row length in elements
+};
+
+template <typename T>
+struct PassParams {
+    T f[2][32];           // taps per output parity (single-parity kinds: both equal)
+    int hl;               // left halo
+    int LT;               // lines per tile (power of two, 4..32)
+    int nseg;
+    Seg<T> seg[MAXSEG];
+};
+
+// Per-kind geometry: taps, parity offsets, left/right halo.
+struct KindGeom {
+    int nt, off0, off1, extra, hl, hr;
+};
+KindGeom kind_geom(int kind);
+
+// Fills p.f and p.hl for a kind and axis spacing (kinetic only).
+template <typename T>
+void fill_taps(PassParams<T>& p, int kind, double hgrid);
+
+// Launches one pass.  R (outputs per thread) must be 4 or 8.
+template <typename T>
+cudaError_t launch_pass(int kind, int mode, int R, const PassParams<T>& p,
+                        long long nblocks, size_t smem, cudaStream_t st);
+
+// Sets the dynamic shared-memory attribute of every pass kernel on the
+// current device (done lazily by launch_pass too; needed before capture).
+template <typename T>
+cudaError_t prepare_pass_kernels();
+
+// Kernel-launch counter behind wvl_kernel_launches().
+void count_launches(unsigned long long k);
+
+// ekin/epot finalisation and density reduction.
+cudaError_t launch_reduce_parts(const double* part, const double* minus, int tiles,
+                                int norb, double* out, cudaStream_t st);
+cudaError_t launch_rho_reduce(const double* parts, long long P, int ngroups,
+                              double* rho, cudaStream_t st);
+
+}  // namespace wvl
