@@ -38,14 +38,22 @@ PER_CELL = 64
 CFG = 2
 METRIC = "H_loc|psi> orbital-applications/s (FP64, batched uneven cells)"
 UNIT = "orbital-applications/s"
-WORKLOAD = {
-    "workload": "batched FP64 local Hamiltonian + density, 192 orbitals: 64 each on "
-                "periodic coarse 56^3, 48^3, 40^3 cells (fine 112^3, 96^3, 80^3), "
-                "8 components, Gaussian-sum V per cell, occ 2.0; autotuned, graph-captured",
-    "orbitals": 3 * PER_CELL,
-    "fine_points_per_step": sum(PER_CELL * 8 * a * b * c for a, b, c in SIZES),
-    "l2": "inputs larger than L2 (1.43 GB per orbital array), no flush",
-}
+
+
+def workload(per_cell):
+    gb = sum(per_cell * 8 * a * b * c for a, b, c in SIZES) * 8 / 1e9
+    return {
+        "workload": f"batched FP64 local Hamiltonian + density, {3 * per_cell} orbitals: "
+                    f"{per_cell} each on periodic coarse 56^3, 48^3, 40^3 cells (fine 112^3, "
+                    "96^3, 80^3), 8 components, Gaussian-sum V per cell, occ 2.0; "
+                    "autotuned, graph-captured",
+        "orbitals": 3 * per_cell,
+        "fine_points_per_step": sum(per_cell * 8 * a * b * c for a, b, c in SIZES),
+        "l2": f"inputs larger than L2 ({gb:.2f} GB per orbital array), no flush",
+    }
+
+
+WORKLOAD = workload(PER_CELL)
 # FP64-pipe operations per fine point of the chain (FMA = 1 op)
 KIN_OPS_PER_POINT_PER_PASS = 29
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of GB300 (2 flops per DFMA)
@@ -58,9 +66,9 @@ def dist_env():
     return rank, world, local
 
 
-def make_inputs(rank):
+def make_inputs(rank, per_cell=PER_CELL):
     from paper_0904_1543_gb300 import inputs
-    cell_of_orb = [c for c in range(3) for _ in range(PER_CELL)]
+    cell_of_orb = [c for c in range(3) for _ in range(per_cell)]
     first = rank * len(cell_of_orb)
     psi = np.concatenate([inputs.orbital(CFG, first + o, SIZES[c])
                           for o, c in enumerate(cell_of_orb)])
@@ -196,9 +204,10 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         if world > 1:
             dist.barrier()
 
-    cell_of_orb, psi_h, Vs_h, occ_h = make_inputs(rank)
+    cell_of_orb, psi_h, Vs_h, occ_h = make_inputs(rank, args.per_cell)
+    WL = workload(args.per_cell)
     cells = [W.Grid(s) for s in SIZES]
-    plan = W.Plan(cells, cell_of_orb, prec=W.WVL_F64, graph=True, autotune=True)
+    plan = W.Plan(cells, cell_of_orb, prec=W.WVL_F64, graph=True, autotune=not args.no_autotune)
     psi = torch.from_numpy(psi_h).to(dev)
     V = [torch.from_numpy(v).to(dev) for v in Vs_h]
     occ = torch.from_numpy(occ_h).to(dev)
@@ -206,7 +215,8 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     ek = torch.empty(len(cell_of_orb), dtype=torch.float64, device=dev)
     ep = torch.empty_like(ek)
     rho = [torch.zeros(c.fine, dtype=torch.float64, device=dev) for c in cells]
-    plan.autotune(psi, V, occ, hpsi=hp, rho=rho)
+    if not args.no_autotune:
+        plan.autotune(psi, V, occ, hpsi=hp, rho=rho)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -227,6 +237,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     barrier()
     torch.cuda.synchronize()
     l0 = W.kernel_launches()
+    print(f"[bench] kernels enqueued before the timed region: {l0}", file=sys.stderr, flush=True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -273,18 +284,20 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         for r, rp in zip(rho, rho_pin):
             rp.copy_(r, non_blocking=True)
 
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms_e2e = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0))
+    ms_e2e = float("nan")
+    if not args.no_e2e:
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e2e = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0))
 
     if world > 1:
         t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
@@ -297,7 +310,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
 
     # roofline of the dominant kernel (kinetic pass, 3 launches per step)
     kin_ms, kin_launches = prof["kinetic"]
-    pts = WORKLOAD["fine_points_per_step"]
+    pts = WL["fine_points_per_step"]
     flops_per_launch = 2.0 * KIN_OPS_PER_POINT_PER_PASS * pts
     kin_avg_s = kin_ms * 1e-3 / max(kin_launches * 3, 1)
     achieved = flops_per_launch / kin_avg_s / 1e12 if kin_launches else None
@@ -311,7 +324,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": WORKLOAD,
+        "data": "synthetic", "config": WL,
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -341,6 +354,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-cell", type=int, default=PER_CELL,
+                    help="orbitals per cell (64 = the benchmark workload; smaller for ncu)")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -132,7 +132,7 @@ def test_hpsi_local_f64(W, n, norb):
         close(host(hp[o]), hp_r[o], RTOL64, f"hpsi {n} orbital {o}")
         assert rel(float(ek[o]), ek_r[o]) < RTOL64, ("ekin", float(ek[o]), ek_r[o])
         assert rel(float(ep[o]), ep_r[o]) < RTOL64, ("epot", float(ep[o]), ep_r[o])
-    close(host(rho) - rho0, rho_r, RTOL64, "rho")
+    close(host(rho), rho0 + rho_r, RTOL64, "rho (accumulated onto 0.125)")
 
 
 def test_config0_full(W):
