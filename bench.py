@@ -328,6 +328,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
+        **({"e2e": None} if args.no_e2e else {}),
         "roofline": roofline,
         "clocks": clk,
         "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
