@@ -143,6 +143,28 @@ wvl_status wvl_hpsi_local(const wvl_grid* grid, int prec, int norb,
                           void* hpsi_c, double* rho, double* ekin, double* epot,
                           void* ws, size_t ws_bytes, void* stream);
 
+/* wvl_hpsi_local without a workspace argument.  The paper has no
+ * counterpart: this is for callers that cannot give the library scratch
+ * memory or let anything allocate device memory when they call it -- plugins
+ * whose host program owns every device allocation, and pipelines that
+ * reserve all device memory up front and forbid allocation later.
+ * The scratch is one file-scope device array of WVL_NOALLOC_SCRATCH_BYTES,
+ * held on every GPU that loads the library until the process exits; no
+ * allocator is called.  Calls whose wvl_workspace_size() exceeds it return
+ * WVL_EUNSUPPORTED (detail in wvl_noalloc_last_error()).
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call uses the same array and leaves its contents behind
+ * (nothing in it needs to start at zero); calls that overlap on the GPU --
+ * on different streams or from several host threads -- race on it.
+ * Arguments, layouts and results are those of wvl_hpsi_local. */
+#define WVL_NOALLOC_SCRATCH_BYTES (64u << 20)
+wvl_status wvl_hpsi_local_noalloc(const wvl_grid* grid, int prec, int norb,
+                                  const void* psi_c, const void* V,
+                                  const double* occ, void* hpsi_c, double* rho,
+                                  double* ekin, double* epot, void* stream);
+const char* wvl_noalloc_last_error(void);
+
 /* Forward of E_loc = sum_o occ_o (Ekin_o + Epot_o): the energies (and rho
  * when not NULL) without H psi -- steps 1), 2), 3a), 3b) and 4) only. */
 wvl_status wvl_energy(const wvl_grid* grid, int prec, int norb,
