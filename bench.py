@@ -198,6 +198,107 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _time_steps(torch, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def measure_variants(args, W, torch, dev):
+    """The FP32 batched form (256 orbitals, coarse 48^3) with its error
+    against the FP64 oracle and its speedup over the FP64 GPU form, and the
+    autograd form (512 orbitals, coarse 64^3, FP32 forward + backward)."""
+    import oracle.wavelet as O
+    from paper_0904_1543_gb300 import inputs
+    out = {}
+    # ---- FP32 batched, coarse 48^3 x 256 orbitals
+    n = (48, 48, 48)
+    g = W.Grid(n)
+    norb = 256
+    psi64 = inputs.orbitals_device(3, norb, n, dev)
+    V64 = torch.from_numpy(inputs.gaussian_potential(3, 0, n)).to(dev)
+    occ = torch.full((norb,), 2.0, dtype=torch.float64, device=dev)
+    psi32, V32 = psi64.float(), V64.float()
+    res = {}
+    for name, p, v, prec in (("f32", psi32, V32, W.WVL_F32), ("f64", psi64, V64, W.WVL_F64)):
+        plan = W.Plan([g], [0] * norb, prec=prec, graph=True, autotune=True)
+        hp = torch.empty_like(p)
+        ek = torch.empty(norb, dtype=torch.float64, device=dev)
+        ep = torch.empty_like(ek)
+        rho = [torch.zeros(g.fine, dtype=torch.float64, device=dev)]
+        plan.autotune(p, [v], occ, hpsi=hp, rho=rho)
+        ms = _time_steps(torch, lambda: plan.hpsi(p, [v], occ, hpsi=hp, rho=rho, ekin=ek,
+                                                  epot=ep), args.steps, 3)
+        rho[0].zero_()
+        plan.hpsi(p, [v], occ, hpsi=hp, rho=rho, ekin=ek, epot=ep)
+        torch.cuda.synchronize()
+        res[name] = (ms, hp, ek, ep, rho[0])
+        del plan
+    ms32, hp32, ek32, ep32, rho32 = res["f32"]
+    ms64, hp64, ek64, ep64, rho64 = res["f64"]
+    # oracle on two sampled orbitals (FP64 arithmetic on the FP32-rounded inputs)
+    Vh = V32.double().cpu().numpy()
+    err_h, err_e = 0.0, 0.0
+    for o in (0, norb - 1):
+        ph = psi32[o].double().cpu().numpy()
+        r = O.hpsi_local(ph, Vh, 2.0, n)
+        err_h = max(err_h, float(np.abs(hp32[o].double().cpu().numpy() - r["hpsi_c"]).max()
+                                 / np.abs(r["hpsi_c"]).max()))
+        err_e = max(err_e, abs(float(ek32[o]) - r["ekin"]) / abs(r["ekin"]),
+                    abs(float(ep32[o]) - r["epot"]) / abs(r["epot"]))
+    # density over all 256 orbitals against the FP64 GPU form (which matches
+    # the oracle to 1e-12 in the parity tests)
+    err_rho = float((rho32 - rho64).abs().max() / rho64.abs().max())
+    out["fp32_batched"] = {
+        "workload": "256 orbitals, periodic coarse 48^3 (fine 96^3), FP32 convolutions, "
+                    "compensated/FP64 reductions, one autotuned graph-captured plan",
+        "value": norb / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
+        "fp64_same_workload": {"value": norb / (ms64 * 1e-3), "ms_per_step": ms64},
+        "speedup_over_fp64": ms64 / ms32,
+        "rel_err_hpsi_vs_oracle": err_h, "rel_err_energies_vs_oracle": err_e,
+        "rel_err_rho_vs_fp64_gpu": err_rho,
+        "error_sample": "H psi and energies: orbitals 0 and 255 against the FP64 oracle; "
+                        "rho: all 256 orbitals against the FP64 GPU form",
+    }
+    del res, hp32, hp64, psi64, psi32
+    torch.cuda.empty_cache()
+    # ---- autograd, coarse 64^3 x 512 orbitals, FP32 forward + backward
+    n = (64, 64, 64)
+    g = W.Grid(n)
+    norb = 512
+    p = inputs.orbitals_device(4, norb, n, dev, torch.float32).requires_grad_(True)
+    v = torch.from_numpy(inputs.gaussian_potential(4, 0, n)).to(dev).float().requires_grad_(True)
+    occ = torch.full((norb,), 2.0, dtype=torch.float64, device=dev)
+
+    def fwd_bwd():
+        p.grad = None
+        v.grad = None
+        E = W.ELoc.apply(p, v, occ, g)
+        E.backward()
+
+    ms = _time_steps(torch, fwd_bwd, max(2, args.steps // 3), 2)
+    out["autograd_fp32"] = {
+        "workload": "E_loc(psi, V) forward + backward through ELoc, 512 orbitals, periodic "
+                    "coarse 64^3 (fine 128^3), FP32 convolutions; backward recomputes "
+                    "real-space psi and applies the adjoint chain",
+        "value": norb / (ms * 1e-3), "unit": "orbital forward+backward/s", "ms_per_step": ms,
+        "checked": "tests/test_gpu_autograd.py: FP64 central differences and oracle adjoint "
+                   "on 4 orbitals at coarse 16^3",
+    }
+    del p, v
+    torch.cuda.empty_cache()
+    return out
+
+
 def _run_ours(args, W, torch, dist, rank, world, local, dev):
 
     def barrier():
@@ -314,7 +415,10 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     flops_per_launch = 2.0 * KIN_OPS_PER_POINT_PER_PASS * pts
     kin_avg_s = kin_ms * 1e-3 / max(kin_launches * 3, 1)
     achieved = flops_per_launch / kin_avg_s / 1e12 if kin_launches else None
-    traffic = None
+    # DRAM bytes of one kinetic pass-1 launch from an ncu capture of the small
+    # profiling case (profiles/kinetic_pass_fp64_small36.md), scaled to this
+    # launch by the fine points processed; null for any other workload.
+    traffic = (1028.3e6 * pts / 33619968) if args.per_cell == PER_CELL else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                 "traffic": traffic, "kernel": "kinetic 1D pass (FP64 DFMA pipe)",
@@ -333,6 +437,8 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         "clocks": clk,
         "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
     }
+    if rank == 0 and world == 1 and not args.no_variants:
+        line["variants"] = measure_variants(args, W, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         off = offsets_of(cell_of_orb)
         done, secs = 0, 0.0
@@ -359,6 +465,8 @@ def main():
                     help="orbitals per cell (64 = the benchmark workload; smaller for ncu)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP32 and autograd forms reported beside the FP64 line")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -80,6 +80,22 @@ def gaussian_potential(cfg: int, cell: int, n, ngauss: int = 8) -> np.ndarray:
     return V
 
 
+def orbitals_device(cfg: int, norb: int, n, device, dtype=None):
+    """Large throughput-only batches drawn on the device: the same
+    distribution as orbitals() (uniform[-1, 1), unit norm per orbital) from
+    torch's seeded Philox generator, seeded with seed(cfg, 0).  Not the
+    SplitMix64 stream: used only where no oracle comparison needs the
+    whole batch (callers copy back the orbitals they check)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed(cfg, 0))
+    m = 8 * n[0] * n[1] * n[2]
+    x = torch.rand((norb, m), generator=gen, device=device, dtype=torch.float64)
+    x = 2.0 * x - 1.0
+    x /= torch.linalg.vector_norm(x, dim=1, keepdim=True)
+    return x if dtype is None else x.to(dtype)
+
+
 def random_field(cfg: int, stream: int, shape) -> np.ndarray:
     """Uniform[-1, 1) array of the given shape (per-pass sweeps)."""
     return uniform(seed(cfg, stream), int(np.prod(shape)), -1.0, 1.0).reshape(shape)

@@ -1,0 +1,115 @@
+"""GPU checks of the differentiable local energy E_loc(psi, V) = sum occ (Ekin + Epot)
+run through paper_0904_1543_gb300.ELoc (forward: energies only; backward:
+the adjoint chain recomputed from psi, dE/dpsi = 2 occ H psi, dE/dV = rho).
+
+E is quadratic in psi and linear in V, so FP64 central differences are exact
+up to rounding (about 1e-16 |E| / h ~ 1e-9 relative at h = 1e-5): the bound
+1e-6 leaves a wide margin.  Gradients against the oracle's adjoint: 1e-11.
+"""
+import numpy as np
+import pytest
+
+import oracle.wavelet as O
+from paper_0904_1543_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_0904_1543_gb300 as W
+    return W
+
+
+def _setup(n=(16, 16, 16), norb=4, cfg=4):
+    psi = inputs.orbitals(cfg, norb, n)
+    V = inputs.gaussian_potential(cfg, 0, n)
+    occ = np.array([2.0, 2.0, 1.0, 0.5])[:norb]
+    return psi, V, occ
+
+
+def test_eloc_gradients_match_oracle_adjoint(W):
+    import torch
+    n = (16, 16, 16)
+    g = W.Grid(n)
+    psi, V, occ = _setup(n)
+    tp = torch.from_numpy(psi).cuda().requires_grad_(True)
+    tV = torch.from_numpy(V).cuda().requires_grad_(True)
+    E = W.ELoc.apply(tp, tV, torch.from_numpy(occ).cuda(), g)
+    E.backward()
+    gpsi_r, gV_r = O.energy_gradients(psi, V, occ, n)
+    E_r = O.energy(psi, V, occ, n)
+    assert abs(float(E) - E_r) < 1e-12 * abs(E_r)
+    d = np.abs(tp.grad.cpu().numpy() - gpsi_r).max() / np.abs(gpsi_r).max()
+    assert d < 1e-11, d
+    d = np.abs(tV.grad.cpu().numpy() - gV_r).max() / np.abs(gV_r).max()
+    assert d < 1e-11, d
+
+
+def test_eloc_finite_differences(W):
+    """16 random directions of psi and V, 64 single coordinates of psi and
+    of V, h = 1e-5, FP64 forward on the GPU."""
+    import torch
+    n = (16, 16, 16)
+    g = W.Grid(n)
+    psi, V, occ = _setup(n)
+    tp = torch.from_numpy(psi).cuda().requires_grad_(True)
+    tV = torch.from_numpy(V).cuda().requires_grad_(True)
+    to = torch.from_numpy(occ).cuda()
+    E = W.ELoc.apply(tp, tV, to, g)
+    E.backward()
+    gp, gv = tp.grad.detach(), tV.grad.detach()
+    h = 1e-5
+
+    def energy(p, v):
+        with torch.no_grad():
+            return float(W.ELoc.apply(p, v, to, g))
+
+    rng = np.random.default_rng(4)
+    worst = 0.0
+    for k in range(16):
+        dp = torch.from_numpy(rng.standard_normal(psi.shape)).cuda()
+        dv = torch.from_numpy(rng.standard_normal(V.shape)).cuda()
+        fd = (energy(tp + h * dp, tV + h * dv) - energy(tp - h * dp, tV - h * dv)) / (2 * h)
+        an = float((gp * dp).sum() + (gv * dv).sum())
+        worst = max(worst, abs(fd - an) / abs(an))
+    for k in range(64):
+        i = int(rng.integers(psi.size))
+        dp = torch.zeros_like(tp).view(-1)
+        dp[i] = 1.0
+        dp = dp.view_as(tp)
+        fd = (energy(tp + h * dp, tV) - energy(tp - h * dp, tV)) / (2 * h)
+        an = float(gp.view(-1)[i])
+        worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * float(gp.abs().max())))
+        j = int(rng.integers(V.size))
+        dv = torch.zeros_like(tV).view(-1)
+        dv[j] = 1.0
+        dv = dv.view_as(tV)
+        fd = (energy(tp, tV + h * dv) - energy(tp, tV - h * dv)) / (2 * h)
+        an = float(gv.view(-1)[j])
+        worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * float(gv.abs().max())))
+    assert worst < 1e-6, worst
+
+
+def test_eloc_fp32_against_oracle(W):
+    """FP32 convolutions, FP64/compensated reductions: gradient errors stay
+    at single-precision level (bound 2e-5 normwise)."""
+    import torch
+    n = (10, 12, 8)
+    g = W.Grid(n)
+    psi, V, occ = _setup(n, cfg=5)
+    p32, V32 = psi.astype(np.float32), V.astype(np.float32)
+    tp = torch.from_numpy(p32).cuda().requires_grad_(True)
+    tV = torch.from_numpy(V32).cuda().requires_grad_(True)
+    E = W.ELoc.apply(tp, tV, torch.from_numpy(occ).cuda(), g)
+    E.backward()
+    gpsi_r, gV_r = O.energy_gradients(p32.astype(np.float64), V32.astype(np.float64), occ, n)
+    E_r = O.energy(p32.astype(np.float64), V32.astype(np.float64), occ, n)
+    assert abs(float(E) - E_r) < 1e-5 * abs(E_r)
+    d = np.abs(tp.grad.double().cpu().numpy() - gpsi_r).max() / np.abs(gpsi_r).max()
+    assert d < 2e-5, d
+    d = np.abs(tV.grad.double().cpu().numpy() - gV_r).max() / np.abs(gV_r).max()
+    assert d < 2e-5, d
