@@ -42,7 +42,7 @@ def test_eloc_gradients_match_oracle_adjoint(W):
     E.backward()
     gpsi_r, gV_r = O.energy_gradients(psi, V, occ, n)
     E_r = O.energy(psi, V, occ, n)
-    assert abs(float(E) - E_r) < 1e-12 * abs(E_r)
+    assert abs(float(E.detach()) - E_r) < 1e-12 * abs(E_r)
     d = np.abs(tp.grad.cpu().numpy() - gpsi_r).max() / np.abs(gpsi_r).max()
     assert d < 1e-11, d
     d = np.abs(tV.grad.cpu().numpy() - gV_r).max() / np.abs(gV_r).max()
@@ -69,29 +69,41 @@ def test_eloc_finite_differences(W):
             return float(W.ELoc.apply(p, v, to, g))
 
     rng = np.random.default_rng(4)
+    E0 = abs(energy(tp, tV))
+    # central differences of a quadratic are exact; what remains is the
+    # rounding of the two energies, at most a few ulps of |E| over 2h
+    floor = 8 * np.finfo(np.float64).eps * E0 / (2 * h)
     worst = 0.0
     for k in range(16):
         dp = torch.from_numpy(rng.standard_normal(psi.shape)).cuda()
         dv = torch.from_numpy(rng.standard_normal(V.shape)).cuda()
         fd = (energy(tp + h * dp, tV + h * dv) - energy(tp - h * dp, tV - h * dv)) / (2 * h)
         an = float((gp * dp).sum() + (gv * dv).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an) + floor, (k, fd, an)
         worst = max(worst, abs(fd - an) / abs(an))
+    assert worst < 1e-6, worst
     for k in range(64):
         i = int(rng.integers(psi.size))
+        j = int(rng.integers(V.size))
         dp = torch.zeros_like(tp).view(-1)
         dp[i] = 1.0
         dp = dp.view_as(tp)
-        fd = (energy(tp + h * dp, tV) - energy(tp - h * dp, tV)) / (2 * h)
-        an = float(gp.view(-1)[i])
-        worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * float(gp.abs().max())))
-        j = int(rng.integers(V.size))
         dv = torch.zeros_like(tV).view(-1)
         dv[j] = 1.0
         dv = dv.view_as(tV)
+        an_p, an_v = float(gp.view(-1)[i]), float(gv.view(-1)[j])
+        # h = 1e-5: exact up to the rounding floor
+        fd = (energy(tp + h * dp, tV) - energy(tp - h * dp, tV)) / (2 * h)
+        assert abs(fd - an_p) <= 1e-6 * abs(an_p) + floor, ("psi", i, fd, an_p)
         fd = (energy(tp, tV + h * dv) - energy(tp, tV - h * dv)) / (2 * h)
-        an = float(gv.view(-1)[j])
-        worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * float(gv.abs().max())))
-    assert worst < 1e-6, worst
+        assert abs(fd - an_v) <= 1e-6 * abs(an_v) + floor, ("V", j, fd, an_v)
+        # a larger step is just as exact (E is quadratic in psi, linear in V)
+        # and brings the rounding floor far below 1e-6 relative
+        H = 0.05
+        fd = (energy(tp + H * dp, tV) - energy(tp - H * dp, tV)) / (2 * H)
+        assert abs(fd - an_p) <= 1e-6 * abs(an_p) + floor * h / H, ("psi big", i)
+        fd = (energy(tp, tV + 1.0 * dv) - energy(tp, tV - 1.0 * dv)) / 2.0
+        assert abs(fd - an_v) <= 1e-6 * abs(an_v) + floor * h, ("V big", j)
 
 
 def test_eloc_fp32_against_oracle(W):
