@@ -308,7 +308,13 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     cell_of_orb, psi_h, Vs_h, occ_h = make_inputs(rank, args.per_cell)
     WL = workload(args.per_cell)
     cells = [W.Grid(s) for s in SIZES]
-    plan = W.Plan(cells, cell_of_orb, prec=W.WVL_F64, graph=True, autotune=not args.no_autotune)
+    f32 = args.prec == "f32"     # FP32 form of the same workload (profiling)
+    tdt = torch.float32 if f32 else torch.float64
+    if f32:
+        psi_h = psi_h.astype(np.float32)
+        Vs_h = [v.astype(np.float32) for v in Vs_h]
+    plan = W.Plan(cells, cell_of_orb, prec=W.WVL_F32 if f32 else W.WVL_F64, graph=True,
+                  autotune=not args.no_autotune)
     psi = torch.from_numpy(psi_h).to(dev)
     V = [torch.from_numpy(v).to(dev) for v in Vs_h]
     occ = torch.from_numpy(occ_h).to(dev)
@@ -364,12 +370,13 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     psi_pin = torch.from_numpy(psi_h).pin_memory()
     V_pin = [torch.from_numpy(v).pin_memory() for v in Vs_h]
     occ_pin = torch.from_numpy(occ_h).pin_memory()
-    hp_pin = torch.empty(psi_h.shape, dtype=torch.float64).pin_memory()
+    hp_pin = torch.empty(psi_h.shape, dtype=tdt).pin_memory()
     ek_pin = torch.empty(len(cell_of_orb), dtype=torch.float64).pin_memory()
     ep_pin = torch.empty_like(ek_pin)
     rho_pin = [torch.empty(c.fine, dtype=torch.float64).pin_memory() for c in cells]
-    h2d = psi_pin.numel() * 8 + sum(v.numel() * 8 for v in V_pin) + occ_pin.numel() * 8
-    d2h = hp_pin.numel() * 8 + 2 * ek_pin.numel() * 8 + sum(r.numel() * 8 for r in rho_pin)
+    es = psi_pin.element_size()
+    h2d = psi_pin.numel() * es + sum(v.numel() * es for v in V_pin) + occ_pin.numel() * 8
+    d2h = hp_pin.numel() * es + 2 * ek_pin.numel() * 8 + sum(r.numel() * 8 for r in rho_pin)
 
     def e2e_step():
         psi.copy_(psi_pin, non_blocking=True)
@@ -418,7 +425,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     # DRAM bytes of one kinetic pass-1 launch from an ncu capture of the small
     # profiling case (profiles/kinetic_pass_fp64_small36.md), scaled to this
     # launch by the fine points processed; null for any other workload.
-    traffic = (1028.3e6 * pts / 33619968) if args.per_cell == PER_CELL else None
+    traffic = (1028.3e6 * pts / 33619968) if (args.per_cell == PER_CELL and not f32) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                 "traffic": traffic, "kernel": "kinetic 1D pass (FP64 DFMA pipe)",
@@ -427,7 +434,8 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if f32 else "f64",
         "data": "synthetic", "config": WL,
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -437,7 +445,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         "clocks": clk,
         "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
     }
-    if rank == 0 and world == 1 and not args.no_variants:
+    if rank == 0 and world == 1 and not args.no_variants and not f32:
         line["variants"] = measure_variants(args, W, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         off = offsets_of(cell_of_orb)
@@ -465,6 +473,8 @@ def main():
                     help="orbitals per cell (64 = the benchmark workload; smaller for ncu)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--prec", choices=["f64", "f32"], default="f64",
+                    help="f32 runs the FP32 form of the same workload (profiling)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32 and autograd forms reported beside the FP64 line")
     args = ap.parse_args()

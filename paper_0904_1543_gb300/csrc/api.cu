@@ -149,7 +149,8 @@ static bool tune_valid(const PassCall<T>& c, const Tune& t) {
     for (const auto& d : c.segs) {
         int n, N;
         pass_dims(d.Nf, c.pass, n, N);
-        if ((size_t)t.LT * rowlen_of(n, t.R, g) * sizeof(T) > 200 * 1024) return false;
+        // two staging buffers must fit
+        if (2 * ((size_t)t.LT * rowlen_of(n, t.R, g) + 2) * sizeof(T) > 200 * 1024) return false;
         if (c.mode == M_POT) {
             const int nslots = (NTHREADS / 32) * (32 / t.LT);
             const int cpt = POT_OUT / t.R;
@@ -240,10 +241,15 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             }
             s.blk0 = blk;
             blk += units * s.tiles;
-            smem = std::max(smem, (size_t)tn.LT * s.rowlen * sizeof(T));
+            smem = std::max(smem, (size_t)tn.LT * s.rowlen);
             p.seg[k] = s;
         }
         p.nseg = k;
+        p.nunits = blk;
+        // two staging buffers, each rounded to 16 bytes
+        const size_t per16 = 16 / sizeof(T);
+        p.bufelems = (int)((smem + per16 - 1) / per16 * per16);
+        smem = 2 * (size_t)p.bufelems * sizeof(T);
         cudaError_t e = launch_pass<T>(c.kind, c.mode, tn.R, p, blk, smem, st);
         if (e != cudaSuccess) return cuda_fail(e, "pass launch");
     }

@@ -24,14 +24,25 @@ static cudaError_t ensure_attr() {
     return cudaSuccess;
 }
 
+// Persistent launch: as many CTAs as fit on the device at once (never more
+// than there are work units); each walks its units with a stride of the grid.
 template <typename T, int KIND, int MODE, int R>
-static cudaError_t launch_one(const PassParams<T>& p, long long nblocks, size_t smem,
+static cudaError_t launch_one(const PassParams<T>& p, long long nunits, size_t smem,
                               cudaStream_t st) {
     cudaError_t err = ensure_attr<T, KIND, MODE, R>();
     if (err != cudaSuccess) return err;
-    if (nblocks <= 0) return cudaSuccess;
-    if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    pass_kernel<T, KIND, MODE, R><<<dim3((unsigned)nblocks), dim3(NTHREADS), smem, st>>>(p);
+    if (nunits <= 0) return cudaSuccess;
+    int dev = 0, nsm = 0, occ = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return err;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel<T, KIND, MODE, R>,
+                                                        NTHREADS, smem);
+    if (err != cudaSuccess) return err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)occ * nsm;
+    if (grid > nunits) grid = nunits;
+    pass_kernel<T, KIND, MODE, R><<<dim3((unsigned)grid), dim3(NTHREADS), smem, st>>>(p);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -2,20 +2,27 @@
 // sm_103a, templated on the element type, the operator, the epilogue and the
 // number of consecutive outputs per thread.
 //
-// A CTA owns a tile of LT consecutive lines of one orbital and keeps the
-// whole periodic lines in shared memory, extended by the left/right halos
-// (wrapped while staging, which is how the periodic boundary is applied).  A
-// thread computes R consecutive outputs of one line from a register window of
-// R + NT - 1 (+1 for the two-phase wavelet filters) shared-memory values; taps
-// are kernel parameters (constant bank) and indices are compile-time, so the
-// inner loop is loads and FMAs only.  Outputs go to F[I][a] with the line index
-// fastest, so each warp's stores are coalesced (LT contiguous elements).
+// A job is a tile of LT consecutive lines of one orbital.  The CTA keeps the
+// whole periodic lines in shared memory, extended by the left/right halos,
+// which are copied from their wrapped positions -- this is how the periodic
+// boundary is applied.  A thread computes R consecutive outputs of one line
+// from a register window of R + NT - 1 (+1 for the two-phase wavelet filters)
+// shared-memory values; taps are kernel parameters (constant bank) and the
+// tap indices are compile-time, so the inner loop is loads and FMAs only.
+// Outputs go to F[I][a] with the line index fastest, so each warp's stores
+// are coalesced (LT contiguous elements).
+//
+// The kernel is persistent and double-buffered: while it computes job k from
+// one staging buffer, the asynchronous copies (cp.async) of job k+1 fill the
+// other, so the arithmetic pipe does not wait for a staging phase.
 #pragma once
 #include <cuda_runtime.h>
 
 #include "wvl_internal.h"
 
 namespace wvl {
+
+constexpr int NWARPS = NTHREADS / 32;
 
 template <int KIND> struct KT;
 template <> struct KT<K_MF>  { static constexpr int NT = 16, OFF0 = 0, OFF1 = 0, EXTRA = 0; };
@@ -59,11 +66,24 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     double t = 0.0;
     if (threadIdx.x == 0) {
         #pragma unroll
-        for (int w = 0; w < NTHREADS / 32; ++w) t += red[w];
+        for (int w = 0; w < NWARPS; ++w) t += red[w];
     }
     __syncthreads();
     return t;
 }
+
+// ------------------------------------------------------ asynchronous copies
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem_dst, const T* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // R outputs of one line from the shared-memory row (srow[j] <-> position
 // i0 - HL + j); acc must hold the initial values.
@@ -83,99 +103,161 @@ __device__ __forceinline__ void conv_chunk(const T* __restrict__ srow,
     }
 }
 
+// ------------------------------------------------------------------- jobs
+struct Job {
+    long long unit;   // global work unit
+    int si;           // segment
+    int tile;
+    int orb;          // orbital within the segment
+    int oe;           // one past the last orbital of the unit
+    bool valid;
+};
+
+template <typename T, int MODE>
+__device__ __forceinline__ Job make_job(const PassParams<T>& p, long long u) {
+    Job J;
+    J.unit = u;
+    J.valid = u < p.nunits;
+    if (!J.valid) return J;
+    int si = 0;
+    #pragma unroll 1
+    while (si + 1 < p.nseg && u >= p.seg[si + 1].blk0) ++si;
+    const Seg<T>& S = p.seg[si];
+    const long long loc = u - S.blk0;
+    J.si = si;
+    J.tile = (int)(loc % S.tiles);
+    const int grp = (int)(loc / S.tiles);
+    if (MODE == M_POT) {
+        J.orb = grp * S.opg;
+        J.oe = min(S.norb, J.orb + S.opg);
+    } else {
+        J.orb = grp;
+        J.oe = grp + 1;
+    }
+    return J;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ Job next_job(const PassParams<T>& p, const Job& J) {
+    if (J.orb + 1 < J.oe) {
+        Job K = J;
+        K.orb += 1;
+        return K;
+    }
+    return make_job<T, MODE>(p, J.unit + gridDim.x);
+}
+
+// Issue the copies of job J's lines (and wrapped halos) into buf.
+template <typename T, int MODE>
+__device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* buf) {
+    const Seg<T>& S = p.seg[J.si];
+    const int n = S.n, rowlen = S.rowlen, hl = p.hl, LT = p.LT;
+    const int a0 = J.tile * LT;
+    const int lt = min(LT, S.N - a0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long P = S.P;
+    #pragma unroll 1
+    for (int r = warp; r < LT; r += NWARPS) {
+        T* row = buf + r * rowlen;
+        if (r >= lt) {
+            for (int j = lane; j < rowlen; j += 32) row[j] = T(0);
+            continue;
+        }
+        const int a = a0 + r;
+        // source position of row slot j is x = (j - hl) mod n
+        int x = lane - hl;
+        while (x < 0) x += n;
+        while (x >= n) x -= n;
+        if (MODE == M_UNCOMP) {
+            // line a = (x3, x2) of the interleaved coarse array; element x1 of
+            // it is c^mu[i3][i2][i1], mu = a1 + 2 a2 + 4 a3
+            const int x3 = a / S.N2, x2 = a - x3 * S.N2;
+            const int mu23 = 2 * (x2 & 1) + 4 * (x3 & 1);
+            const T* cc = S.in + (long long)J.orb * P;
+            const T* cf = cc + (P >> 3);
+            const long long cb = ((long long)(x3 >> 1) * S.n2 + (x2 >> 1)) * S.n1;
+            #pragma unroll 1
+            for (int j = lane; j < rowlen; j += 32) {
+                const int mu = mu23 + (x & 1);
+                const long long ci = cb + (x >> 1);
+                cp_async(row + j, (mu == 0) ? cc + ci : cf + ci * 7 + mu - 1);
+                x += 32;
+                while (x >= n) x -= n;
+            }
+        } else {
+            const T* src = S.in + (long long)J.orb * P + (long long)a * n;
+            #pragma unroll 1
+            for (int j = lane; j < rowlen; j += 32) {
+                cp_async(row + j, src + x);
+                x += 32;
+                while (x >= n) x -= n;
+            }
+        }
+    }
+}
+
 template <typename T, int KIND, int MODE, int R>
 __global__ void __launch_bounds__(NTHREADS)
 pass_kernel(const __grid_constant__ PassParams<T> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tile = reinterpret_cast<T*>(smem_raw);
-    __shared__ double red[NTHREADS / 32];
+    T* const bufs = reinterpret_cast<T*>(smem_raw);
+    __shared__ double red[NWARPS];
 
-    // segment of this block
-    const long long b = blockIdx.x;
-    int si = 0;
-    #pragma unroll 1
-    while (si + 1 < p.nseg && b >= p.seg[si + 1].blk0) ++si;
-    const Seg<T>& S = p.seg[si];
-    const long long u = b - S.blk0;
-    const int tileidx = (int)(u % S.tiles);
-    const int unit = (int)(u / S.tiles);
-    int ob, oe;
-    if (MODE == M_POT) {
-        ob = unit * S.opg;
-        oe = min(S.norb, ob + S.opg);
-    } else {
-        ob = unit;
-        oe = unit + 1;
-    }
-
-    const int LT = p.LT, n = S.n, N = S.N, hl = p.hl, rowlen = S.rowlen;
-    const int a0 = tileidx * LT;
-    const int lt = min(LT, N - a0);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int LT = p.LT, hl = p.hl;
     const int spw = 32 / LT;
     const int line = lane & (LT - 1);
     const int slot = warp * spw + lane / LT;
-    const int nslots = (NTHREADS / 32) * spw;
-    const int nchunks = (n + R - 1) / R;
-    const long long P = S.P;
-    const bool line_ok = line < lt;
-    const T* srow_line = tile + line * rowlen;
-
+    const int nslots = NWARPS * spw;
+    constexpr bool KM = (MODE == M_KMID || MODE == M_KLAST);
     constexpr int CPT = (MODE == M_POT) ? POT_OUT / R : 1;
-    Acc<T> racc[CPT][R];   // M_POT: density per owned output, kept across orbitals
+
+    Job cur = make_job<T, MODE>(p, blockIdx.x);
+    if (!cur.valid) return;
+    stage<T, MODE>(p, cur, bufs);
+    cp_commit();
+
+    Acc<T> racc[CPT][R];   // M_POT: density per owned output, across a unit's orbitals
+    int b = 0;
 
     #pragma unroll 1
-    for (int orb = ob; orb < oe; ++orb) {
-        // ---------------- stage the lines (with periodic halos) in smem
-        #pragma unroll 1
-        for (int r = warp; r < LT; r += NTHREADS / 32) {
-            T* row = tile + r * rowlen + hl;
-            if (r < lt) {
-                const int a = a0 + r;
-                if (MODE == M_UNCOMP) {
-                    // line a = (x3, x2) of the interleaved coarse array; element
-                    // x1 of it is c^mu[i3][i2][i1], mu = a1 + 2 a2 + 4 a3
-                    const int x3 = a / S.N2, x2 = a - x3 * S.N2;
-                    const int i3 = x3 >> 1, i2 = x2 >> 1;
-                    const int mu23 = 2 * (x2 & 1) + 4 * (x3 & 1);
-                    const long long m = P >> 3;
-                    const T* cc = S.in + (long long)orb * P;
-                    const T* cf = cc + m;
-                    const long long cb = ((long long)i3 * S.n2 + i2) * S.n1;
-                    #pragma unroll 2
-                    for (int i = lane; i < n; i += 32) {
-                        const int mu = mu23 + (i & 1);
-                        const long long ci = cb + (i >> 1);
-                        row[i] = (mu == 0) ? cc[ci] : cf[ci * 7 + mu - 1];
-                    }
-                } else {
-                    const T* src = S.in + (long long)orb * P + (long long)a * n;
-                    #pragma unroll 4
-                    for (int i = lane; i < n; i += 32) row[i] = src[i];
-                }
-            } else {
-                for (int i = lane; i < n; i += 32) row[i] = T(0);
-            }
-        }
-        __syncthreads();
-        #pragma unroll 1
-        for (int r = warp; r < LT; r += NTHREADS / 32) {
-            T* row = tile + r * rowlen;
-            for (int j = lane; j < rowlen; j += 32) {
-                if (j < hl || j >= hl + n) {
-                    int x = (j - hl) % n;
-                    if (x < 0) x += n;
-                    row[j] = row[hl + x];
-                }
-            }
+    while (true) {
+        const Job nxt = next_job<T, MODE>(p, cur);
+        if (nxt.valid) {
+            stage<T, MODE>(p, nxt, bufs + (b ^ 1) * p.bufelems);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
         }
         __syncthreads();
 
-        // ---------------- convolve, epilogue
+        // ---------------------------------------------- compute job cur
+        const Seg<T>& S = p.seg[cur.si];
+        const int n = S.n, N = S.N, rowlen = S.rowlen;
+        const int a0 = cur.tile * LT;
+        const int lt = min(LT, N - a0);
+        const bool line_ok = line < lt;
+        const int nchunks = (n + R - 1) / R;
+        const long long P = S.P;
+        const int orb = cur.orb;
+        const long long obase = (long long)orb * P;
+        const T* srow_line = bufs + b * p.bufelems + line * rowlen;
         Acc<T> e;   // energy partial of this orbital
         double occ = 0.0;
         if (MODE == M_POT) occ = S.occ ? S.occ[orb] : 1.0;
-        const long long obase = (long long)orb * P;
+
+        // K_{p-1} of the thread's next chunk, fetched one chunk ahead
+        T kv[R];
+        #pragma unroll
+        for (int r = 0; r < R; ++r) kv[r] = T(0);
+        const T* kline = nullptr;
+        if (KM && S.in2 != nullptr && line_ok) {
+            kline = S.in2 + obase + (long long)(a0 + line) * n;
+            #pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (slot * R + r < n) kv[r] = kline[slot * R + r];
+        }
 
         // M_POT: CPT * nslots >= nchunks (launcher guarantees), so the outer
         // loop runs once and racc[cc] always maps to the same outputs.
@@ -188,14 +270,12 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                 const int i0 = c * R;
                 T acc[R];
                 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] = T(0);
-                if (MODE == M_KMID || MODE == M_KLAST) {
-                    if (S.in2 != nullptr && line_ok) {
-                        const T* kp = S.in2 + obase + (long long)(a0 + line) * n + i0;
-                        #pragma unroll
-                        for (int r = 0; r < R; ++r)
-                            if (i0 + r < n) acc[r] = kp[r];
-                    }
+                for (int r = 0; r < R; ++r) acc[r] = KM ? kv[r] : T(0);
+                if (KM && kline != nullptr) {
+                    const int i1 = (c + nslots) * R;
+                    #pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (i1 + r < n) kv[r] = kline[i1 + r];
                 }
                 conv_chunk<T, KIND, R>(srow_line + i0, p, acc);
                 if (!line_ok) continue;
@@ -238,26 +318,37 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
 
         if ((MODE == M_POT && S.aux) || MODE == M_KLAST) {
             const double t = block_sum(e.get(), red);
-            if (threadIdx.x == 0) S.part[(long long)orb * S.tiles + tileidx] = t;
+            if (threadIdx.x == 0) S.part[(long long)orb * S.tiles + cur.tile] = t;
         }
-        __syncthreads();   // smem reused by the next orbital
-    }
 
-    if (MODE == M_POT && S.rho != nullptr && line_ok) {
-        const int grp = unit;
-        #pragma unroll
-        for (int cc = 0; cc < CPT; ++cc) {
-            const int c = slot + cc * nslots;
-            if (c >= nchunks) continue;
-            #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int I = c * R + r;
-                if (I >= n) continue;
-                const long long oidx = (long long)I * N + a0 + line;
-                if (S.rho_gstride == 0) S.rho[oidx] += racc[cc][r].get();
-                else S.rho[grp * S.rho_gstride + oidx] = racc[cc][r].get();
+        // M_POT: the unit ends -> flush its density
+        if (MODE == M_POT && (!nxt.valid || nxt.unit != cur.unit)) {
+            if (S.rho != nullptr && line_ok) {
+                const long long grp = (cur.unit - S.blk0) / S.tiles;
+                #pragma unroll
+                for (int cc = 0; cc < CPT; ++cc) {
+                    const int c = slot + cc * nslots;
+                    #pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int I = c * R + r;
+                        if (c < nchunks && I < n) {
+                            const long long oidx = (long long)I * N + a0 + line;
+                            if (S.rho_gstride == 0) S.rho[oidx] += racc[cc][r].get();
+                            else S.rho[grp * S.rho_gstride + oidx] = racc[cc][r].get();
+                        }
+                    }
+                }
             }
+            #pragma unroll
+            for (int cc = 0; cc < CPT; ++cc)
+                #pragma unroll
+                for (int r = 0; r < R; ++r) racc[cc][r].reset();
         }
+
+        __syncthreads();   // buffer b is refilled by the next iteration's copies
+        if (!nxt.valid) break;
+        cur = nxt;
+        b ^= 1;
     }
 }
 

@@ -54,7 +54,7 @@ struct Seg {
     const double* occ;    // M_POT: occupations of the segment's orbitals
     long long P;          // elements per orbital
     long long rho_gstride;// M_POT: 0 -> rho += (direct), else group g writes rho[g*stride]
-    long long blk0;       // first block index of the segment in the launch
+    long long blk0;       // first work unit of the segment in the launch
     int n, N;             // line length and line count of this pass
     int N1, N2;           // fine extents (index decoding)
     int n1, n2;           // coarse extents (compressed layout)
@@ -64,9 +64,15 @@ struct Seg {
     int rowlen;           // shared-memory row length in elements
 };
 
+// A work unit is one (orbital, tile) -- or, for M_POT, one (orbital group,
+// tile) whose orbitals the CTA walks in order.  The kernel is persistent:
+// CTA b takes units b, b + gridDim.x, ... and stages the next job in the
+// second shared-memory buffer while it computes the current one.
 template <typename T>
 struct PassParams {
     T f[2][32];           // taps per output parity (single-parity kinds: both equal)
+    long long nunits;     // work units over all segments
+    int bufelems;         // elements of one staging buffer (two are allocated)
     int hl;               // left halo
     int LT;               // lines per tile (power of two, 4..32)
     int nseg;
