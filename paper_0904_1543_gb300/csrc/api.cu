@@ -106,7 +106,12 @@ static int num_sms() {
 struct Tune {
     int R = 8;
     int LT = 32;
+    bool persist = false;   // persistent double-buffered grid vs one CTA per job
 };
+
+// one staging buffer per CTA unless it prefetches (persistent grid, or the
+// orbital walk of the potential pass)
+static int nbuf(int mode, const Tune& t) { return (t.persist || mode == M_POT) ? 2 : 1; }
 
 enum Op { OP_HPSI, OP_ENERGY, OP_DENSITY, OP_SYN, OP_ANA, OP_MF, OP_MFT, OP_KIN };
 enum Stage { ST_SYN = 0, ST_MF = 1, ST_MFT = 2, ST_KIN = 3, ST_ANA = 4, ST_RED = 5 };
@@ -149,8 +154,9 @@ static bool tune_valid(const PassCall<T>& c, const Tune& t) {
     for (const auto& d : c.segs) {
         int n, N;
         pass_dims(d.Nf, c.pass, n, N);
-        // two staging buffers must fit
-        if (2 * ((size_t)t.LT * rowlen_of(n, t.R, g) + 2) * sizeof(T) > 200 * 1024) return false;
+        // the staging buffers must fit
+        if (nbuf(c.mode, t) * ((size_t)t.LT * rowlen_of(n, t.R, g) + 2) * sizeof(T) > 200 * 1024)
+            return false;
         if (c.mode == M_POT) {
             const int nslots = (NTHREADS / 32) * (32 / t.LT);
             const int cpt = POT_OUT / t.R;
@@ -176,6 +182,9 @@ template <typename T>
 static Tune default_tune(const PassCall<T>& c) {
     const long long want = 2LL * num_sms();
     const int lts[4] = {32, 16, 8, 4};
+    // FP64 passes are bound by the FP64 pipe and want occupancy (one CTA per
+    // job); FP32 passes want the prefetch of the persistent grid
+    const bool persist = sizeof(T) == 4;
     for (int R : {8, 4}) {
         Tune best;
         bool have = false;
@@ -183,6 +192,7 @@ static Tune default_tune(const PassCall<T>& c) {
             Tune t;
             t.R = R;
             t.LT = lt;
+            t.persist = persist;
             if (!tune_valid(c, t)) continue;
             best = t;
             have = true;
@@ -249,8 +259,8 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
         // two staging buffers, each rounded to 16 bytes
         const size_t per16 = 16 / sizeof(T);
         p.bufelems = (int)((smem + per16 - 1) / per16 * per16);
-        smem = 2 * (size_t)p.bufelems * sizeof(T);
-        cudaError_t e = launch_pass<T>(c.kind, c.mode, tn.R, p, blk, smem, st);
+        smem = nbuf(c.mode, tn) * (size_t)p.bufelems * sizeof(T);
+        cudaError_t e = launch_pass<T>(c.kind, c.mode, tn.R, p, blk, smem, st, tn.persist);
         if (e != cudaSuccess) return cuda_fail(e, "pass launch");
     }
     return WVL_OK;
@@ -1028,10 +1038,12 @@ static wvl_status plan_tune(wvl_plan* plan, const void* psi, const void* const* 
         float bt = 1e30f;
         Tune bv = default_tune(c);
         for (int R : {4, 8})
-            for (int lt : {32, 16, 8, 4}) {
+            for (int lt : {32, 16, 8, 4})
+            for (int ps = 0; ps < 2; ++ps) {
                 Tune t;
                 t.R = R;
                 t.LT = lt;
+                t.persist = ps != 0;
                 if (!tune_valid(c, t)) continue;
                 float tot = 0.f;
                 bool ok = true;
@@ -1089,8 +1101,9 @@ wvl_status wvl_plan_describe(const wvl_plan* plan, char* buf, size_t len) {
     std::string s = plan->tuned ? "autotuned\n" : "defaults\n";
     for (const auto& kv : plan->tune) {
         char line[128];
-        snprintf(line, sizeof line, "%s mode %d pass %d: R=%d LT=%d\n", kn[kv.first / 100],
-                 (kv.first / 10) % 10, kv.first % 10, kv.second.R, kv.second.LT);
+        snprintf(line, sizeof line, "%s mode %d pass %d: R=%d LT=%d %s\n", kn[kv.first / 100],
+                 (kv.first / 10) % 10, kv.first % 10, kv.second.R, kv.second.LT,
+                 kv.second.persist ? "persistent" : "one CTA per job");
         s += line;
     }
     std::strncpy(buf, s.c_str(), len - 1);

@@ -28,7 +28,7 @@ static cudaError_t ensure_attr() {
 // than there are work units); each walks its units with a stride of the grid.
 template <typename T, int KIND, int MODE, int R>
 static cudaError_t launch_one(const PassParams<T>& p, long long nunits, size_t smem,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool persistent) {
     cudaError_t err = ensure_attr<T, KIND, MODE, R>();
     if (err != cudaSuccess) return err;
     if (nunits <= 0) return cudaSuccess;
@@ -40,8 +40,9 @@ static cudaError_t launch_one(const PassParams<T>& p, long long nunits, size_t s
                                                         NTHREADS, smem);
     if (err != cudaSuccess) return err;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    long long grid = (long long)occ * nsm;
+    long long grid = persistent ? (long long)occ * nsm : nunits;
     if (grid > nunits) grid = nunits;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     pass_kernel<T, KIND, MODE, R><<<dim3((unsigned)grid), dim3(NTHREADS), smem, st>>>(p);
     count_launches(1);
     return cudaGetLastError();
@@ -63,26 +64,26 @@ static cudaError_t prepare_r() {
 
 template <typename T, int R>
 static cudaError_t launch_r(int kind, int mode, const PassParams<T>& p, long long nb,
-                            size_t smem, cudaStream_t st) {
+                            size_t smem, cudaStream_t st, bool ps) {
     switch (kind) {
     case K_SYN:
-        if (mode == M_UNCOMP) return launch_one<T, K_SYN, M_UNCOMP, R>(p, nb, smem, st);
-        if (mode == M_PLAIN) return launch_one<T, K_SYN, M_PLAIN, R>(p, nb, smem, st);
+        if (mode == M_UNCOMP) return launch_one<T, K_SYN, M_UNCOMP, R>(p, nb, smem, st, ps);
+        if (mode == M_PLAIN) return launch_one<T, K_SYN, M_PLAIN, R>(p, nb, smem, st, ps);
         break;
     case K_ANA:
-        if (mode == M_COMP) return launch_one<T, K_ANA, M_COMP, R>(p, nb, smem, st);
-        if (mode == M_PLAIN) return launch_one<T, K_ANA, M_PLAIN, R>(p, nb, smem, st);
+        if (mode == M_COMP) return launch_one<T, K_ANA, M_COMP, R>(p, nb, smem, st, ps);
+        if (mode == M_PLAIN) return launch_one<T, K_ANA, M_PLAIN, R>(p, nb, smem, st, ps);
         break;
     case K_MF:
-        if (mode == M_POT) return launch_one<T, K_MF, M_POT, R>(p, nb, smem, st);
-        if (mode == M_PLAIN) return launch_one<T, K_MF, M_PLAIN, R>(p, nb, smem, st);
+        if (mode == M_POT) return launch_one<T, K_MF, M_POT, R>(p, nb, smem, st, ps);
+        if (mode == M_PLAIN) return launch_one<T, K_MF, M_PLAIN, R>(p, nb, smem, st, ps);
         break;
     case K_MFT:
-        if (mode == M_PLAIN) return launch_one<T, K_MFT, M_PLAIN, R>(p, nb, smem, st);
+        if (mode == M_PLAIN) return launch_one<T, K_MFT, M_PLAIN, R>(p, nb, smem, st, ps);
         break;
     case K_KIN:
-        if (mode == M_KMID) return launch_one<T, K_KIN, M_KMID, R>(p, nb, smem, st);
-        if (mode == M_KLAST) return launch_one<T, K_KIN, M_KLAST, R>(p, nb, smem, st);
+        if (mode == M_KMID) return launch_one<T, K_KIN, M_KMID, R>(p, nb, smem, st, ps);
+        if (mode == M_KLAST) return launch_one<T, K_KIN, M_KLAST, R>(p, nb, smem, st, ps);
         break;
     }
     return cudaErrorInvalidValue;
@@ -91,9 +92,10 @@ static cudaError_t launch_r(int kind, int mode, const PassParams<T>& p, long lon
 #define WVL_INSTANTIATE_LAUNCH(T)                                                    \
     template <>                                                                      \
     cudaError_t launch_pass<T>(int kind, int mode, int R, const PassParams<T>& p,    \
-                               long long nblocks, size_t smem, cudaStream_t st) {    \
-        if (R == 4) return launch_r<T, 4>(kind, mode, p, nblocks, smem, st);         \
-        if (R == 8) return launch_r<T, 8>(kind, mode, p, nblocks, smem, st);         \
+                               long long nblocks, size_t smem, cudaStream_t st,      \
+                               bool ps) {                                            \
+        if (R == 4) return launch_r<T, 4>(kind, mode, p, nblocks, smem, st, ps);     \
+        if (R == 8) return launch_r<T, 8>(kind, mode, p, nblocks, smem, st, ps);     \
         return cudaErrorInvalidValue;                                                \
     }                                                                                \
     template <>                                                                      \

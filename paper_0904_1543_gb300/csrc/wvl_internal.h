@@ -92,7 +92,7 @@ void fill_taps(PassParams<T>& p, int kind, double hgrid);
 // Launches one pass.  R (outputs per thread) must be 4 or 8.
 template <typename T>
 cudaError_t launch_pass(int kind, int mode, int R, const PassParams<T>& p,
-                        long long nblocks, size_t smem, cudaStream_t st);
+                        long long nunits, size_t smem, cudaStream_t st, bool persistent);
 
 // Sets the dynamic shared-memory attribute of every pass kernel on the
 // current device (done lazily by launch_pass too; needed before capture).
