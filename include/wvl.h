@@ -172,6 +172,23 @@ wvl_status wvl_energy(const wvl_grid* grid, int prec, int norb,
                       double* rho, double* ekin, double* epot,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* Preconditioning step (paper Eq. precon, Sec. "Kinetic convolution" with
+ * K_0 = -eps s): for each orbital o, ncg iterations of the preconditioned
+ * conjugate gradient for
+ *     A x = g,   A = S^T (-1/2 Lap - eps_o) S   (S = synthesis, orthogonal)
+ * on compressed coefficients, from x_0 = 0, with the diagonal of A (one value
+ * per component mu, by translation invariance) as preconditioner.
+ * g, x: device [norb][8 n1 n2 n3] (must not alias); eps: device double[norb],
+ * each eps_o < 0 so that A is positive definite; rr (nullable, device
+ * double[norb]) receives the final squared residual |g - A x|^2.
+ * Workspace: wvl_precondition_workspace_size().  All scalars of the
+ * iteration stay on the device: nothing synchronises with the host. */
+wvl_status wvl_precondition_workspace_size(const wvl_grid* grid, int prec, int norb,
+                                           size_t* bytes);
+wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void* g,
+                            const double* eps, int ncg, void* x, double* rr,
+                            void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched plans: many orbitals on cells of different sizes in one enqueue
  * (the paper's orbital distribution, Sec. "Parallel distribution", inside

@@ -399,3 +399,32 @@ class ELoc(torch.autograd.Function):
         if ctx.needs_input_grad[1]:
             gV = (rho * g).to(V.dtype)
         return gpsi, gV, None, None
+
+
+def precondition(g, eps, grid: Grid, ncg=5, x=None, want_residual=True):
+    """ncg iterations of preconditioned CG for (S^T (-1/2 Lap - eps_o) S) x = g
+    per orbital (the preconditioning step).  g: (norb, 8 n1 n2 n3); eps:
+    float64 (norb,) on the device, each < 0.  Returns (x, |g - A x|^2)."""
+    norb = _norb(g, grid.ncoef)
+    x = torch.empty_like(g) if x is None else x
+    rr = torch.empty(norb, dtype=torch.float64, device=g.device) if want_residual else None
+    _dev(g, "g"), _dev(eps, "eps"), _dev(x, "x")
+    L = lib()
+    if not getattr(L, "_pc_declared", False):
+        Gp = ctypes.POINTER(_Grid)
+        L.wvl_precondition_workspace_size.restype = ctypes.c_int
+        L.wvl_precondition_workspace_size.argtypes = [Gp, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.POINTER(_sz)]
+        L.wvl_precondition.restype = ctypes.c_int
+        L.wvl_precondition.argtypes = [Gp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int,
+                                       _vp, _vp, _vp, _sz, _vp]
+        L._pc_declared = True
+    prec = _prec(g)
+    need = _sz(0)
+    _check(L.wvl_precondition_workspace_size(ctypes.byref(grid.c()), prec, max(norb, 1),
+                                             ctypes.byref(need)))
+    st = _stream(g.device)
+    ws, wsb = _workspace(need.value, g.device, st)
+    _check(L.wvl_precondition(ctypes.byref(grid.c()), prec, norb, g.data_ptr(), eps.data_ptr(),
+                              int(ncg), x.data_ptr(), _p(rr), ws, wsb, st))
+    return x, rr

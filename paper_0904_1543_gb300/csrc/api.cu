@@ -113,7 +113,7 @@ struct Tune {
 // orbital walk of the potential pass)
 static int nbuf(int mode, const Tune& t) { return (t.persist || mode == M_POT) ? 2 : 1; }
 
-enum Op { OP_HPSI, OP_ENERGY, OP_DENSITY, OP_SYN, OP_ANA, OP_MF, OP_MFT, OP_KIN };
+enum Op { OP_HPSI, OP_ENERGY, OP_DENSITY, OP_SYN, OP_ANA, OP_MF, OP_MFT, OP_KIN, OP_HELM };
 enum Stage { ST_SYN = 0, ST_MF = 1, ST_MFT = 2, ST_KIN = 3, ST_ANA = 4, ST_RED = 5 };
 
 constexpr int GMAX = 16;   // orbital groups per cell in the potential pass
@@ -285,6 +285,7 @@ struct CellRun {
     double* epart;
     double* kpart;
     double* rpart;
+    const double* eps = nullptr;   // OP_HELM: per-orbital shift
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -365,6 +366,35 @@ static std::vector<PassCall<T>> build_calls(int op, std::vector<CellRun<T>>& run
     switch (op) {
     case OP_SYN:
         synthesis(true);
+        break;
+    case OP_HELM:
+        // A c = S^T (K s - eps s), s = S c: the kinetic passes with K_0 = -eps s
+        // (Eq. kinetic1d), between synthesis and analysis
+        synthesis(false);                      // s -> D
+        add(K_KIN, M_KMID, 1, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, D_), B(r, A_));
+            d.s.eps = r.eps;
+            d.s.out2 = B(r, C_);
+            d.hax = r.hg[0];
+            return d;
+        });
+        add(K_KIN, M_KMID, 2, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, C_), B(r, B_));
+            d.s.in2 = B(r, A_);
+            d.s.out2 = B(r, D_);
+            d.hax = r.hg[1];
+            return d;
+        });
+        add(K_KIN, M_KLAST, 3, ST_KIN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, D_), B(r, A_));
+            d.s.in2 = B(r, B_);
+            d.s.part = r.kpart;
+            d.hax = r.hg[2];
+            return d;
+        });
+        add(K_ANA, M_PLAIN, 1, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
+        add(K_ANA, M_PLAIN, 2, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, B_), B(r, A_)); });
+        add(K_ANA, M_COMP, 3, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), r.out); });
         break;
     case OP_ANA:
         add(K_ANA, M_PLAIN, 1, ST_ANA, [&](CellRun<T>& r) { return seg_for(r, r.in, B(r, A_)); });
@@ -651,6 +681,124 @@ static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void
     return run_op<T>(op, runs, nullptr, nullptr, static_cast<cudaStream_t>(stream));
 }
 
+// ------------------------------------------------------------ preconditioner
+// Diagonal of S_d^T T_d S_d on a periodic line of 2 nc fine points for the
+// scaling (a = 0) and wavelet (a = 1) component of coarse point 0: the
+// synthesis of that unit coefficient, the 29-tap kinetic filter, and the
+// analysis entry.  By Eq. (fprod) and S_d^T S_d = 1, the diagonal of
+// S^T K S for component mu = a1 + 2 a2 + 4 a3 is D_1[a1] + D_2[a2] + D_3[a3].
+static void diag1d(int nc, double hgrid, double out[2]) {
+    const FilterSet& F = filters();
+    const int N = 2 * nc;
+    auto wrap = [N](int i) { return ((i % N) + N) % N; };
+    std::vector<double> s(N), t(N);
+    const double sc = -1.0 / (2.0 * hgrid * hgrid);
+    for (int a = 0; a < 2; ++a) {
+        const double* f = (a == 0) ? F.h : F.g;
+        std::fill(s.begin(), s.end(), 0.0);
+        for (int k = -7; k <= 8; ++k) s[wrap(k)] += f[k + 7];
+        for (int I = 0; I < N; ++I) {
+            double v = 0.0;
+            for (int l = -14; l <= 14; ++l) v += sc * F.a[l + 14] * s[wrap(I - l)];
+            t[I] = v;
+        }
+        double y = 0.0;
+        for (int k = -7; k <= 8; ++k) y += f[k + 7] * t[wrap(k)];
+        out[a] = y;
+    }
+}
+
+static void helmholtz_diag(const int n[3], const double hg[3], double d[8]) {
+    double D[3][2];
+    for (int ax = 0; ax < 3; ++ax) diag1d(n[ax], hg[ax], D[ax]);
+    for (int mu = 0; mu < 8; ++mu) d[mu] = D[0][mu & 1] + D[1][(mu >> 1) & 1] + D[2][mu >> 2];
+}
+
+static int pcg_blocks(long long len) {
+    long long b = (len + 4 * 256 - 1) / (4 * 256);
+    return (int)std::max(1LL, std::min(b, 64LL));
+}
+
+static size_t precond_ws_bytes(const int Nf[3], int norb, size_t elt) {
+    const long long P = (long long)Nf[0] * Nf[1] * Nf[2];
+    size_t b = run_ws_bytes(Nf, norb, elt);
+    b += 4 * align256((size_t)norb * P * elt);
+    b += align256((size_t)norb * pcg_blocks(P) * sizeof(double));
+    b += 3 * align256((size_t)norb * sizeof(double));
+    return b;
+}
+
+template <typename T>
+static wvl_status run_precond(const wvl_grid* grid, int norb, const T* g, const double* eps,
+                              int ncg, T* x, double* rr, void* ws, size_t ws_bytes,
+                              cudaStream_t st) {
+    CellRun<T> r;
+    grid_dims(grid, r.n, r.Nf, r.hg, r.P);
+    r.norb = norb;
+    r.eps = eps;
+    r.V = nullptr;
+    r.rho = nullptr;
+    r.occ = nullptr;
+    r.ekin = nullptr;
+    r.epot = nullptr;
+    const size_t need = precond_ws_bytes(r.Nf, norb, sizeof(T));
+    if (!ws) return fail(WVL_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(WVL_EINVAL, "workspace is not 256-byte aligned");
+    if (ws_bytes < need)
+        return fail(WVL_ENOMEM_WS, "workspace has %zu bytes, %zu needed", ws_bytes, need);
+    char* w = static_cast<char*>(ws);
+    carve(r, w);
+    w += run_ws_bytes(r.Nf, norb, sizeof(T));
+    const size_t vb = align256((size_t)norb * r.P * sizeof(T));
+    T* rv = reinterpret_cast<T*>(w);
+    T* zv = reinterpret_cast<T*>(w + vb);
+    T* pv = reinterpret_cast<T*>(w + 2 * vb);
+    T* Ap = reinterpret_cast<T*>(w + 3 * vb);
+    w += 4 * vb;
+    PcgParams q;
+    helmholtz_diag(r.n, r.hg, q.diag);
+    q.eps = eps;
+    q.len = r.P;
+    q.m = r.P / 8;
+    q.norb = norb;
+    q.nblk = pcg_blocks(r.P);
+    q.part = reinterpret_cast<double*>(w);
+    w += align256((size_t)norb * q.nblk * sizeof(double));
+    double* rz0 = reinterpret_cast<double*>(w);
+    double* rz1 = reinterpret_cast<double*>(w + align256(norb * sizeof(double)));
+    double* pq = reinterpret_cast<double*>(w + 2 * align256(norb * sizeof(double)));
+
+    cudaError_t e;
+#define WVL_CU(call, what)                                  \
+    do {                                                    \
+        if ((e = (call)) != cudaSuccess) return cuda_fail(e, what); \
+    } while (0)
+    WVL_CU(launch_pcg<T>(PCG_INIT, q, x, rv, zv, pv, g, nullptr, nullptr, st), "pcg init");
+    WVL_CU(launch_reduce_parts(q.part, nullptr, q.nblk, norb, rz0, st), "pcg r.z");
+    for (int it = 0; it < ncg; ++it) {
+        r.in = pv;
+        r.out = Ap;
+        std::vector<CellRun<T>> runs(1, r);
+        wvl_status s = run_op<T>(OP_HELM, runs, nullptr, nullptr, st);
+        if (s != WVL_OK) return s;
+        WVL_CU(launch_pcg<T>(PCG_DOT, q, pv, Ap, nullptr, nullptr, nullptr, nullptr, nullptr, st),
+               "pcg p.Ap");
+        WVL_CU(launch_reduce_parts(q.part, nullptr, q.nblk, norb, pq, st), "pcg p.Ap");
+        WVL_CU(launch_pcg<T>(PCG_STEP, q, x, rv, zv, pv, Ap, rz0, pq, st), "pcg step");
+        WVL_CU(launch_reduce_parts(q.part, nullptr, q.nblk, norb, rz1, st), "pcg r.z");
+        WVL_CU(launch_pcg<T>(PCG_DIR, q, pv, nullptr, zv, nullptr, nullptr, rz1, rz0, st),
+               "pcg direction");
+        std::swap(rz0, rz1);
+    }
+    if (rr) {
+        WVL_CU(launch_pcg<T>(PCG_DOT, q, rv, rv, nullptr, nullptr, nullptr, nullptr, nullptr, st),
+               "pcg r.r");
+        WVL_CU(launch_reduce_parts(q.part, nullptr, q.nblk, norb, rr, st), "pcg r.r");
+    }
+#undef WVL_CU
+    return WVL_OK;
+}
+
 static wvl_status dispatch_single(int op, const wvl_grid* grid, int prec, int norb,
                                   const void* in, void* out, const void* V,
                                   const double* occ, double* rho, double* ekin,
@@ -843,6 +991,39 @@ wvl_status wvl_energy(const wvl_grid* grid, int prec, int norb, const void* psi_
     WVL_TRY(check_ptr(epot, "epot", true));
     return dispatch_single(OP_ENERGY, grid, prec, norb, psi_c, nullptr, V, occ, rho, ekin,
                            epot, ws, ws_bytes, stream);
+}
+
+wvl_status wvl_precondition_workspace_size(const wvl_grid* grid, int prec, int norb,
+                                           size_t* bytes) {
+    g_err[0] = 0;
+    WVL_TRY(check_grid(grid));
+    WVL_TRY(check_prec(prec));
+    if (norb < 0) return fail(WVL_EINVAL, "norb < 0");
+    if (!bytes) return fail(WVL_EINVAL, "bytes is NULL");
+    int n[3], Nf[3];
+    double hg[3];
+    long long P;
+    grid_dims(grid, n, Nf, hg, P);
+    *bytes = precond_ws_bytes(Nf, std::max(norb, 1), prec == WVL_F64 ? 8 : 4);
+    return WVL_OK;
+}
+
+wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void* g,
+                            const double* eps, int ncg, void* x, double* rr, void* ws,
+                            size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_ptr(g, "g", true));
+    WVL_TRY(check_ptr(eps, "eps", true));
+    WVL_TRY(check_ptr(x, "x", true));
+    WVL_TRY(check_ptr(rr, "rr", false));
+    if (ncg < 0 || ncg > 10000) return fail(WVL_EINVAL, "ncg = %d out of range", ncg);
+    if (g == x) return fail(WVL_EINVAL, "g and x must not alias");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (prec == WVL_F64)
+        return run_precond<double>(grid, norb, static_cast<const double*>(g), eps, ncg,
+                                   static_cast<double*>(x), rr, ws, ws_bytes, st);
+    return run_precond<float>(grid, norb, static_cast<const float*>(g), eps, ncg,
+                              static_cast<float*>(x), rr, ws, ws_bytes, st);
 }
 
 // ----------------------------------------------------------------- plans

@@ -271,6 +271,12 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                 T acc[R];
                 #pragma unroll
                 for (int r = 0; r < R; ++r) acc[r] = KM ? kv[r] : T(0);
+                if (MODE == M_KMID && S.in2 == nullptr && S.eps != nullptr) {
+                    // K_0 = -eps s: the Helmholtz operator of the preconditioner
+                    const T me = T(-S.eps[orb]);
+                    #pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] = me * srow_line[hl + i0 + r];
+                }
                 if (KM && kline != nullptr) {
                     const int i1 = (c + nslots) * R;
                     #pragma unroll

@@ -52,6 +52,7 @@ struct Seg {
     double* rho;          // M_POT: density target (null = none)
     double* part;         // per (orbital, tile) partial sums, [norb][tiles]
     const double* occ;    // M_POT: occupations of the segment's orbitals
+    const double* eps;    // M_KMID pass 1 without in2: K_0 = -eps[o] G (Helmholtz shift)
     long long P;          // elements per orbital
     long long rho_gstride;// M_POT: 0 -> rho += (direct), else group g writes rho[g*stride]
     long long blk0;       // first work unit of the segment in the launch
@@ -98,6 +99,23 @@ cudaError_t launch_pass(int kind, int mode, int R, const PassParams<T>& p,
 // current device (done lazily by launch_pass too; needed before capture).
 template <typename T>
 cudaError_t prepare_pass_kernels();
+
+// Preconditioned conjugate gradient on compressed coefficients (pcg.cu).
+struct PcgParams {
+    double diag[8];       // diagonal of S^T K S per component mu
+    const double* eps;    // per-orbital shift (device)
+    double* part;         // block partials [norb][nblk]
+    long long len;        // compressed length per orbital (8 m)
+    long long m;          // coarse points
+    int norb;
+    int nblk;             // blocks per orbital
+};
+enum PcgOp { PCG_INIT = 0, PCG_DOT = 1, PCG_STEP = 2, PCG_DIR = 3 };
+// INIT: (a=x, b=r, c=z, d=p, e=g);  DOT: (a, b) -> partials;
+// STEP: (a=x, b=r, c=z, d=p, e=Ap, s1=rz, s2=pq);  DIR: (a=p, c=z, s1=rz_new, s2=rz_old)
+template <typename T>
+cudaError_t launch_pcg(int which, const PcgParams& q, T* a, T* b, T* c, T* d, const T* e,
+                       const double* s1, const double* s2, cudaStream_t st);
 
 // Kernel-launch counter behind wvl_kernel_launches().
 void count_launches(unsigned long long k);
