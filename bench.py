@@ -269,7 +269,24 @@ def measure_variants(args, W, torch, dev):
         "error_sample": "H psi and energies: orbitals 0 and 255 against the FP64 oracle; "
                         "rho: all 256 orbitals against the FP64 GPU form",
     }
-    del res, hp32, hp64, psi64, psi32
+    del res, hp32, hp64, psi32
+    # ---- preconditioner: 5 PCG iterations of the Helmholtz equation, FP64,
+    # the same 256 orbitals of coarse 48^3 (eps_o in [-1.5, -0.2])
+    eps = -torch.linspace(0.2, 1.5, norb, dtype=torch.float64, device=dev)
+    ncg = 5
+    ms_pc = _time_steps(torch, lambda: W.precondition(psi64, eps, g, ncg), max(2, args.steps // 3), 2)
+    pts = norb * 8 * n[0] * n[1] * n[2]
+    # FP64-pipe work per CG iteration and fine point: synthesis 48 + kinetic 87
+    # + analysis 48 DFMA (vector updates are memory-bound and not counted)
+    out["precond_fp64"] = {
+        "workload": "Helmholtz preconditioner (Eq. precon), 5 PCG iterations per orbital, "
+                    "256 orbitals on periodic coarse 48^3, FP64",
+        "value": norb / (ms_pc * 1e-3), "unit": "orbitals preconditioned/s (5 iterations)",
+        "ms_per_step": ms_pc,
+        "fp64_tflops": 2.0 * 183 * pts * ncg / (ms_pc * 1e-3) / 1e12,
+        "checked": "tests/test_gpu_precond.py: PCG iterates against the oracle (1e-11)",
+    }
+    del psi64
     torch.cuda.empty_cache()
     # ---- autograd, coarse 64^3 x 512 orbitals, FP32 forward + backward
     n = (64, 64, 64)
