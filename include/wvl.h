@@ -189,6 +189,47 @@ wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void
                             const double* eps, int ncg, void* x, double* rr,
                             void* ws, size_t ws_bytes, void* stream);
 
+/* Localisation regions of the compressed form (paper Sec. "Daubechies basis
+ * and wavelet transformation", Eq. wavef0: the scaling sum runs over the
+ * low-resolution region, the wavelet sum over the generally smaller
+ * high-resolution region, and only those coefficients are stored).
+ * An orbital's compressed vector then holds ncoarse scaling coefficients
+ * (coarse-region points in lexicographic order, i1 fastest) followed by
+ * nfine groups of the 7 wavelet coefficients (fine-region points in the
+ * same order, mu = 1..7 fastest); orbital o starts at o (ncoarse + 7 nfine).
+ * coarse_index, fine_index: DEVICE int32 [n3][n2][n1]; coarse_index[p] is
+ * the position of c^0 of coarse point p, fine_index[p] = k such that c^mu
+ * sits at ncoarse + 7 k + mu - 1; -1 off the region.  Off-region
+ * coefficients are zero on input and dropped on output (H is restricted to
+ * the region: P^T H P). */
+typedef struct {
+    const int* coarse_index;
+    const int* fine_index;
+    long long ncoarse, nfine;
+} wvl_region;
+
+/* Host helper: index arrays (HOST int32 [n1 n2 n3]) and counts from two
+ * HOST masks (uint8 [n3][n2][n1], nonzero = in the region). */
+wvl_status wvl_region_index(const wvl_grid* grid, const unsigned char* coarse_mask,
+                            const unsigned char* fine_mask, int* coarse_index,
+                            int* fine_index, long long* ncoarse, long long* nfine);
+
+/* The entry points above, with region-compressed coefficient arrays. */
+wvl_status wvl_synthesis_region(const wvl_grid* grid, const wvl_region* region, int prec,
+                                int norb, const void* psi_c, void* s,
+                                void* ws, size_t ws_bytes, void* stream);
+wvl_status wvl_analysis_region(const wvl_grid* grid, const wvl_region* region, int prec,
+                               int norb, const void* z, void* psi_c,
+                               void* ws, size_t ws_bytes, void* stream);
+wvl_status wvl_density_region(const wvl_grid* grid, const wvl_region* region, int prec,
+                              int norb, const void* psi_c, const double* occ, double* rho,
+                              void* ws, size_t ws_bytes, void* stream);
+wvl_status wvl_hpsi_local_region(const wvl_grid* grid, const wvl_region* region, int prec,
+                                 int norb, const void* psi_c, const void* V,
+                                 const double* occ, void* hpsi_c, double* rho,
+                                 double* ekin, double* epot,
+                                 void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched plans: many orbitals on cells of different sizes in one enqueue
  * (the paper's orbital distribution, Sec. "Parallel distribution", inside

@@ -428,3 +428,111 @@ def precondition(g, eps, grid: Grid, ncg=5, x=None, want_residual=True):
     _check(L.wvl_precondition(ctypes.byref(grid.c()), prec, norb, g.data_ptr(), eps.data_ptr(),
                               int(ncg), x.data_ptr(), _p(rr), ws, wsb, st))
     return x, rr
+
+
+class _Region(ctypes.Structure):
+    _fields_ = [("coarse_index", _vp), ("fine_index", _vp), ("ncoarse", ctypes.c_longlong),
+                ("nfine", ctypes.c_longlong)]
+
+
+def _declare_region(L):
+    if getattr(L, "_region_declared", False):
+        return
+    Gp, Rp = ctypes.POINTER(_Grid), ctypes.POINTER(_Region)
+    sig = {
+        "wvl_region_index": [Gp, _vp, _vp, _vp, _vp, _vp, _vp],
+        "wvl_synthesis_region": [Gp, Rp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp],
+        "wvl_analysis_region": [Gp, Rp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp],
+        "wvl_density_region": [Gp, Rp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _vp],
+        "wvl_hpsi_local_region": [Gp, Rp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, _vp, _sz, _vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.restype = ctypes.c_int
+        f.argtypes = args
+    L._region_declared = True
+
+
+class Region:
+    """Localisation region of the compressed form: boolean masks of shape
+    (n3, n2, n1) for the points that keep their scaling coefficient (coarse)
+    and their seven wavelet coefficients (fine)."""
+
+    def __init__(self, grid: Grid, coarse_mask, fine_mask, device="cuda"):
+        import numpy as np
+        L = lib()
+        _declare_region(L)
+        m = grid.n[0] * grid.n[1] * grid.n[2]
+        cm = np.ascontiguousarray(coarse_mask, dtype=np.uint8).reshape(-1)
+        fm = np.ascontiguousarray(fine_mask, dtype=np.uint8).reshape(-1)
+        if cm.size != m or fm.size != m:
+            raise ValueError("masks must have n1 n2 n3 entries")
+        ci = np.empty(m, dtype=np.int32)
+        fi = np.empty(m, dtype=np.int32)
+        nc, nf = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        _check(L.wvl_region_index(ctypes.byref(grid.c()), cm.ctypes.data, fm.ctypes.data,
+                                  ci.ctypes.data, fi.ctypes.data, ctypes.byref(nc),
+                                  ctypes.byref(nf)))
+        self.grid = grid
+        self.coarse_index = torch.from_numpy(ci).to(device)
+        self.fine_index = torch.from_numpy(fi).to(device)
+        self.ncoarse, self.nfine = nc.value, nf.value
+        self.clen = self.ncoarse + 7 * self.nfine
+
+    def c(self):
+        return _Region(self.coarse_index.data_ptr(), self.fine_index.data_ptr(), self.ncoarse,
+                       self.nfine)
+
+
+def _run_region(name, grid, region, prec, norb, device, *ptrs):
+    L = lib()
+    _declare_region(L)
+    st = _stream(device)
+    ws, wsb = _workspace(workspace_size(grid, prec, max(norb, 1)), device, st)
+    _check(getattr(L, name)(ctypes.byref(grid.c()), ctypes.byref(region.c()), prec, norb,
+                            *ptrs, ws, wsb, st))
+
+
+def synthesis_region(psi_c, grid: Grid, region: Region, out=None):
+    norb = _norb(psi_c, region.clen) if region.clen else 0
+    out = torch.empty((norb, *grid.fine), dtype=psi_c.dtype, device=psi_c.device) if out is None else out
+    _dev(psi_c, "psi_c"), _dev(out, "out")
+    _run_region("wvl_synthesis_region", grid, region, _prec(psi_c), norb, psi_c.device,
+                psi_c.data_ptr(), out.data_ptr())
+    return out
+
+
+def analysis_region(z, grid: Grid, region: Region, out=None):
+    norb = _norb(z, grid.ncoef)
+    out = torch.empty((norb, region.clen), dtype=z.dtype, device=z.device) if out is None else out
+    _dev(z, "z"), _dev(out, "out")
+    _run_region("wvl_analysis_region", grid, region, _prec(z), norb, z.device, z.data_ptr(),
+                out.data_ptr())
+    return out
+
+
+def density_region(psi_c, occ, grid: Grid, region: Region, rho=None):
+    norb = occ.numel()
+    rho = torch.zeros(grid.fine, dtype=torch.float64, device=psi_c.device) if rho is None else rho
+    _dev(psi_c, "psi_c"), _dev(occ, "occ"), _dev(rho, "rho")
+    _run_region("wvl_density_region", grid, region, _prec(psi_c), norb, psi_c.device,
+                psi_c.data_ptr(), occ.data_ptr(), rho.data_ptr())
+    return rho
+
+
+def hpsi_local_region(psi_c, V, occ, grid: Grid, region: Region, rho=None, out=None):
+    norb = occ.numel()
+    if psi_c.numel() != norb * region.clen:
+        raise ValueError("psi_c must hold norb region-compressed orbitals")
+    out = torch.empty_like(psi_c) if out is None else out
+    ek = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    ep = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    for t, nm in ((psi_c, "psi_c"), (V, "V"), (occ, "occ"), (out, "out")):
+        _dev(t, nm)
+    if rho is not None:
+        _dev(rho, "rho")
+    _run_region("wvl_hpsi_local_region", grid, region, _prec(psi_c), norb, psi_c.device,
+                psi_c.data_ptr(), V.data_ptr(), occ.data_ptr(), out.data_ptr(), _p(rho),
+                ek.data_ptr(), ep.data_ptr())
+    return out, ek, ep

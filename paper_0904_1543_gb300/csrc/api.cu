@@ -286,6 +286,10 @@ struct CellRun {
     double* kpart;
     double* rpart;
     const double* eps = nullptr;   // OP_HELM: per-orbital shift
+    const int* mapc = nullptr;     // localisation region (nullptr: full grid)
+    const int* mapf = nullptr;
+    long long clen = 0;            // region: compressed length per orbital
+    long long ncoarse = 0;         // region: stored scaling coefficients
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -327,6 +331,11 @@ static SegDesc<T> seg_for(const CellRun<T>& c, const T* in, T* out) {
     d.s.n2 = c.n[1];
     d.s.norb = c.norb;
     d.s.opg = 1;
+    // compressed form: full grid unless a localisation region is given
+    d.s.mapc = c.mapc;
+    d.s.mapf = c.mapf;
+    d.s.clen = c.mapc ? c.clen : c.P;
+    d.s.ncoarse = c.mapc ? c.ncoarse : c.P / 8;
     for (int k = 0; k < 3; ++k) d.Nf[k] = c.Nf[k];
     return d;
 }
@@ -660,10 +669,16 @@ template <typename T>
 static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void* in,
                               void* out, const void* V, const double* occ, double* rho,
                               double* ekin, double* epot, void* ws, size_t ws_bytes,
-                              void* stream) {
+                              void* stream, const wvl_region* reg) {
     CellRun<T> r;
     grid_dims(grid, r.n, r.Nf, r.hg, r.P);
     r.norb = norb;
+    if (reg) {
+        r.mapc = reg->coarse_index;
+        r.mapf = reg->fine_index;
+        r.ncoarse = reg->ncoarse;
+        r.clen = reg->ncoarse + 7 * reg->nfine;
+    }
     r.in = static_cast<const T*>(in);
     r.out = static_cast<T*>(out);
     r.V = static_cast<const T*>(V);
@@ -802,13 +817,25 @@ static wvl_status run_precond(const wvl_grid* grid, int norb, const T* g, const 
 static wvl_status dispatch_single(int op, const wvl_grid* grid, int prec, int norb,
                                   const void* in, void* out, const void* V,
                                   const double* occ, double* rho, double* ekin,
-                                  double* epot, void* ws, size_t ws_bytes, void* stream) {
+                                  double* epot, void* ws, size_t ws_bytes, void* stream,
+                                  const wvl_region* reg = nullptr) {
     g_err[0] = 0;
     if (prec == WVL_F64)
         return single_cell<double>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
-                                   ws_bytes, stream);
+                                   ws_bytes, stream, reg);
     return single_cell<float>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
-                              ws_bytes, stream);
+                              ws_bytes, stream, reg);
+}
+
+static wvl_status check_region(const wvl_grid* grid, const wvl_region* reg) {
+    if (!reg) return fail(WVL_EINVAL, "region is NULL");
+    WVL_TRY(check_ptr(reg->coarse_index, "region coarse_index", true));
+    WVL_TRY(check_ptr(reg->fine_index, "region fine_index", true));
+    const long long m = (long long)grid->n1 * grid->n2 * grid->n3;
+    if (reg->ncoarse < 0 || reg->ncoarse > m || reg->nfine < 0 || reg->nfine > m)
+        return fail(WVL_EINVAL, "region counts out of range (ncoarse %lld, nfine %lld, %lld points)",
+                    reg->ncoarse, reg->nfine, m);
+    return WVL_OK;
 }
 
 }  // namespace wvl
@@ -1024,6 +1051,77 @@ wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void
                                    static_cast<double*>(x), rr, ws, ws_bytes, st);
     return run_precond<float>(grid, norb, static_cast<const float*>(g), eps, ncg,
                               static_cast<float*>(x), rr, ws, ws_bytes, st);
+}
+
+// ------------------------------------------------------ localisation regions
+wvl_status wvl_region_index(const wvl_grid* grid, const unsigned char* coarse_mask,
+                            const unsigned char* fine_mask, int* coarse_index,
+                            int* fine_index, long long* ncoarse, long long* nfine) {
+    g_err[0] = 0;
+    WVL_TRY(check_grid(grid));
+    if (!coarse_mask || !fine_mask || !coarse_index || !fine_index || !ncoarse || !nfine)
+        return fail(WVL_EINVAL, "NULL argument");
+    const long long m = (long long)grid->n1 * grid->n2 * grid->n3;
+    if (m > 0x7fffffffLL) return fail(WVL_EUNSUPPORTED, "grid too large for int32 indices");
+    long long c = 0, f = 0;
+    for (long long p = 0; p < m; ++p) {
+        coarse_index[p] = coarse_mask[p] ? (int)c++ : -1;
+        fine_index[p] = fine_mask[p] ? (int)f++ : -1;
+    }
+    *ncoarse = c;
+    *nfine = f;
+    return WVL_OK;
+}
+
+wvl_status wvl_synthesis_region(const wvl_grid* grid, const wvl_region* region, int prec,
+                                int norb, const void* psi_c, void* s, void* ws,
+                                size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_region(grid, region));
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    WVL_TRY(check_ptr(s, "s", true));
+    return dispatch_single(OP_SYN, grid, prec, norb, psi_c, s, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, ws, ws_bytes, stream, region);
+}
+
+wvl_status wvl_analysis_region(const wvl_grid* grid, const wvl_region* region, int prec,
+                               int norb, const void* z, void* psi_c, void* ws,
+                               size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_region(grid, region));
+    WVL_TRY(check_ptr(z, "z", true));
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    return dispatch_single(OP_ANA, grid, prec, norb, z, psi_c, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, ws, ws_bytes, stream, region);
+}
+
+wvl_status wvl_density_region(const wvl_grid* grid, const wvl_region* region, int prec,
+                              int norb, const void* psi_c, const double* occ, double* rho,
+                              void* ws, size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_region(grid, region));
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    WVL_TRY(check_ptr(occ, "occ", true));
+    WVL_TRY(check_ptr(rho, "rho", true));
+    return dispatch_single(OP_DENSITY, grid, prec, norb, psi_c, nullptr, nullptr, occ, rho,
+                           nullptr, nullptr, ws, ws_bytes, stream, region);
+}
+
+wvl_status wvl_hpsi_local_region(const wvl_grid* grid, const wvl_region* region, int prec,
+                                 int norb, const void* psi_c, const void* V, const double* occ,
+                                 void* hpsi_c, double* rho, double* ekin, double* epot,
+                                 void* ws, size_t ws_bytes, void* stream) {
+    WVL_COMMON_CHECKS();
+    WVL_TRY(check_region(grid, region));
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    WVL_TRY(check_ptr(V, "V", true));
+    WVL_TRY(check_ptr(occ, "occ", true));
+    WVL_TRY(check_ptr(hpsi_c, "hpsi_c", true));
+    WVL_TRY(check_ptr(rho, "rho", false));
+    WVL_TRY(check_ptr(ekin, "ekin", true));
+    WVL_TRY(check_ptr(epot, "epot", true));
+    return dispatch_single(OP_HPSI, grid, prec, norb, psi_c, hpsi_c, V, occ, rho, ekin, epot,
+                           ws, ws_bytes, stream, region);
 }
 
 // ----------------------------------------------------------------- plans

@@ -81,6 +81,18 @@ __device__ __forceinline__ void cp_async(T* smem_dst, const T* gsrc) {
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
+// copy, or zero-fill the destination when the source does not exist
+template <typename T>
+__device__ __forceinline__ void cp_async_or_zero(T* smem_dst, const T* gsrc, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const unsigned nbytes = valid ? (unsigned)sizeof(T) : 0u;
+    if constexpr (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gsrc),
+                     "r"(nbytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gsrc),
+                     "r"(nbytes) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -173,16 +185,30 @@ __device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* b
             // it is c^mu[i3][i2][i1], mu = a1 + 2 a2 + 4 a3
             const int x3 = a / S.N2, x2 = a - x3 * S.N2;
             const int mu23 = 2 * (x2 & 1) + 4 * (x3 & 1);
-            const T* cc = S.in + (long long)J.orb * P;
-            const T* cf = cc + (P >> 3);
+            const T* cc = S.in + (long long)J.orb * S.clen;
+            const T* cf = cc + S.ncoarse;
             const long long cb = ((long long)(x3 >> 1) * S.n2 + (x2 >> 1)) * S.n1;
-            #pragma unroll 1
-            for (int j = lane; j < rowlen; j += 32) {
-                const int mu = mu23 + (x & 1);
-                const long long ci = cb + (x >> 1);
-                cp_async(row + j, (mu == 0) ? cc + ci : cf + ci * 7 + mu - 1);
-                x += 32;
-                while (x >= n) x -= n;
+            if (S.mapc == nullptr) {
+                #pragma unroll 1
+                for (int j = lane; j < rowlen; j += 32) {
+                    const int mu = mu23 + (x & 1);
+                    const long long ci = cb + (x >> 1);
+                    cp_async(row + j, (mu == 0) ? cc + ci : cf + ci * 7 + mu - 1);
+                    x += 32;
+                    while (x >= n) x -= n;
+                }
+            } else {
+                // localisation region: coefficients off the region are zero
+                #pragma unroll 1
+                for (int j = lane; j < rowlen; j += 32) {
+                    const int mu = mu23 + (x & 1);
+                    const long long ci = cb + (x >> 1);
+                    const int k = (mu == 0) ? S.mapc[ci] : S.mapf[ci];
+                    const T* src = (k < 0) ? cc : ((mu == 0) ? cc + k : cf + (long long)k * 7 + mu - 1);
+                    cp_async_or_zero(row + j, src, k >= 0);
+                    x += 32;
+                    while (x >= n) x -= n;
+                }
             }
         } else {
             const T* src = S.in + (long long)J.orb * P + (long long)a * n;
@@ -299,9 +325,18 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                         const int mu = (X1 & 1) + 2 * (X2 & 1) + 4 * (I & 1);
                         const long long ci =
                             ((long long)(I >> 1) * S.n2 + (X2 >> 1)) * S.n1 + (X1 >> 1);
-                        T* cc0 = S.out + obase;
-                        if (mu == 0) cc0[ci] = acc[r];
-                        else cc0[(P >> 3) + ci * 7 + mu - 1] = acc[r];
+                        T* cc0 = S.out + (long long)orb * S.clen;
+                        if (S.mapc == nullptr) {
+                            if (mu == 0) cc0[ci] = acc[r];
+                            else cc0[S.ncoarse + ci * 7 + mu - 1] = acc[r];
+                        } else {
+                            // localisation region: only the stored coefficients
+                            const int k = (mu == 0) ? S.mapc[ci] : S.mapf[ci];
+                            if (k >= 0) {
+                                if (mu == 0) cc0[k] = acc[r];
+                                else cc0[S.ncoarse + (long long)k * 7 + mu - 1] = acc[r];
+                            }
+                        }
                     } else if (MODE == M_KMID) {
                         S.out[obase + oidx] = acc[r];
                         S.out2[obase + oidx] = srow_line[hl + I];

@@ -53,6 +53,10 @@ struct Seg {
     double* part;         // per (orbital, tile) partial sums, [norb][tiles]
     const double* occ;    // M_POT: occupations of the segment's orbitals
     const double* eps;    // M_KMID pass 1 without in2: K_0 = -eps[o] G (Helmholtz shift)
+    const int* mapc;      // M_UNCOMP/M_COMP with a localisation region: coarse point ->
+    const int* mapf;      //   position of c^0 / index k of c^{1..7} (ncoarse + 7k), or -1
+    long long clen;       // compressed length of one orbital (orbital stride there)
+    long long ncoarse;    // scaling coefficients stored (start of the wavelet block)
     long long P;          // elements per orbital
     long long rho_gstride;// M_POT: 0 -> rho += (direct), else group g writes rho[g*stride]
     long long blk0;       // first work unit of the segment in the launch
