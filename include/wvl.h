@@ -189,6 +189,28 @@ wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void
                             const double* eps, int ncg, void* x, double* rr,
                             void* ws, size_t ws_bytes, void* stream);
 
+/* Free (isolated) boundary conditions (the paper's GPU code is periodic; its
+ * CPU convolutions also admit isolated conditions, Sec. "Wavelet
+ * transformation and Magic Filters convolutions"): the orbital's basis
+ * functions are those of the coarse points of the box `grid` (n1 x n2 x n3),
+ * with the compressed layout of the periodic entry points on that box, and
+ * every operator acts on the whole space -- input arrays are zero outside,
+ * outputs extend beyond the box.  V and rho cover the box plus
+ * WVL_FREE_PAD coarse points (2 WVL_FREE_PAD fine points) on every side:
+ * fine extents 2 (n_d + 2 WVL_FREE_PAD), index 0 at fine coordinate
+ * -2 WVL_FREE_PAD.  H couples coarse points at most 15 apart, so the
+ * periodic operator on that padded cell, restricted to the box, is the
+ * free-space operator exactly; that is how it is computed. */
+#define WVL_FREE_PAD 8
+wvl_status wvl_free_workspace_size(const wvl_grid* grid, int prec, int norb, size_t* bytes);
+wvl_status wvl_hpsi_local_free(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                               const void* V, const double* occ, void* hpsi_c, double* rho,
+                               double* ekin, double* epot, void* ws, size_t ws_bytes,
+                               void* stream);
+wvl_status wvl_density_free(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                            const double* occ, double* rho, void* ws, size_t ws_bytes,
+                            void* stream);
+
 /* Localisation regions of the compressed form (paper Sec. "Daubechies basis
  * and wavelet transformation", Eq. wavef0: the scaling sum runs over the
  * low-resolution region, the wavelet sum over the generally smaller

@@ -536,3 +536,66 @@ def hpsi_local_region(psi_c, V, occ, grid: Grid, region: Region, rho=None, out=N
                 psi_c.data_ptr(), V.data_ptr(), occ.data_ptr(), out.data_ptr(), _p(rho),
                 ek.data_ptr(), ep.data_ptr())
     return out, ek, ep
+
+
+FREE_PAD = 8   # coarse points of padding per side (WVL_FREE_PAD)
+
+
+def free_fine(grid: Grid):
+    """(N3, N2, N1) of V and rho for free boundary conditions on box `grid`."""
+    return tuple(2 * (v + 2 * FREE_PAD) for v in (grid.n[2], grid.n[1], grid.n[0]))
+
+
+def _declare_free(L):
+    if getattr(L, "_free_declared", False):
+        return
+    Gp = ctypes.POINTER(_Grid)
+    L.wvl_free_workspace_size.restype = ctypes.c_int
+    L.wvl_free_workspace_size.argtypes = [Gp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_sz)]
+    L.wvl_hpsi_local_free.restype = ctypes.c_int
+    L.wvl_hpsi_local_free.argtypes = [Gp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
+                                      _vp, _vp, _vp, _sz, _vp]
+    L.wvl_density_free.restype = ctypes.c_int
+    L.wvl_density_free.argtypes = [Gp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _vp]
+    L._free_declared = True
+
+
+def _free_ws(grid, prec, norb, device):
+    L = lib()
+    _declare_free(L)
+    need = _sz(0)
+    _check(L.wvl_free_workspace_size(ctypes.byref(grid.c()), prec, max(norb, 1),
+                                     ctypes.byref(need)))
+    st = _stream(device)
+    ws, wsb = _workspace(need.value, device, st)
+    return L, ws, wsb, st
+
+
+def hpsi_local_free(psi_c, V, occ, grid: Grid, rho=None, out=None):
+    """Free boundary conditions: psi_c on the coarse points of the box,
+    V and rho on free_fine(grid).  Returns (hpsi_c, ekin, epot)."""
+    norb = _norb(psi_c, grid.ncoef)
+    out = torch.empty_like(psi_c) if out is None else out
+    ek = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    ep = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    for t, nm in ((psi_c, "psi_c"), (V, "V"), (occ, "occ"), (out, "out")):
+        _dev(t, nm)
+    if rho is not None:
+        _dev(rho, "rho")
+    prec = _prec(psi_c)
+    L, ws, wsb, st = _free_ws(grid, prec, norb, psi_c.device)
+    _check(L.wvl_hpsi_local_free(ctypes.byref(grid.c()), prec, norb, psi_c.data_ptr(),
+                                 V.data_ptr(), occ.data_ptr(), out.data_ptr(), _p(rho),
+                                 ek.data_ptr(), ep.data_ptr(), ws, wsb, st))
+    return out, ek, ep
+
+
+def density_free(psi_c, occ, grid: Grid, rho=None):
+    norb = _norb(psi_c, grid.ncoef)
+    rho = torch.zeros(free_fine(grid), dtype=torch.float64, device=psi_c.device) if rho is None else rho
+    _dev(psi_c, "psi_c"), _dev(occ, "occ"), _dev(rho, "rho")
+    prec = _prec(psi_c)
+    L, ws, wsb, st = _free_ws(grid, prec, norb, psi_c.device)
+    _check(L.wvl_density_free(ctypes.byref(grid.c()), prec, norb, psi_c.data_ptr(),
+                              occ.data_ptr(), rho.data_ptr(), ws, wsb, st))
+    return rho

@@ -296,6 +296,8 @@ struct CellRun {
     const int* mapf = nullptr;
     long long clen = 0;            // region: compressed length per orbital
     long long ncoarse = 0;         // region: stored scaling coefficients
+    int bx[3] = {0, 0, 0};         // free BC: box extents inside the padded cell
+    int boff = 0;                  // free BC: padding (coarse points per side)
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -337,11 +339,17 @@ static SegDesc<T> seg_for(const CellRun<T>& c, const T* in, T* out) {
     d.s.n2 = c.n[1];
     d.s.norb = c.norb;
     d.s.opg = 1;
-    // compressed form: full grid unless a localisation region is given
+    // compressed form: full grid unless a localisation region or the box of
+    // free boundary conditions is given
+    const bool reg = c.mapc != nullptr || c.bx[0] > 0;
     d.s.mapc = c.mapc;
     d.s.mapf = c.mapf;
-    d.s.clen = c.mapc ? c.clen : c.P;
-    d.s.ncoarse = c.mapc ? c.ncoarse : c.P / 8;
+    d.s.clen = reg ? c.clen : c.P;
+    d.s.ncoarse = reg ? c.ncoarse : c.P / 8;
+    d.s.bx1 = c.bx[0];
+    d.s.bx2 = c.bx[1];
+    d.s.bx3 = c.bx[2];
+    d.s.boff = c.boff;
     for (int k = 0; k < 3; ++k) d.Nf[k] = c.Nf[k];
     return d;
 }
@@ -692,6 +700,54 @@ static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void
     r.occ = occ;
     r.ekin = ekin;
     r.epot = epot;
+    const size_t need = run_ws_bytes(r.Nf, norb, sizeof(T));
+    if (!ws) return fail(WVL_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(WVL_EINVAL, "workspace is not 256-byte aligned");
+    if (ws_bytes < need)
+        return fail(WVL_ENOMEM_WS, "workspace has %zu bytes, %zu needed", ws_bytes, need);
+    carve(r, static_cast<char*>(ws));
+    std::vector<CellRun<T>> runs(1, r);
+    return run_op<T>(op, runs, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------- free boundaries
+// Free (isolated) boundary conditions: the orbital lives on the coarse points
+// of the box; every operator acts on the whole space.  The interaction range
+// of H is 15 coarse points (synthesis 8 + magic filter 8 fine points out,
+// then back), so the periodic operator on a cell padded by FREE_PAD >= 8
+// coarse points per side, restricted to the box, is the free-space operator
+// exactly; V and rho cover the padded cell.
+constexpr int FREE_PAD = WVL_FREE_PAD;
+
+static void padded_grid(const wvl_grid* g, wvl_grid* out) {
+    *out = *g;
+    out->n1 += 2 * FREE_PAD;
+    out->n2 += 2 * FREE_PAD;
+    out->n3 += 2 * FREE_PAD;
+}
+
+template <typename T>
+static wvl_status free_cell(int op, const wvl_grid* box, int norb, const void* in, void* out,
+                           const void* V, const double* occ, double* rho, double* ekin,
+                           double* epot, void* ws, size_t ws_bytes, void* stream) {
+    wvl_grid g;
+    padded_grid(box, &g);
+    CellRun<T> r;
+    grid_dims(&g, r.n, r.Nf, r.hg, r.P);
+    r.norb = norb;
+    r.in = static_cast<const T*>(in);
+    r.out = static_cast<T*>(out);
+    r.V = static_cast<const T*>(V);
+    r.rho = rho;
+    r.occ = occ;
+    r.ekin = ekin;
+    r.epot = epot;
+    r.bx[0] = box->n1;
+    r.bx[1] = box->n2;
+    r.bx[2] = box->n3;
+    r.boff = FREE_PAD;
+    r.ncoarse = (long long)box->n1 * box->n2 * box->n3;
+    r.clen = 8 * r.ncoarse;
     const size_t need = run_ws_bytes(r.Nf, norb, sizeof(T));
     if (!ws) return fail(WVL_EINVAL, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(WVL_EINVAL, "workspace is not 256-byte aligned");
@@ -1057,6 +1113,62 @@ wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void
                                    static_cast<double*>(x), rr, ws, ws_bytes, st);
     return run_precond<float>(grid, norb, static_cast<const float*>(g), eps, ncg,
                               static_cast<float*>(x), rr, ws, ws_bytes, st);
+}
+
+// -------------------------------------------------------- free boundaries
+wvl_status wvl_free_workspace_size(const wvl_grid* grid, int prec, int norb, size_t* bytes) {
+    g_err[0] = 0;
+    WVL_TRY(check_grid(grid));
+    wvl_grid g;
+    padded_grid(grid, &g);
+    WVL_TRY(check_grid(&g));
+    return wvl_workspace_size(&g, prec, norb, bytes);
+}
+
+static wvl_status free_checks(const wvl_grid* grid, int prec, int norb) {
+    g_err[0] = 0;
+    WVL_TRY(check_grid(grid));
+    WVL_TRY(check_prec(prec));
+    wvl_grid g;
+    padded_grid(grid, &g);
+    WVL_TRY(check_grid(&g));
+    if (norb < 0) return fail(WVL_EINVAL, "norb < 0");
+    return WVL_OK;
+}
+
+wvl_status wvl_hpsi_local_free(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                               const void* V, const double* occ, void* hpsi_c, double* rho,
+                               double* ekin, double* epot, void* ws, size_t ws_bytes,
+                               void* stream) {
+    WVL_TRY(free_checks(grid, prec, norb));
+    if (norb == 0) return WVL_OK;
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    WVL_TRY(check_ptr(V, "V", true));
+    WVL_TRY(check_ptr(occ, "occ", true));
+    WVL_TRY(check_ptr(hpsi_c, "hpsi_c", true));
+    WVL_TRY(check_ptr(rho, "rho", false));
+    WVL_TRY(check_ptr(ekin, "ekin", true));
+    WVL_TRY(check_ptr(epot, "epot", true));
+    if (prec == WVL_F64)
+        return free_cell<double>(OP_HPSI, grid, norb, psi_c, hpsi_c, V, occ, rho, ekin, epot, ws,
+                                 ws_bytes, stream);
+    return free_cell<float>(OP_HPSI, grid, norb, psi_c, hpsi_c, V, occ, rho, ekin, epot, ws,
+                            ws_bytes, stream);
+}
+
+wvl_status wvl_density_free(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                            const double* occ, double* rho, void* ws, size_t ws_bytes,
+                            void* stream) {
+    WVL_TRY(free_checks(grid, prec, norb));
+    if (norb == 0) return WVL_OK;
+    WVL_TRY(check_ptr(psi_c, "psi_c", true));
+    WVL_TRY(check_ptr(occ, "occ", true));
+    WVL_TRY(check_ptr(rho, "rho", true));
+    if (prec == WVL_F64)
+        return free_cell<double>(OP_DENSITY, grid, norb, psi_c, nullptr, nullptr, occ, rho,
+                                 nullptr, nullptr, ws, ws_bytes, stream);
+    return free_cell<float>(OP_DENSITY, grid, norb, psi_c, nullptr, nullptr, occ, rho, nullptr,
+                            nullptr, ws, ws_bytes, stream);
 }
 
 // ------------------------------------------------------ localisation regions

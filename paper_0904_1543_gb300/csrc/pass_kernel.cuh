@@ -115,6 +115,23 @@ __device__ __forceinline__ void conv_chunk(const T* __restrict__ srow,
     }
 }
 
+// Position of coarse point (i1, i2, i3) in the stored compressed vector:
+// the scaling coefficient c^0 sits at k, c^mu (mu >= 1) at ncoarse + 7 k + mu - 1;
+// -1 if the point is outside the localisation region or the box of free
+// boundary conditions (whose cell is padded by boff points per side).
+template <typename T>
+__device__ __forceinline__ int stored_index(const Seg<T>& S, long long ci, int i1, int i2,
+                                            int i3, int mu) {
+    if (S.bx1 > 0) {
+        const int j1 = i1 - S.boff, j2 = i2 - S.boff, j3 = i3 - S.boff;
+        if ((unsigned)j1 >= (unsigned)S.bx1 || (unsigned)j2 >= (unsigned)S.bx2 ||
+            (unsigned)j3 >= (unsigned)S.bx3)
+            return -1;
+        return (j3 * S.bx2 + j2) * S.bx1 + j1;
+    }
+    return (mu == 0) ? S.mapc[ci] : S.mapf[ci];
+}
+
 // ------------------------------------------------------------------- jobs
 struct Job {
     long long unit;   // global work unit
@@ -188,7 +205,7 @@ __device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* b
             const T* cc = S.in + (long long)J.orb * S.clen;
             const T* cf = cc + S.ncoarse;
             const long long cb = ((long long)(x3 >> 1) * S.n2 + (x2 >> 1)) * S.n1;
-            if (S.mapc == nullptr) {
+            if (S.mapc == nullptr && S.bx1 == 0) {
                 #pragma unroll 1
                 for (int j = lane; j < rowlen; j += 32) {
                     const int mu = mu23 + (x & 1);
@@ -198,12 +215,12 @@ __device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* b
                     while (x >= n) x -= n;
                 }
             } else {
-                // localisation region: coefficients off the region are zero
+                // region or box: coefficients off it are zero
                 #pragma unroll 1
                 for (int j = lane; j < rowlen; j += 32) {
                     const int mu = mu23 + (x & 1);
                     const long long ci = cb + (x >> 1);
-                    const int k = (mu == 0) ? S.mapc[ci] : S.mapf[ci];
+                    const int k = stored_index(S, ci, x >> 1, x2 >> 1, x3 >> 1, mu);
                     const T* src = (k < 0) ? cc : ((mu == 0) ? cc + k : cf + (long long)k * 7 + mu - 1);
                     cp_async_or_zero(row + j, src, k >= 0);
                     x += 32;
@@ -326,12 +343,12 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                         const long long ci =
                             ((long long)(I >> 1) * S.n2 + (X2 >> 1)) * S.n1 + (X1 >> 1);
                         T* cc0 = S.out + (long long)orb * S.clen;
-                        if (S.mapc == nullptr) {
+                        if (S.mapc == nullptr && S.bx1 == 0) {
                             if (mu == 0) cc0[ci] = acc[r];
                             else cc0[S.ncoarse + ci * 7 + mu - 1] = acc[r];
                         } else {
-                            // localisation region: only the stored coefficients
-                            const int k = (mu == 0) ? S.mapc[ci] : S.mapf[ci];
+                            // region or box: only the stored coefficients
+                            const int k = stored_index(S, ci, X1 >> 1, X2 >> 1, I >> 1, mu);
                             if (k >= 0) {
                                 if (mu == 0) cc0[k] = acc[r];
                                 else cc0[S.ncoarse + (long long)k * 7 + mu - 1] = acc[r];

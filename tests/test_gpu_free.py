@@ -1,0 +1,48 @@
+"""GPU parity of free (isolated) boundary conditions against the free-space
+oracle (dense non-circulant operators on an extended grid, no wrap-around).
+FP64 bound 1e-12 as in the other parity tests."""
+import numpy as np
+import pytest
+
+import oracle.free as FR
+from paper_0904_1543_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+RTOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_0904_1543_gb300 as W
+    return W
+
+
+@pytest.mark.parametrize("n,norb", [((2, 3, 2), 2), ((4, 3, 5), 2), ((1, 1, 1), 1)])
+def test_hpsi_free(W, n, norb):
+    import torch
+    g = W.Grid(n)
+    pad = W.FREE_PAD
+    padded = tuple(v + 2 * pad for v in n)
+    psi = inputs.orbitals(111, norb, n)
+    Vp = inputs.gaussian_potential(111, 0, padded)
+    occ = np.array([2.0, 1.0][:norb])
+    rho = torch.zeros(W.free_fine(g), dtype=torch.float64, device="cuda")
+    hp, ek, ep = W.hpsi_local_free(torch.from_numpy(psi).cuda(), torch.from_numpy(Vp).cuda(),
+                                   torch.from_numpy(occ).cuda(), g, rho=rho)
+    Vx = FR.extend(Vp, n, 2 * pad)
+    rho_ref = 0.0
+    for o in range(norb):
+        r = FR.hpsi_local(psi[o], Vx, occ[o], n)
+        ref = r["hpsi_c"]
+        assert np.abs(hp[o].cpu().numpy() - ref).max() < RTOL64 * np.abs(ref).max()
+        assert abs(float(ek[o]) - r["ekin"]) < RTOL64 * abs(r["ekin"])
+        assert abs(float(ep[o]) - r["epot"]) < RTOL64 * abs(r["epot"])
+        rho_ref = rho_ref + r["rho"]
+    got = rho.cpu().numpy()
+    ref = FR.restrict(rho_ref, 2 * pad)
+    assert np.abs(got - ref).max() < RTOL64 * np.abs(ref).max()
+    rho2 = W.density_free(torch.from_numpy(psi).cuda(), torch.from_numpy(occ).cuda(), g)
+    assert np.abs(rho2.cpu().numpy() - ref).max() < RTOL64 * np.abs(ref).max()
