@@ -287,6 +287,34 @@ def measure_variants(args, W, torch, dev):
         "checked": "tests/test_gpu_precond.py: PCG iterates against the oracle (1e-11)",
     }
     del psi64
+    # ---- localisation regions: 64 orbitals on the periodic 48^3 cell, each
+    # stored on a ball of radius 20 (scaling) / 10 (wavelets) coarse points
+    cm, fm = inputs.sphere_masks(n, (24, 24, 24), 20.0, 10.0)
+    reg = W.Region(g, cm, fm)
+    nr = 64
+    pr = inputs.vectors_device(5, nr, reg.clen, dev)
+    occr = torch.full((nr,), 2.0, dtype=torch.float64, device=dev)
+    ms_r = _time_steps(torch, lambda: W.hpsi_local_region(pr, V64, occr, g, reg), 3, 2)
+    out["region_fp64"] = {
+        "workload": "local Hamiltonian on region-compressed orbitals, 64 orbitals on a periodic "
+                    "coarse 48^3 cell, coarse region a ball of radius 20, fine region radius 10, FP64",
+        "value": nr / (ms_r * 1e-3), "unit": UNIT, "ms_per_step": ms_r,
+        "stored_fraction": reg.clen / (8 * n[0] * n[1] * n[2]),
+        "checked": "tests/test_gpu_region.py (1e-12 against the oracle)",
+    }
+    # ---- free boundary conditions: 64 orbitals on a 32^3 box (padded cell 48^3)
+    nb = (32, 32, 32)
+    gb = W.Grid(nb)
+    pf = inputs.orbitals_device(6, nr, nb, dev)
+    Vf = torch.from_numpy(inputs.gaussian_potential(6, 0, tuple(v + 2 * W.FREE_PAD for v in nb))).to(dev)
+    ms_f = _time_steps(torch, lambda: W.hpsi_local_free(pf, Vf, occr, gb), 3, 2)
+    out["free_bc_fp64"] = {
+        "workload": "local Hamiltonian with free boundary conditions, 64 orbitals on a coarse "
+                    "32^3 box (computed on the 48^3 cell padded by 8 points per side), FP64",
+        "value": nr / (ms_f * 1e-3), "unit": UNIT, "ms_per_step": ms_f,
+        "checked": "tests/test_gpu_free.py (1e-12 against the free-space oracle)",
+    }
+    del pr, pf
     torch.cuda.empty_cache()
     # ---- autograd, coarse 64^3 x 512 orbitals, FP32 forward + backward
     n = (64, 64, 64)

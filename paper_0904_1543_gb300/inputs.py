@@ -86,11 +86,16 @@ def orbitals_device(cfg: int, norb: int, n, device, dtype=None):
     torch's seeded Philox generator, seeded with seed(cfg, 0).  Not the
     SplitMix64 stream: used only where no oracle comparison needs the
     whole batch (callers copy back the orbitals they check)."""
+    return vectors_device(cfg, norb, 8 * n[0] * n[1] * n[2], device, dtype)
+
+
+def vectors_device(cfg: int, norb: int, length: int, device, dtype=None):
+    """norb unit-norm vectors of `length` uniform[-1, 1) entries drawn on the
+    device (torch Philox, seed(cfg, 0)); e.g. region-compressed orbitals."""
     import torch
     gen = torch.Generator(device=device)
     gen.manual_seed(seed(cfg, 0))
-    m = 8 * n[0] * n[1] * n[2]
-    x = torch.rand((norb, m), generator=gen, device=device, dtype=torch.float64)
+    x = torch.rand((norb, length), generator=gen, device=device, dtype=torch.float64)
     x = 2.0 * x - 1.0
     x /= torch.linalg.vector_norm(x, dim=1, keepdim=True)
     return x if dtype is None else x.to(dtype)
@@ -99,3 +104,15 @@ def orbitals_device(cfg: int, norb: int, n, device, dtype=None):
 def random_field(cfg: int, stream: int, shape) -> np.ndarray:
     """Uniform[-1, 1) array of the given shape (per-pass sweeps)."""
     return uniform(seed(cfg, stream), int(np.prod(shape)), -1.0, 1.0).reshape(shape)
+
+
+def sphere_masks(n, centre, r_coarse, r_fine):
+    """Coarse and fine localisation regions shaped as balls around `centre`
+    (coarse grid units, minimum-image distance): boolean (n3, n2, n1) masks."""
+    idx = np.meshgrid(*[np.arange(v) for v in (n[2], n[1], n[0])], indexing="ij")
+    d2 = np.zeros(idx[0].shape)
+    for ax, (v, c) in enumerate(zip((n[2], n[1], n[0]), (centre[2], centre[1], centre[0]))):
+        x = idx[ax] - c
+        x = x - v * np.round(x / v)
+        d2 += x * x
+    return d2 <= r_coarse ** 2, d2 <= r_fine ** 2
