@@ -66,10 +66,31 @@ def dist_env():
     return rank, world, local
 
 
+def rank_first_orbital(rank, per_rank):
+    """Weak scaling: rank r owns orbitals r * per_rank .. (r + 1) * per_rank - 1
+    of the synthetic stream (disjoint, no data shared between ranks)."""
+    return rank * per_rank
+
+
+def max_over_ranks(times, dist, world, device="cpu"):
+    """The slowest rank's times (timing is the only cross-rank exchange)."""
+    if world <= 1:
+        return list(times)
+    import torch
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_throughput(norb_per_rank, world, steps, ms):
+    """Whole-job orbital applications per second over all ranks."""
+    return norb_per_rank * world * steps / (ms * 1e-3)
+
+
 def make_inputs(rank, per_cell=PER_CELL):
     from paper_0904_1543_gb300 import inputs
     cell_of_orb = [c for c in range(3) for _ in range(per_cell)]
-    first = rank * len(cell_of_orb)
+    first = rank_first_orbital(rank, len(cell_of_orb))
     psi = np.concatenate([inputs.orbital(CFG, first + o, SIZES[c])
                           for o, c in enumerate(cell_of_orb)])
     Vs = [inputs.gaussian_potential(CFG, c, SIZES[c]) for c in range(3)]
@@ -494,14 +515,9 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         # H psi must equal the device-resident result bit for bit
         e2e_ok = bool(torch.equal(hp_pin, hp.cpu()))
 
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
-
-    norb_total = len(cell_of_orb) * world
-    value = norb_total * args.steps / (ms * 1e-3)
-    value_e2e = norb_total * args.steps / (ms_e2e * 1e-3)
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], dist, world, dev)
+    value = job_throughput(len(cell_of_orb), world, args.steps, ms)
+    value_e2e = job_throughput(len(cell_of_orb), world, args.steps, ms_e2e)
 
     # roofline of the dominant kernel (kinetic pass, 3 launches per step)
     kin_ms, kin_launches = prof["kinetic"]
