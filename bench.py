@@ -437,12 +437,15 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     V_pin = [torch.from_numpy(v).pin_memory() for v in Vs_h]
     occ_pin = torch.from_numpy(occ_h).pin_memory()
     hp_pin = torch.empty(psi_h.shape, dtype=tdt).pin_memory()
-    ek_pin = torch.empty(len(cell_of_orb), dtype=torch.float64).pin_memory()
-    ep_pin = torch.empty_like(ek_pin)
+    # the per-orbital energies travel in one 1 MiB buffer: on this system
+    # device-to-host copies of a few KB block the host until the stream
+    # drains, which would serialise the pipeline below
+    nen = max(2 * len(cell_of_orb), 1 << 17)
+    en_pin = torch.empty(nen, dtype=torch.float64).pin_memory()
     rho_pin = [torch.empty(c.fine, dtype=torch.float64).pin_memory() for c in cells]
     es = psi_pin.element_size()
     h2d = psi_pin.numel() * es + sum(v.numel() * es for v in V_pin) + occ_pin.numel() * 8
-    d2h = hp_pin.numel() * es + 2 * ek_pin.numel() * 8 + sum(r.numel() * 8 for r in rho_pin)
+    d2h = hp_pin.numel() * es + en_pin.numel() * 8 + sum(r.numel() * 8 for r in rho_pin)
 
     # Pipelined steps: copies in on one stream, the plan on the compute
     # stream, copies out on a third; two device buffer sets (each with its
@@ -458,18 +461,20 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         sets = []
         for k in range(2):
             if k == 0:
-                bp, bpsi, bhp, bek, bep, brho, bV, bocc = plan, psi, hp, ek, ep, rho, V, occ
+                bp, bpsi, bhp, brho, bV, bocc = plan, psi, hp, rho, V, occ
             else:
                 bp = W.Plan(cells, cell_of_orb, prec=W.WVL_F32 if f32 else W.WVL_F64,
                             graph=True, autotune=not args.no_autotune)
                 bpsi, bhp = torch.empty_like(psi), torch.empty_like(hp)
-                bek, bep = torch.empty_like(ek), torch.empty_like(ep)
                 brho = [torch.empty_like(r) for r in rho]
                 bV = [torch.empty_like(v) for v in V]
                 bocc = torch.empty_like(occ)
                 if not args.no_autotune:
                     bp.autotune(psi, V, occ, hpsi=bhp, rho=brho)
-            sets.append(dict(plan=bp, psi=bpsi, hp=bhp, ek=bek, ep=bep, rho=brho, V=bV, occ=bocc,
+            ben = torch.zeros(nen, dtype=torch.float64, device=dev)
+            no = len(cell_of_orb)
+            sets.append(dict(plan=bp, psi=bpsi, hp=bhp, en=ben, ek=ben[:no], ep=ben[no:2 * no],
+                             rho=brho, V=bV, occ=bocc,
                              ev_in=torch.cuda.Event(), ev_comp=torch.cuda.Event(),
                              ev_out=torch.cuda.Event()))
         for b in sets:
@@ -493,8 +498,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
             s_out.wait_event(b["ev_comp"])
             with torch.cuda.stream(s_out):
                 hp_pin.copy_(b["hp"], non_blocking=True)
-                ek_pin.copy_(b["ek"], non_blocking=True)
-                ep_pin.copy_(b["ep"], non_blocking=True)
+                en_pin.copy_(b["en"], non_blocking=True)
                 for r, rp in zip(b["rho"], rho_pin):
                     rp.copy_(r, non_blocking=True)
             b["ev_out"].record(s_out)
