@@ -159,7 +159,7 @@ static bool tune_valid(const PassCall<T>& c, const Tune& t) {
             return false;
         if (c.mode == M_POT) {
             const int nslots = (NTHREADS / 32) * (32 / t.LT);
-            const int cpt = POT_OUT / t.R;
+            const int cpt = pot_out<T>() / t.R;
             if ((long long)cpt * nslots < (n + t.R - 1) / t.R) return false;
         }
     }

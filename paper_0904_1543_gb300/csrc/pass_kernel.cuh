@@ -253,7 +253,7 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
     const int slot = warp * spw + lane / LT;
     const int nslots = NWARPS * spw;
     constexpr bool KM = (MODE == M_KMID || MODE == M_KLAST);
-    constexpr int CPT = (MODE == M_POT) ? POT_OUT / R : 1;
+    constexpr int CPT = (MODE == M_POT) ? pot_out<T>() / R : 1;
 
     Job cur = make_job<T, MODE>(p, blockIdx.x);
     if (!cur.valid) return;

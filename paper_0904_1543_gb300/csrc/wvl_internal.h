@@ -36,7 +36,10 @@ enum Mode {
 
 constexpr int MAXSEG = 8;      // cells (segments) per launch
 constexpr int NTHREADS = 128;  // threads per CTA (4 warps)
-constexpr int POT_OUT = 32;    // register-resident rho outputs per thread (M_POT)
+// register-resident density outputs per thread in M_POT: 32 FP64 sums, or 16
+// compensated FP32 pairs (keeps the FP32 kernel at <= 128 registers)
+template <typename T>
+__host__ __device__ constexpr int pot_out() { return sizeof(T) == 8 ? 32 : 16; }
 constexpr int MAX_FINE = 1024; // largest fine extent of one axis
 
 // One cell's orbitals inside one pass launch.  Element offsets are per
