@@ -202,6 +202,19 @@ wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void
  * periodic operator on that padded cell, restricted to the box, is the
  * free-space operator exactly; that is how it is computed. */
 #define WVL_FREE_PAD 8
+/* Mixed conditions: free_axes (HOST int[3], x y z) = 1 for a free axis, 0 for
+ * a periodic one; padding (and the extent of V and rho) grows only along the
+ * free axes.  One free axis = the surface (slab) conditions of the CPU code;
+ * three = wvl_hpsi_local_free; none = wvl_hpsi_local. */
+wvl_status wvl_bc_workspace_size(const wvl_grid* grid, const int* free_axes, int prec,
+                                 int norb, size_t* bytes);
+wvl_status wvl_hpsi_local_bc(const wvl_grid* grid, const int* free_axes, int prec, int norb,
+                             const void* psi_c, const void* V, const double* occ,
+                             void* hpsi_c, double* rho, double* ekin, double* epot,
+                             void* ws, size_t ws_bytes, void* stream);
+wvl_status wvl_density_bc(const wvl_grid* grid, const int* free_axes, int prec, int norb,
+                          const void* psi_c, const double* occ, double* rho,
+                          void* ws, size_t ws_bytes, void* stream);
 wvl_status wvl_free_workspace_size(const wvl_grid* grid, int prec, int norb, size_t* bytes);
 wvl_status wvl_hpsi_local_free(const wvl_grid* grid, int prec, int norb, const void* psi_c,
                                const void* V, const double* occ, void* hpsi_c, double* rho,

@@ -108,3 +108,87 @@ def restrict(A_ext, pad_fine):
     o = E - pad_fine
     sz = [A_ext.shape[k] - 2 * o for k in range(3)]
     return A_ext[o:o + sz[0], o:o + sz[1], o:o + sz[2]]
+
+
+# --------------------------------------------------------------------------
+# mixed conditions: each axis periodic (circulant on 2n points) or free
+# --------------------------------------------------------------------------
+def mat_synthesis_periodic(nc):
+    """(2 nc) x (2 nc): s_i = sum_j h_{i-2j} c_j + g_{i-2j} d_j, i mod 2 nc."""
+    h, g = F.h(), F.g()
+    N = 2 * nc
+    A = np.zeros((N, N))
+    for j in range(nc):
+        for t in range(F.NTAP):
+            k = F.J_LO + t
+            A[(2 * j + k) % N, 2 * j] += h[t]
+            A[(2 * j + k) % N, 2 * j + 1] += g[t]
+    return A
+
+
+def mat_conv_periodic(N, taps, shifts):
+    A = np.zeros((N, N))
+    for I in range(N):
+        for c, k in zip(taps, shifts):
+            A[I, (I - k) % N] += c
+    return A
+
+
+def _axis_mats(nc, free, hg):
+    """(synthesis, magic filter, kinetic) matrices of one axis."""
+    w, k0 = F.magic()
+    a = F.kinetic_a()
+    if free:
+        return mat_synthesis(nc), mat_mf(nc), mat_kin(nc, hg)
+    N = 2 * nc
+    return (mat_synthesis_periodic(nc), mat_conv_periodic(N, w, k0 + np.arange(16)),
+            mat_conv_periodic(N, -a / (2 * hg * hg), np.arange(-14, 15)))
+
+
+def hpsi_local_bc(psi_c, V_ext, occ, n, free_axes, hgrid=(0.25, 0.25, 0.25)):
+    """Local Hamiltonian with per-axis conditions (free_axes[d] = 1: free).
+    V_ext and rho span [-E, 2n + E) along free axes, [0, 2n) along periodic
+    ones."""
+    X = W.uncompress(psi_c, n)
+    M = [_axis_mats(n[d], free_axes[d], hgrid[d]) for d in range(3)]
+    S = [m[0] for m in M]
+    Mf = [m[1] for m in M]
+    s = _apply(S, X)
+    psir = _apply(Mf, s)
+    y = _apply([m.T for m in Mf], V_ext * psir)
+    kin = np.zeros_like(s)
+    for ax in range(3):
+        mats = [np.eye(s.shape[2]), np.eye(s.shape[1]), np.eye(s.shape[0])]
+        mats[ax] = M[ax][2]
+        kin += _apply(mats, s)
+    out = _apply([m.T for m in S], y + kin)
+    return {"hpsi_c": W.compress(out, n), "rho": occ * psir * psir,
+            "epot": float(np.sum(V_ext * psir * psir)), "ekin": float(np.sum(s * kin))}
+
+
+def extend_bc(V_pad, n, pad_fine, free_axes):
+    """Potential on the padded cell (pad_fine fine points per side along free
+    axes) -> the oracle's grid (extended by E along free axes)."""
+    shp, sl = [], []
+    for ax, d in enumerate((2, 1, 0)):
+        if free_axes[d]:
+            shp.append(2 * n[d] + 2 * E)
+            o = E - pad_fine
+            sl.append(slice(o, o + V_pad.shape[ax]))
+        else:
+            shp.append(2 * n[d])
+            sl.append(slice(0, 2 * n[d]))
+    Vx = np.zeros(shp)
+    Vx[tuple(sl)] = V_pad
+    return Vx
+
+
+def restrict_bc(A_ext, n, pad_fine, free_axes):
+    sl = []
+    for ax, d in enumerate((2, 1, 0)):
+        if free_axes[d]:
+            o = E - pad_fine
+            sl.append(slice(o, A_ext.shape[ax] - o))
+        else:
+            sl.append(slice(None))
+    return A_ext[tuple(sl)]

@@ -599,3 +599,44 @@ def density_free(psi_c, occ, grid: Grid, rho=None):
     _check(L.wvl_density_free(ctypes.byref(grid.c()), prec, norb, psi_c.data_ptr(),
                               occ.data_ptr(), rho.data_ptr(), ws, wsb, st))
     return rho
+
+
+def bc_fine(grid: Grid, free_axes):
+    """(N3, N2, N1) of V and rho for per-axis free (1) / periodic (0) conditions."""
+    fa = tuple(int(v) for v in free_axes)
+    return tuple(2 * (grid.n[d] + (2 * FREE_PAD if fa[d] else 0)) for d in (2, 1, 0))
+
+
+def hpsi_local_bc(psi_c, V, occ, grid: Grid, free_axes, rho=None, out=None):
+    """Local Hamiltonian with per-axis conditions: free_axes = (x, y, z), 1 =
+    free (isolated), 0 = periodic; one free axis gives surface conditions.
+    V and rho on bc_fine(grid, free_axes).  Returns (hpsi_c, ekin, epot)."""
+    L = lib()
+    if not getattr(L, "_bc_declared", False):
+        Gp, Ip = ctypes.POINTER(_Grid), ctypes.POINTER(ctypes.c_int)
+        L.wvl_bc_workspace_size.restype = ctypes.c_int
+        L.wvl_bc_workspace_size.argtypes = [Gp, Ip, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(_sz)]
+        L.wvl_hpsi_local_bc.restype = ctypes.c_int
+        L.wvl_hpsi_local_bc.argtypes = [Gp, Ip, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                        _vp, _vp, _vp, _vp, _sz, _vp]
+        L._bc_declared = True
+    fa = (ctypes.c_int * 3)(*[int(v) for v in free_axes])
+    norb = _norb(psi_c, grid.ncoef)
+    out = torch.empty_like(psi_c) if out is None else out
+    ek = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    ep = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
+    for t, nm in ((psi_c, "psi_c"), (V, "V"), (occ, "occ"), (out, "out")):
+        _dev(t, nm)
+    if rho is not None:
+        _dev(rho, "rho")
+    prec = _prec(psi_c)
+    need = _sz(0)
+    _check(L.wvl_bc_workspace_size(ctypes.byref(grid.c()), fa, prec, max(norb, 1),
+                                   ctypes.byref(need)))
+    st = _stream(psi_c.device)
+    ws, wsb = _workspace(need.value, psi_c.device, st)
+    _check(L.wvl_hpsi_local_bc(ctypes.byref(grid.c()), fa, prec, norb, psi_c.data_ptr(),
+                               V.data_ptr(), occ.data_ptr(), out.data_ptr(), _p(rho),
+                               ek.data_ptr(), ep.data_ptr(), ws, wsb, st))
+    return out, ek, ep

@@ -296,8 +296,8 @@ struct CellRun {
     const int* mapf = nullptr;
     long long clen = 0;            // region: compressed length per orbital
     long long ncoarse = 0;         // region: stored scaling coefficients
-    int bx[3] = {0, 0, 0};         // free BC: box extents inside the padded cell
-    int boff = 0;                  // free BC: padding (coarse points per side)
+    int bx[3] = {0, 0, 0};         // free/surface BC: box extents inside the padded cell
+    int bo[3] = {0, 0, 0};         // free/surface BC: padding per side along each axis
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -349,7 +349,9 @@ static SegDesc<T> seg_for(const CellRun<T>& c, const T* in, T* out) {
     d.s.bx1 = c.bx[0];
     d.s.bx2 = c.bx[1];
     d.s.bx3 = c.bx[2];
-    d.s.boff = c.boff;
+    d.s.bo1 = c.bo[0];
+    d.s.bo2 = c.bo[1];
+    d.s.bo3 = c.bo[2];
     for (int k = 0; k < 3; ++k) d.Nf[k] = c.Nf[k];
     return d;
 }
@@ -710,28 +712,29 @@ static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void
     return run_op<T>(op, runs, nullptr, nullptr, static_cast<cudaStream_t>(stream));
 }
 
-// ------------------------------------------------------- free boundaries
-// Free (isolated) boundary conditions: the orbital lives on the coarse points
-// of the box; every operator acts on the whole space.  The interaction range
-// of H is 15 coarse points (synthesis 8 + magic filter 8 fine points out,
-// then back), so the periodic operator on a cell padded by FREE_PAD >= 8
-// coarse points per side, restricted to the box, is the free-space operator
-// exactly; V and rho cover the padded cell.
+// -------------------------------------------------- free / surface boundaries
+// Free (isolated) boundary conditions along an axis: the orbital lives on the
+// coarse points of the box; every operator acts on the whole line.  The
+// interaction range of H is 15 coarse points (synthesis 8 + magic filter 8
+// fine points out, then back), so the periodic operator on a cell padded by
+// FREE_PAD >= 8 coarse points per side along each free axis, restricted to
+// the box, is the free-space operator exactly; V and rho cover the padded
+// cell.  Surface conditions: one free axis, two periodic.
 constexpr int FREE_PAD = WVL_FREE_PAD;
 
-static void padded_grid(const wvl_grid* g, wvl_grid* out) {
+static void padded_grid(const wvl_grid* g, const int fa[3], wvl_grid* out) {
     *out = *g;
-    out->n1 += 2 * FREE_PAD;
-    out->n2 += 2 * FREE_PAD;
-    out->n3 += 2 * FREE_PAD;
+    out->n1 += fa[0] ? 2 * FREE_PAD : 0;
+    out->n2 += fa[1] ? 2 * FREE_PAD : 0;
+    out->n3 += fa[2] ? 2 * FREE_PAD : 0;
 }
 
 template <typename T>
-static wvl_status free_cell(int op, const wvl_grid* box, int norb, const void* in, void* out,
-                           const void* V, const double* occ, double* rho, double* ekin,
-                           double* epot, void* ws, size_t ws_bytes, void* stream) {
+static wvl_status bc_cell(int op, const wvl_grid* box, const int fa[3], int norb, const void* in,
+                         void* out, const void* V, const double* occ, double* rho, double* ekin,
+                         double* epot, void* ws, size_t ws_bytes, void* stream) {
     wvl_grid g;
-    padded_grid(box, &g);
+    padded_grid(box, fa, &g);
     CellRun<T> r;
     grid_dims(&g, r.n, r.Nf, r.hg, r.P);
     r.norb = norb;
@@ -745,7 +748,7 @@ static wvl_status free_cell(int op, const wvl_grid* box, int norb, const void* i
     r.bx[0] = box->n1;
     r.bx[1] = box->n2;
     r.bx[2] = box->n3;
-    r.boff = FREE_PAD;
+    for (int d = 0; d < 3; ++d) r.bo[d] = fa[d] ? FREE_PAD : 0;
     r.ncoarse = (long long)box->n1 * box->n2 * box->n3;
     r.clen = 8 * r.ncoarse;
     const size_t need = run_ws_bytes(r.Nf, norb, sizeof(T));
@@ -1115,32 +1118,36 @@ wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void
                               static_cast<float*>(x), rr, ws, ws_bytes, st);
 }
 
-// -------------------------------------------------------- free boundaries
-wvl_status wvl_free_workspace_size(const wvl_grid* grid, int prec, int norb, size_t* bytes) {
-    g_err[0] = 0;
-    WVL_TRY(check_grid(grid));
-    wvl_grid g;
-    padded_grid(grid, &g);
-    WVL_TRY(check_grid(&g));
-    return wvl_workspace_size(&g, prec, norb, bytes);
-}
+// ------------------------------------------------- free / surface boundaries
+static const int kAllFree[3] = {1, 1, 1};
 
-static wvl_status free_checks(const wvl_grid* grid, int prec, int norb) {
+static wvl_status bc_checks(const wvl_grid* grid, const int* fa, int prec, int norb) {
     g_err[0] = 0;
+    if (!fa) return fail(WVL_EINVAL, "free_axes is NULL");
+    for (int d = 0; d < 3; ++d)
+        if (fa[d] != 0 && fa[d] != 1) return fail(WVL_EINVAL, "free_axes[%d] must be 0 or 1", d);
     WVL_TRY(check_grid(grid));
     WVL_TRY(check_prec(prec));
     wvl_grid g;
-    padded_grid(grid, &g);
+    padded_grid(grid, fa, &g);
     WVL_TRY(check_grid(&g));
     if (norb < 0) return fail(WVL_EINVAL, "norb < 0");
     return WVL_OK;
 }
 
-wvl_status wvl_hpsi_local_free(const wvl_grid* grid, int prec, int norb, const void* psi_c,
-                               const void* V, const double* occ, void* hpsi_c, double* rho,
-                               double* ekin, double* epot, void* ws, size_t ws_bytes,
-                               void* stream) {
-    WVL_TRY(free_checks(grid, prec, norb));
+wvl_status wvl_bc_workspace_size(const wvl_grid* grid, const int* free_axes, int prec, int norb,
+                                 size_t* bytes) {
+    WVL_TRY(bc_checks(grid, free_axes, prec, std::max(norb, 0)));
+    wvl_grid g;
+    padded_grid(grid, free_axes, &g);
+    return wvl_workspace_size(&g, prec, norb, bytes);
+}
+
+wvl_status wvl_hpsi_local_bc(const wvl_grid* grid, const int* free_axes, int prec, int norb,
+                             const void* psi_c, const void* V, const double* occ, void* hpsi_c,
+                             double* rho, double* ekin, double* epot, void* ws, size_t ws_bytes,
+                             void* stream) {
+    WVL_TRY(bc_checks(grid, free_axes, prec, norb));
     if (norb == 0) return WVL_OK;
     WVL_TRY(check_ptr(psi_c, "psi_c", true));
     WVL_TRY(check_ptr(V, "V", true));
@@ -1150,25 +1157,43 @@ wvl_status wvl_hpsi_local_free(const wvl_grid* grid, int prec, int norb, const v
     WVL_TRY(check_ptr(ekin, "ekin", true));
     WVL_TRY(check_ptr(epot, "epot", true));
     if (prec == WVL_F64)
-        return free_cell<double>(OP_HPSI, grid, norb, psi_c, hpsi_c, V, occ, rho, ekin, epot, ws,
-                                 ws_bytes, stream);
-    return free_cell<float>(OP_HPSI, grid, norb, psi_c, hpsi_c, V, occ, rho, ekin, epot, ws,
-                            ws_bytes, stream);
+        return bc_cell<double>(OP_HPSI, grid, free_axes, norb, psi_c, hpsi_c, V, occ, rho, ekin,
+                               epot, ws, ws_bytes, stream);
+    return bc_cell<float>(OP_HPSI, grid, free_axes, norb, psi_c, hpsi_c, V, occ, rho, ekin, epot,
+                          ws, ws_bytes, stream);
 }
 
-wvl_status wvl_density_free(const wvl_grid* grid, int prec, int norb, const void* psi_c,
-                            const double* occ, double* rho, void* ws, size_t ws_bytes,
-                            void* stream) {
-    WVL_TRY(free_checks(grid, prec, norb));
+wvl_status wvl_density_bc(const wvl_grid* grid, const int* free_axes, int prec, int norb,
+                          const void* psi_c, const double* occ, double* rho, void* ws,
+                          size_t ws_bytes, void* stream) {
+    WVL_TRY(bc_checks(grid, free_axes, prec, norb));
     if (norb == 0) return WVL_OK;
     WVL_TRY(check_ptr(psi_c, "psi_c", true));
     WVL_TRY(check_ptr(occ, "occ", true));
     WVL_TRY(check_ptr(rho, "rho", true));
     if (prec == WVL_F64)
-        return free_cell<double>(OP_DENSITY, grid, norb, psi_c, nullptr, nullptr, occ, rho,
-                                 nullptr, nullptr, ws, ws_bytes, stream);
-    return free_cell<float>(OP_DENSITY, grid, norb, psi_c, nullptr, nullptr, occ, rho, nullptr,
-                            nullptr, ws, ws_bytes, stream);
+        return bc_cell<double>(OP_DENSITY, grid, free_axes, norb, psi_c, nullptr, nullptr, occ,
+                               rho, nullptr, nullptr, ws, ws_bytes, stream);
+    return bc_cell<float>(OP_DENSITY, grid, free_axes, norb, psi_c, nullptr, nullptr, occ, rho,
+                          nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+wvl_status wvl_free_workspace_size(const wvl_grid* grid, int prec, int norb, size_t* bytes) {
+    return wvl_bc_workspace_size(grid, kAllFree, prec, norb, bytes);
+}
+
+wvl_status wvl_hpsi_local_free(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                               const void* V, const double* occ, void* hpsi_c, double* rho,
+                               double* ekin, double* epot, void* ws, size_t ws_bytes,
+                               void* stream) {
+    return wvl_hpsi_local_bc(grid, kAllFree, prec, norb, psi_c, V, occ, hpsi_c, rho, ekin, epot,
+                             ws, ws_bytes, stream);
+}
+
+wvl_status wvl_density_free(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                            const double* occ, double* rho, void* ws, size_t ws_bytes,
+                            void* stream) {
+    return wvl_density_bc(grid, kAllFree, prec, norb, psi_c, occ, rho, ws, ws_bytes, stream);
 }
 
 // ------------------------------------------------------ localisation regions

@@ -117,13 +117,14 @@ __device__ __forceinline__ void conv_chunk(const T* __restrict__ srow,
 
 // Position of coarse point (i1, i2, i3) in the stored compressed vector:
 // the scaling coefficient c^0 sits at k, c^mu (mu >= 1) at ncoarse + 7 k + mu - 1;
-// -1 if the point is outside the localisation region or the box of free
-// boundary conditions (whose cell is padded by boff points per side).
+// -1 if the point is outside the localisation region or the box of free /
+// surface boundary conditions (whose cell is padded by bo_d points per side
+// along each free axis d).
 template <typename T>
 __device__ __forceinline__ int stored_index(const Seg<T>& S, long long ci, int i1, int i2,
                                             int i3, int mu) {
     if (S.bx1 > 0) {
-        const int j1 = i1 - S.boff, j2 = i2 - S.boff, j3 = i3 - S.boff;
+        const int j1 = i1 - S.bo1, j2 = i2 - S.bo2, j3 = i3 - S.bo3;
         if ((unsigned)j1 >= (unsigned)S.bx1 || (unsigned)j2 >= (unsigned)S.bx2 ||
             (unsigned)j3 >= (unsigned)S.bx3)
             return -1;

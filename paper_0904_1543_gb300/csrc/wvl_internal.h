@@ -60,8 +60,8 @@ struct Seg {
     const int* mapf;      //   position of c^0 / index k of c^{1..7} (ncoarse + 7k), or -1
     long long clen;       // compressed length of one orbital (orbital stride there)
     long long ncoarse;    // scaling coefficients stored (start of the wavelet block)
-    int bx1, bx2, bx3;    // free boundary conditions: box extents inside the padded
-    int boff;             //   cell and its offset (coarse points); bx1 = 0 otherwise
+    int bx1, bx2, bx3;    // free/surface boundary conditions: box extents inside the
+    int bo1, bo2, bo3;    //   padded cell and its offsets (coarse points); bx1 = 0 otherwise
     long long P;          // elements per orbital
     long long rho_gstride;// M_POT: 0 -> rho += (direct), else group g writes rho[g*stride]
     long long blk0;       // first work unit of the segment in the launch

@@ -46,3 +46,30 @@ def test_hpsi_free(W, n, norb):
     assert np.abs(got - ref).max() < RTOL64 * np.abs(ref).max()
     rho2 = W.density_free(torch.from_numpy(psi).cuda(), torch.from_numpy(occ).cuda(), g)
     assert np.abs(rho2.cpu().numpy() - ref).max() < RTOL64 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("free_axes", [(0, 0, 1), (1, 0, 0), (0, 1, 1), (0, 0, 0)])
+def test_hpsi_mixed_conditions(W, free_axes):
+    """Surface (one free axis) and other mixed conditions against the oracle
+    with per-axis circulant / free-space matrices."""
+    import torch
+    n = (3, 2, 4)
+    g = W.Grid(n, (0.25, 0.3, 0.2))
+    pad = W.FREE_PAD
+    padded = tuple(v + (2 * pad if free_axes[d] else 0) for d, v in enumerate(n))
+    psi = inputs.orbitals(112, 2, n)
+    Vp = inputs.gaussian_potential(112, 0, padded)
+    occ = np.array([2.0, 1.0])
+    rho = torch.zeros(W.bc_fine(g, free_axes), dtype=torch.float64, device="cuda")
+    hp, ek, ep = W.hpsi_local_bc(torch.from_numpy(psi).cuda(), torch.from_numpy(Vp).cuda(),
+                                 torch.from_numpy(occ).cuda(), g, free_axes, rho=rho)
+    Vx = FR.extend_bc(Vp, n, 2 * pad, free_axes)
+    rho_ref = 0.0
+    for o in range(2):
+        r = FR.hpsi_local_bc(psi[o], Vx, occ[o], n, free_axes, g.h)
+        assert np.abs(hp[o].cpu().numpy() - r["hpsi_c"]).max() < RTOL64 * np.abs(r["hpsi_c"]).max()
+        assert abs(float(ek[o]) - r["ekin"]) < RTOL64 * abs(r["ekin"])
+        assert abs(float(ep[o]) - r["epot"]) < RTOL64 * abs(r["epot"])
+        rho_ref = rho_ref + r["rho"]
+    ref = FR.restrict_bc(rho_ref, n, 2 * pad, free_axes)
+    assert np.abs(rho.cpu().numpy() - ref).max() < RTOL64 * np.abs(ref).max()
