@@ -250,7 +250,8 @@ def measure_variants(args, W, torch, dev):
     occ = torch.full((norb,), 2.0, dtype=torch.float64, device=dev)
     psi32, V32 = psi64.float(), V64.float()
     res = {}
-    for name, p, v, prec in (("f32", psi32, V32, W.WVL_F32), ("f64", psi64, V64, W.WVL_F64)):
+    for name, p, v, prec in (("f32", psi32, V32, W.WVL_F32), ("f64", psi64, V64, W.WVL_F64),
+                             ("emu", psi64, V64, W.WVL_F64_EMU)):
         plan = W.Plan([g], [0] * norb, prec=prec, graph=True, autotune=True)
         hp = torch.empty_like(p)
         ek = torch.empty(norb, dtype=torch.float64, device=dev)
@@ -266,6 +267,7 @@ def measure_variants(args, W, torch, dev):
         del plan
     ms32, hp32, ek32, ep32, rho32 = res["f32"]
     ms64, hp64, ek64, ep64, rho64 = res["f64"]
+    mse, hpe, eke, epe, rhoe = res["emu"]
     # oracle on two sampled orbitals (FP64 arithmetic on the FP32-rounded inputs)
     Vh = V32.double().cpu().numpy()
     err_h, err_e = 0.0, 0.0
@@ -290,7 +292,29 @@ def measure_variants(args, W, torch, dev):
         "error_sample": "H psi and energies: orbitals 0 and 255 against the FP64 oracle; "
                         "rho: all 256 orbitals against the FP64 GPU form",
     }
-    del res, hp32, hp64, psi32
+    # FP64-accurate tensor-core form: oracle on the same two orbitals (FP64
+    # inputs), and every orbital against the native FP64 form
+    Vd = V64.cpu().numpy()
+    emu_h, emu_e = 0.0, 0.0
+    for o in (0, norb - 1):
+        r = O.hpsi_local(psi64[o].cpu().numpy(), Vd, 2.0, n)
+        emu_h = max(emu_h, float(np.abs(hpe[o].cpu().numpy() - r["hpsi_c"]).max()
+                                 / np.abs(r["hpsi_c"]).max()))
+        emu_e = max(emu_e, abs(float(eke[o]) - r["ekin"]) / abs(r["ekin"]),
+                    abs(float(epe[o]) - r["epot"]) / abs(r["epot"]))
+    out["fp64_emu_batched"] = {
+        "workload": "256 orbitals, periodic coarse 48^3 (fine 96^3), FP64 arrays; every "
+                    "convolution sum on the FP16 tensor cores (six 10-bit digits per operand, "
+                    "exact FP32 partial sums, 64-bit recombination), one graph-captured plan",
+        "value": norb / (mse * 1e-3), "unit": UNIT, "ms_per_step": mse,
+        "speedup_over_fp64": ms64 / mse,
+        "rel_err_hpsi_vs_oracle": emu_h, "rel_err_energies_vs_oracle": emu_e,
+        "rel_diff_hpsi_vs_fp64_gpu": float((hpe - hp64).abs().max() / hp64.abs().max()),
+        "rel_diff_rho_vs_fp64_gpu": float((rhoe - rho64).abs().max() / rho64.abs().max()),
+        "error_sample": "oracle: orbitals 0 and 255; FP64 GPU form: all 256 orbitals",
+        "timeouts": W.wait_timeouts(),
+    }
+    del res, hp32, hp64, hpe, psi32
     # ---- preconditioner: 5 PCG iterations of the Helmholtz equation, FP64,
     # the same 256 orbitals of coarse 48^3 (eps_o in [-1.5, -0.2])
     eps = -torch.linspace(0.2, 1.5, norb, dtype=torch.float64, device=dev)
@@ -375,11 +399,13 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     WL = workload(args.per_cell)
     cells = [W.Grid(s) for s in SIZES]
     f32 = args.prec == "f32"     # FP32 form of the same workload (profiling)
+    emu = args.prec == "f64emu"  # FP64-accurate tensor-core form (profiling)
+    pcode = W.WVL_F32 if f32 else (W.WVL_F64_EMU if emu else W.WVL_F64)
     tdt = torch.float32 if f32 else torch.float64
     if f32:
         psi_h = psi_h.astype(np.float32)
         Vs_h = [v.astype(np.float32) for v in Vs_h]
-    plan = W.Plan(cells, cell_of_orb, prec=W.WVL_F32 if f32 else W.WVL_F64, graph=True,
+    plan = W.Plan(cells, cell_of_orb, prec=pcode, graph=True,
                   autotune=not args.no_autotune)
     psi = torch.from_numpy(psi_h).to(dev)
     V = [torch.from_numpy(v).to(dev) for v in Vs_h]
@@ -463,7 +489,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
             if k == 0:
                 bp, bpsi, bhp, brho, bV, bocc = plan, psi, hp, rho, V, occ
             else:
-                bp = W.Plan(cells, cell_of_orb, prec=W.WVL_F32 if f32 else W.WVL_F64,
+                bp = W.Plan(cells, cell_of_orb, prec=pcode,
                             graph=True, autotune=not args.no_autotune)
                 bpsi, bhp = torch.empty_like(psi), torch.empty_like(hp)
                 brho = [torch.empty_like(r) for r in rho]
@@ -532,7 +558,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     # DRAM bytes of one kinetic pass-1 launch from an ncu capture of the small
     # profiling case (profiles/kinetic_pass_fp64_small36.md), scaled to this
     # launch by the fine points processed; null for any other workload.
-    traffic = (1031.3e6 * pts / 33619968) if (args.per_cell == PER_CELL and not f32) else None
+    traffic = (1031.3e6 * pts / 33619968) if (args.per_cell == PER_CELL and args.prec == "f64") else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                 "traffic": traffic, "kernel": "kinetic 1D pass (FP64 DFMA pipe)",
@@ -542,7 +568,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if f32 else "f64",
+        "dtype": "f32" if f32 else ("f64 (f16-digit tensor-core emulation)" if emu else "f64"),
         "data": "synthetic", "config": WL,
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "pipelined": "copies in / plan / copies out on "
@@ -554,7 +580,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         "clocks": clk,
         "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
     }
-    if rank == 0 and world == 1 and not args.no_variants and not f32:
+    if rank == 0 and world == 1 and not args.no_variants and args.prec == "f64":
         line["variants"] = measure_variants(args, W, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         off = offsets_of(cell_of_orb)
@@ -582,8 +608,9 @@ def main():
                     help="orbitals per cell (64 = the benchmark workload; smaller for ncu)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--prec", choices=["f64", "f32"], default="f64",
-                    help="f32 runs the FP32 form of the same workload (profiling)")
+    ap.add_argument("--prec", choices=["f64", "f32", "f64emu"], default="f64",
+                    help="f32 / f64emu run the FP32 / tensor-core FP64 form of the same "
+                         "workload (profiling)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32 and autograd forms reported beside the FP64 line")
     args = ap.parse_args()

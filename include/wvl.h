@@ -27,6 +27,15 @@
  *   and potential arrays are float; rho, occ and energies stay double, and
  *   every reduction (rho over orbitals, Ekin, Epot) is carried at least in
  *   compensated single (~48-bit) inside a thread and in double above it.
+ *   WVL_F64_EMU -- arrays as WVL_F64; every 1D convolution sum of the
+ *   passes (Eqs. 1dconvtrans, kinetic1d) is evaluated on the FP16 tensor
+ *   cores instead of the FP64 pipe: operands split into six signed 10-bit
+ *   digits on a per-line (data) and per-filter (taps) power-of-two scale,
+ *   digit products summed exactly in FP32 accumulators, recombined in
+ *   64-bit integers.  The error per convolution is below 2^-52 of
+ *   max|f| max|x| over the line (the order of FP64 rounding); pointwise
+ *   steps and reductions are FP64.  All entry points that take `prec`
+ *   accept it; the preconditioner's CG vector updates stay FP64.
  * Memory: every data pointer is DEVICE memory owned by the caller and must be
  *   16-byte aligned; the library allocates nothing on these calls.  Scratch
  *   space is the caller's workspace `ws` of `ws_bytes` bytes, at least
@@ -58,7 +67,7 @@ typedef enum {
     WVL_EUNSUPPORTED = 5   /* size or option outside what is implemented  */
 } wvl_status;
 
-typedef enum { WVL_F64 = 0, WVL_F32 = 1 } wvl_prec;
+typedef enum { WVL_F64 = 0, WVL_F32 = 1, WVL_F64_EMU = 2 } wvl_prec;
 
 /* Coarse grid and fine spacing h'_d = h_d / 2 (paper Eq. wavefhigh). */
 typedef struct {
@@ -79,6 +88,13 @@ int wvl_device_count(void);
 /* Running count of kernels this library has enqueued in this process: direct
  * launches plus every kernel node of each replayed plan graph. */
 unsigned long long wvl_kernel_launches(void);
+
+/* Bounded device-side waits that gave up since the previous call (the
+ * tensor-core passes of WVL_F64_EMU wait on their MMAs for at most ~2 s;
+ * on expiry the kernel stops, leaves its outputs incomplete and counts it
+ * here).  Synchronises the current device.  No counterpart in the paper.
+ * Returns WVL_ETIMEOUT when the count is nonzero, WVL_OK otherwise. */
+wvl_status wvl_wait_timeouts(unsigned* count);
 
 /*
  * Filters derived by the library (host computation, no GPU needed), FP64.

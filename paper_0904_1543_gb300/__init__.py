@@ -24,10 +24,10 @@ from . import _build
 __all__ = [
     "WvlError", "Grid", "lib", "filters", "workspace_size", "synthesis", "analysis",
     "magicfilter", "magicfilter_T", "kinetic", "density", "hpsi_local", "energy",
-    "Plan", "ELoc", "device_count",
+    "Plan", "ELoc", "device_count", "wait_timeouts", "WVL_F64", "WVL_F32", "WVL_F64_EMU",
 ]
 
-WVL_F64, WVL_F32 = 0, 1
+WVL_F64, WVL_F32, WVL_F64_EMU = 0, 1, 2
 WVL_PLAN_GRAPH, WVL_PLAN_AUTOTUNE = 1, 2
 WVL_NSTAGE = 6
 STAGES = ("synthesis", "magicfilter+potential", "magicfilter_T", "kinetic", "analysis",
@@ -77,6 +77,7 @@ def _declare(L):
         "wvl_version": (ctypes.c_int, []),
         "wvl_device_count": (ctypes.c_int, []),
         "wvl_kernel_launches": (ctypes.c_ulonglong, []),
+        "wvl_wait_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
         "wvl_filters": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
         "wvl_workspace_size": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_sz)]),
         "wvl_synthesis": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
@@ -140,6 +141,16 @@ def kernel_launches():
     return lib().wvl_kernel_launches()
 
 
+def wait_timeouts():
+    """Bounded device-side waits (tensor-core passes) that gave up since the
+    previous call; synchronises the device.  0 on a healthy run."""
+    c = ctypes.c_uint(0)
+    st = lib().wvl_wait_timeouts(ctypes.byref(c))
+    if st not in (0, 4):
+        _check(st)
+    return c.value
+
+
 def filters():
     """The library's own filters: h, g (16), w (16) with k0, a (29)."""
     import numpy as np
@@ -150,7 +161,13 @@ def filters():
     return {"h": h, "g": g, "w": w, "k0": k0.value, "a": a}
 
 
-def _prec(t):
+def _prec(t, emu=False):
+    """WVL_F64 / WVL_F32 from the dtype; emu=True selects WVL_F64_EMU (float64
+    arrays, convolution sums on the tensor cores)."""
+    if emu:
+        if t.dtype != torch.float64:
+            raise TypeError("emu=True needs float64 arrays")
+        return WVL_F64_EMU
     if t.dtype == torch.float64:
         return WVL_F64
     if t.dtype == torch.float32:
@@ -208,41 +225,41 @@ def _run(fn, grid, prec, norb, device, *ptrs):
     _check(fn(ctypes.byref(grid.c()), prec, norb, *ptrs, ws, wsb, st))
 
 
-def synthesis(psi_c, grid: Grid, out=None):
+def synthesis(psi_c, grid: Grid, out=None, emu=False):
     """Steps 1)+2): compressed coefficients -> fine scaling coefficients."""
     norb = _norb(psi_c, grid.ncoef)
     out = torch.empty((norb, *grid.fine), dtype=psi_c.dtype, device=psi_c.device) if out is None else out
     _dev(psi_c, "psi_c"), _dev(out, "out")
-    _run(lib().wvl_synthesis, grid, _prec(psi_c), norb, psi_c.device, psi_c.data_ptr(), out.data_ptr())
+    _run(lib().wvl_synthesis, grid, _prec(psi_c, emu), norb, psi_c.device, psi_c.data_ptr(), out.data_ptr())
     return out
 
 
-def analysis(z, grid: Grid, out=None):
+def analysis(z, grid: Grid, out=None, emu=False):
     """Steps 6)+7): fine -> compressed (transpose of synthesis)."""
     norb = _norb(z, grid.ncoef)
     out = torch.empty((norb, grid.ncoef), dtype=z.dtype, device=z.device) if out is None else out
     _dev(z, "z"), _dev(out, "out")
-    _run(lib().wvl_analysis, grid, _prec(z), norb, z.device, z.data_ptr(), out.data_ptr())
+    _run(lib().wvl_analysis, grid, _prec(z, emu), norb, z.device, z.data_ptr(), out.data_ptr())
     return out
 
 
-def magicfilter(s, grid: Grid, out=None):
+def magicfilter(s, grid: Grid, out=None, emu=False):
     norb = _norb(s, grid.ncoef)
     out = torch.empty_like(s) if out is None else out
     _dev(s, "s"), _dev(out, "out")
-    _run(lib().wvl_magicfilter, grid, _prec(s), norb, s.device, s.data_ptr(), out.data_ptr())
+    _run(lib().wvl_magicfilter, grid, _prec(s, emu), norb, s.device, s.data_ptr(), out.data_ptr())
     return out
 
 
-def magicfilter_T(y, grid: Grid, out=None):
+def magicfilter_T(y, grid: Grid, out=None, emu=False):
     norb = _norb(y, grid.ncoef)
     out = torch.empty_like(y) if out is None else out
     _dev(y, "y"), _dev(out, "out")
-    _run(lib().wvl_magicfilter_T, grid, _prec(y), norb, y.device, y.data_ptr(), out.data_ptr())
+    _run(lib().wvl_magicfilter_T, grid, _prec(y, emu), norb, y.device, y.data_ptr(), out.data_ptr())
     return out
 
 
-def kinetic(s, grid: Grid, k0=None, out=None, want_ekin=True):
+def kinetic(s, grid: Grid, k0=None, out=None, want_ekin=True, emu=False):
     """out = K0 + (-1/2 Lap) s and ekin[o] = <s_o, -1/2 Lap s_o>."""
     norb = _norb(s, grid.ncoef)
     out = torch.empty_like(s) if out is None else out
@@ -250,22 +267,22 @@ def kinetic(s, grid: Grid, k0=None, out=None, want_ekin=True):
     _dev(s, "s"), _dev(out, "out")
     if k0 is not None:
         _dev(k0, "k0")
-    _run(lib().wvl_kinetic, grid, _prec(s), norb, s.device, s.data_ptr(), _p(k0),
+    _run(lib().wvl_kinetic, grid, _prec(s, emu), norb, s.device, s.data_ptr(), _p(k0),
          out.data_ptr(), _p(ek))
     return out, ek
 
 
-def density(psi_c, occ, grid: Grid, rho=None):
+def density(psi_c, occ, grid: Grid, rho=None, emu=False):
     """rho += sum_o occ_o |psi_r,o|^2 (float64, (N3, N2, N1))."""
     norb = _norb(psi_c, grid.ncoef)
     rho = torch.zeros(grid.fine, dtype=torch.float64, device=psi_c.device) if rho is None else rho
     _dev(psi_c, "psi_c"), _dev(occ, "occ"), _dev(rho, "rho")
-    _run(lib().wvl_density, grid, _prec(psi_c), norb, psi_c.device, psi_c.data_ptr(),
+    _run(lib().wvl_density, grid, _prec(psi_c, emu), norb, psi_c.device, psi_c.data_ptr(),
          occ.data_ptr(), rho.data_ptr())
     return rho
 
 
-def hpsi_local(psi_c, V, occ, grid: Grid, rho=None, out=None):
+def hpsi_local(psi_c, V, occ, grid: Grid, rho=None, out=None, emu=False):
     """H_loc psi for norb orbitals of one cell; rho += density if given.
     Returns (hpsi_c, ekin, epot)."""
     norb = _norb(psi_c, grid.ncoef)
@@ -276,12 +293,12 @@ def hpsi_local(psi_c, V, occ, grid: Grid, rho=None, out=None):
         _dev(t, nm)
     if rho is not None:
         _dev(rho, "rho")
-    _run(lib().wvl_hpsi_local, grid, _prec(psi_c), norb, psi_c.device, psi_c.data_ptr(),
+    _run(lib().wvl_hpsi_local, grid, _prec(psi_c, emu), norb, psi_c.device, psi_c.data_ptr(),
          V.data_ptr(), occ.data_ptr(), out.data_ptr(), _p(rho), ek.data_ptr(), ep.data_ptr())
     return out, ek, ep
 
 
-def energy(psi_c, V, occ, grid: Grid, rho=None):
+def energy(psi_c, V, occ, grid: Grid, rho=None, emu=False):
     """Per-orbital (ekin, epot) without H psi; rho += density if given."""
     norb = _norb(psi_c, grid.ncoef)
     ek = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
@@ -290,7 +307,7 @@ def energy(psi_c, V, occ, grid: Grid, rho=None):
         _dev(t, nm)
     if rho is not None:
         _dev(rho, "rho")
-    _run(lib().wvl_energy, grid, _prec(psi_c), norb, psi_c.device, psi_c.data_ptr(),
+    _run(lib().wvl_energy, grid, _prec(psi_c, emu), norb, psi_c.device, psi_c.data_ptr(),
          V.data_ptr(), occ.data_ptr(), _p(rho), ek.data_ptr(), ep.data_ptr())
     return ek, ep
 
@@ -401,7 +418,7 @@ class ELoc(torch.autograd.Function):
         return gpsi, gV, None, None
 
 
-def precondition(g, eps, grid: Grid, ncg=5, x=None, want_residual=True):
+def precondition(g, eps, grid: Grid, ncg=5, x=None, want_residual=True, emu=False):
     """ncg iterations of preconditioned CG for (S^T (-1/2 Lap - eps_o) S) x = g
     per orbital (the preconditioning step).  g: (norb, 8 n1 n2 n3); eps:
     float64 (norb,) on the device, each < 0.  Returns (x, |g - A x|^2)."""
@@ -419,7 +436,7 @@ def precondition(g, eps, grid: Grid, ncg=5, x=None, want_residual=True):
         L.wvl_precondition.argtypes = [Gp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int,
                                        _vp, _vp, _vp, _sz, _vp]
         L._pc_declared = True
-    prec = _prec(g)
+    prec = _prec(g, emu)
     need = _sz(0)
     _check(L.wvl_precondition_workspace_size(ctypes.byref(grid.c()), prec, max(norb, 1),
                                              ctypes.byref(need)))
@@ -494,34 +511,34 @@ def _run_region(name, grid, region, prec, norb, device, *ptrs):
                             *ptrs, ws, wsb, st))
 
 
-def synthesis_region(psi_c, grid: Grid, region: Region, out=None):
+def synthesis_region(psi_c, grid: Grid, region: Region, out=None, emu=False):
     norb = _norb(psi_c, region.clen) if region.clen else 0
     out = torch.empty((norb, *grid.fine), dtype=psi_c.dtype, device=psi_c.device) if out is None else out
     _dev(psi_c, "psi_c"), _dev(out, "out")
-    _run_region("wvl_synthesis_region", grid, region, _prec(psi_c), norb, psi_c.device,
+    _run_region("wvl_synthesis_region", grid, region, _prec(psi_c, emu), norb, psi_c.device,
                 psi_c.data_ptr(), out.data_ptr())
     return out
 
 
-def analysis_region(z, grid: Grid, region: Region, out=None):
+def analysis_region(z, grid: Grid, region: Region, out=None, emu=False):
     norb = _norb(z, grid.ncoef)
     out = torch.empty((norb, region.clen), dtype=z.dtype, device=z.device) if out is None else out
     _dev(z, "z"), _dev(out, "out")
-    _run_region("wvl_analysis_region", grid, region, _prec(z), norb, z.device, z.data_ptr(),
+    _run_region("wvl_analysis_region", grid, region, _prec(z, emu), norb, z.device, z.data_ptr(),
                 out.data_ptr())
     return out
 
 
-def density_region(psi_c, occ, grid: Grid, region: Region, rho=None):
+def density_region(psi_c, occ, grid: Grid, region: Region, rho=None, emu=False):
     norb = occ.numel()
     rho = torch.zeros(grid.fine, dtype=torch.float64, device=psi_c.device) if rho is None else rho
     _dev(psi_c, "psi_c"), _dev(occ, "occ"), _dev(rho, "rho")
-    _run_region("wvl_density_region", grid, region, _prec(psi_c), norb, psi_c.device,
+    _run_region("wvl_density_region", grid, region, _prec(psi_c, emu), norb, psi_c.device,
                 psi_c.data_ptr(), occ.data_ptr(), rho.data_ptr())
     return rho
 
 
-def hpsi_local_region(psi_c, V, occ, grid: Grid, region: Region, rho=None, out=None):
+def hpsi_local_region(psi_c, V, occ, grid: Grid, region: Region, rho=None, out=None, emu=False):
     norb = occ.numel()
     if psi_c.numel() != norb * region.clen:
         raise ValueError("psi_c must hold norb region-compressed orbitals")
@@ -532,7 +549,7 @@ def hpsi_local_region(psi_c, V, occ, grid: Grid, region: Region, rho=None, out=N
         _dev(t, nm)
     if rho is not None:
         _dev(rho, "rho")
-    _run_region("wvl_hpsi_local_region", grid, region, _prec(psi_c), norb, psi_c.device,
+    _run_region("wvl_hpsi_local_region", grid, region, _prec(psi_c, emu), norb, psi_c.device,
                 psi_c.data_ptr(), V.data_ptr(), occ.data_ptr(), out.data_ptr(), _p(rho),
                 ek.data_ptr(), ep.data_ptr())
     return out, ek, ep
@@ -571,7 +588,7 @@ def _free_ws(grid, prec, norb, device):
     return L, ws, wsb, st
 
 
-def hpsi_local_free(psi_c, V, occ, grid: Grid, rho=None, out=None):
+def hpsi_local_free(psi_c, V, occ, grid: Grid, rho=None, out=None, emu=False):
     """Free boundary conditions: psi_c on the coarse points of the box,
     V and rho on free_fine(grid).  Returns (hpsi_c, ekin, epot)."""
     norb = _norb(psi_c, grid.ncoef)
@@ -582,7 +599,7 @@ def hpsi_local_free(psi_c, V, occ, grid: Grid, rho=None, out=None):
         _dev(t, nm)
     if rho is not None:
         _dev(rho, "rho")
-    prec = _prec(psi_c)
+    prec = _prec(psi_c, emu)
     L, ws, wsb, st = _free_ws(grid, prec, norb, psi_c.device)
     _check(L.wvl_hpsi_local_free(ctypes.byref(grid.c()), prec, norb, psi_c.data_ptr(),
                                  V.data_ptr(), occ.data_ptr(), out.data_ptr(), _p(rho),
@@ -590,11 +607,11 @@ def hpsi_local_free(psi_c, V, occ, grid: Grid, rho=None, out=None):
     return out, ek, ep
 
 
-def density_free(psi_c, occ, grid: Grid, rho=None):
+def density_free(psi_c, occ, grid: Grid, rho=None, emu=False):
     norb = _norb(psi_c, grid.ncoef)
     rho = torch.zeros(free_fine(grid), dtype=torch.float64, device=psi_c.device) if rho is None else rho
     _dev(psi_c, "psi_c"), _dev(occ, "occ"), _dev(rho, "rho")
-    prec = _prec(psi_c)
+    prec = _prec(psi_c, emu)
     L, ws, wsb, st = _free_ws(grid, prec, norb, psi_c.device)
     _check(L.wvl_density_free(ctypes.byref(grid.c()), prec, norb, psi_c.data_ptr(),
                               occ.data_ptr(), rho.data_ptr(), ws, wsb, st))
@@ -607,7 +624,7 @@ def bc_fine(grid: Grid, free_axes):
     return tuple(2 * (grid.n[d] + (2 * FREE_PAD if fa[d] else 0)) for d in (2, 1, 0))
 
 
-def hpsi_local_bc(psi_c, V, occ, grid: Grid, free_axes, rho=None, out=None):
+def hpsi_local_bc(psi_c, V, occ, grid: Grid, free_axes, rho=None, out=None, emu=False):
     """Local Hamiltonian with per-axis conditions: free_axes = (x, y, z), 1 =
     free (isolated), 0 = periodic; one free axis gives surface conditions.
     V and rho on bc_fine(grid, free_axes).  Returns (hpsi_c, ekin, epot)."""
@@ -630,7 +647,7 @@ def hpsi_local_bc(psi_c, V, occ, grid: Grid, free_axes, rho=None, out=None):
         _dev(t, nm)
     if rho is not None:
         _dev(rho, "rho")
-    prec = _prec(psi_c)
+    prec = _prec(psi_c, emu)
     need = _sz(0)
     _check(L.wvl_bc_workspace_size(ctypes.byref(grid.c()), fa, prec, max(norb, 1),
                                    ctypes.byref(need)))

@@ -19,6 +19,7 @@
 
 #include "wvl.h"
 #include "wvl_internal.h"
+#include "emu.cuh"
 
 namespace wvl {
 
@@ -139,6 +140,7 @@ template <typename T>
 struct PassCall {
     int kind, mode, pass, stage;
     std::vector<SegDesc<T>> segs;
+    bool emu = false;        // FP64 convolutions on the tensor cores (emu.cuh)
 };
 
 static int rowlen_of(int n, int R, const KindGeom& g) {
@@ -212,16 +214,25 @@ static Tune default_tune(const PassCall<T>& c) {
     return t;
 }
 
+static cudaError_t launch_emu_t(int kind, int mode, const PassParams<double>& p, long long n,
+                               cudaStream_t st) {
+    return launch_pass_emu(kind, mode, p, n, st);
+}
+static cudaError_t launch_emu_t(int, int, const PassParams<float>&, long long, cudaStream_t) {
+    return cudaErrorInvalidValue;
+}
+
 template <typename T>
 static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
     const KindGeom g = kind_geom(c.kind);
+    const bool emu = c.emu;
     size_t i = 0;
     while (i < c.segs.size()) {
         PassParams<T> p;
         std::memset(&p, 0, sizeof p);
         const double hax = c.segs[i].hax;
         fill_taps(p, c.kind, hax);
-        p.LT = tn.LT;
+        p.LT = emu ? emu::M : tn.LT;
         long long blk = 0;
         size_t smem = 0;
         int k = 0;
@@ -231,8 +242,16 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             if (c.kind == K_KIN && i > first && d.hax != hax) break;
             Seg<T>& s = d.s;
             pass_dims(d.Nf, c.pass, s.n, s.N);
-            s.tiles = (s.N + tn.LT - 1) / tn.LT;
-            s.rowlen = rowlen_of(s.n, tn.R, g);
+            if (emu) {
+                // units: 128-line tiles x 32-output windows
+                s.nwin = (s.n + emu::N - 1) / emu::N;
+                s.tiles = (s.N + emu::M - 1) / emu::M * s.nwin;
+                s.rowlen = 0;
+            } else {
+                s.nwin = 1;
+                s.tiles = (s.N + tn.LT - 1) / tn.LT;
+                s.rowlen = rowlen_of(s.n, tn.R, g);
+            }
             long long units = s.norb;
             if (c.mode == M_POT) {
                 const long long want = 4LL * num_sms();
@@ -257,11 +276,16 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             }
             s.blk0 = blk;
             blk += units * s.tiles;
-            smem = std::max(smem, (size_t)tn.LT * s.rowlen);
+            if (!emu) smem = std::max(smem, (size_t)tn.LT * s.rowlen);
             p.seg[k] = s;
         }
         p.nseg = k;
         p.nunits = blk;
+        if (emu) {
+            cudaError_t e = launch_emu_t(c.kind, c.mode, p, blk, st);
+            if (e != cudaSuccess) return cuda_fail(e, "emulated pass launch");
+            continue;
+        }
         // two staging buffers, each rounded to 16 bytes
         const size_t per16 = 16 / sizeof(T);
         p.bufelems = (int)((smem + per16 - 1) / per16 * per16);
@@ -298,13 +322,17 @@ struct CellRun {
     long long ncoarse = 0;         // region: stored scaling coefficients
     int bx[3] = {0, 0, 0};         // free/surface BC: box extents inside the padded cell
     int bo[3] = {0, 0, 0};         // free/surface BC: padding per side along each axis
+    bool emu = false;              // FP64 convolutions on the tensor cores (emu.cuh)
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// partial sums per orbital of the passes that write them (the last axis):
+// tiles of LT_MIN lines, or 128-line tiles x 32-output windows when emulated
 static long long tiles_max(const int Nf[3]) {
     long long N = (long long)Nf[1] * Nf[0];
-    return (N + LT_MIN - 1) / LT_MIN;
+    const long long emu_tiles = (N + emu::M - 1) / emu::M * ((Nf[2] + emu::N - 1) / emu::N);
+    return std::max((N + LT_MIN - 1) / LT_MIN, emu_tiles);
 }
 
 // workspace bytes of one cell run
@@ -361,6 +389,7 @@ static std::vector<PassCall<T>> build_calls(int op, std::vector<CellRun<T>>& run
     std::vector<PassCall<T>> calls;
     auto add = [&](int kind, int mode, int pass, int stage, auto&& make) {
         PassCall<T> c{kind, mode, pass, stage, {}};
+        c.emu = !runs.empty() && runs.front().emu;
         for (auto& r : runs) c.segs.push_back(make(r));
         calls.push_back(std::move(c));
     };
@@ -643,7 +672,8 @@ static wvl_status run_op(int op, std::vector<CellRun<T>>& runs, const TuneTable*
 
 // ------------------------------------------------------------ validation
 static wvl_status check_prec(int prec) {
-    if (prec != WVL_F64 && prec != WVL_F32) return fail(WVL_EINVAL, "prec must be WVL_F64 or WVL_F32");
+    if (prec != WVL_F64 && prec != WVL_F32 && prec != WVL_F64_EMU)
+        return fail(WVL_EINVAL, "prec must be WVL_F64, WVL_F32 or WVL_F64_EMU");
     return WVL_OK;
 }
 static wvl_status check_grid(const wvl_grid* g) {
@@ -685,10 +715,11 @@ template <typename T>
 static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void* in,
                               void* out, const void* V, const double* occ, double* rho,
                               double* ekin, double* epot, void* ws, size_t ws_bytes,
-                              void* stream, const wvl_region* reg) {
+                              void* stream, const wvl_region* reg, bool emu) {
     CellRun<T> r;
     grid_dims(grid, r.n, r.Nf, r.hg, r.P);
     r.norb = norb;
+    r.emu = emu;
     if (reg) {
         r.mapc = reg->coarse_index;
         r.mapf = reg->fine_index;
@@ -732,12 +763,13 @@ static void padded_grid(const wvl_grid* g, const int fa[3], wvl_grid* out) {
 template <typename T>
 static wvl_status bc_cell(int op, const wvl_grid* box, const int fa[3], int norb, const void* in,
                          void* out, const void* V, const double* occ, double* rho, double* ekin,
-                         double* epot, void* ws, size_t ws_bytes, void* stream) {
+                         double* epot, void* ws, size_t ws_bytes, void* stream, bool emu) {
     wvl_grid g;
     padded_grid(box, fa, &g);
     CellRun<T> r;
     grid_dims(&g, r.n, r.Nf, r.hg, r.P);
     r.norb = norb;
+    r.emu = emu;
     r.in = static_cast<const T*>(in);
     r.out = static_cast<T*>(out);
     r.V = static_cast<const T*>(V);
@@ -811,10 +843,11 @@ static size_t precond_ws_bytes(const int Nf[3], int norb, size_t elt) {
 template <typename T>
 static wvl_status run_precond(const wvl_grid* grid, int norb, const T* g, const double* eps,
                               int ncg, T* x, double* rr, void* ws, size_t ws_bytes,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool emu) {
     CellRun<T> r;
     grid_dims(grid, r.n, r.Nf, r.hg, r.P);
     r.norb = norb;
+    r.emu = emu;
     r.eps = eps;
     r.V = nullptr;
     r.rho = nullptr;
@@ -885,11 +918,11 @@ static wvl_status dispatch_single(int op, const wvl_grid* grid, int prec, int no
                                   double* epot, void* ws, size_t ws_bytes, void* stream,
                                   const wvl_region* reg = nullptr) {
     g_err[0] = 0;
-    if (prec == WVL_F64)
+    if (prec != WVL_F32)
         return single_cell<double>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
-                                   ws_bytes, stream, reg);
+                                   ws_bytes, stream, reg, prec == WVL_F64_EMU);
     return single_cell<float>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
-                              ws_bytes, stream, reg);
+                              ws_bytes, stream, reg, false);
 }
 
 static wvl_status check_region(const wvl_grid* grid, const wvl_region* reg) {
@@ -956,6 +989,17 @@ int wvl_version(void) { return 10000; }
 
 unsigned long long wvl_kernel_launches(void) { return g_launches.load(); }
 
+wvl_status wvl_wait_timeouts(unsigned* count) {
+    g_err[0] = 0;
+    if (!count) return fail(WVL_EINVAL, "count is NULL");
+    *count = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    e = emu_take_timeouts(count);
+    if (e != cudaSuccess) return cuda_fail(e, "timeout counter");
+    return *count ? fail(WVL_ETIMEOUT, "%u bounded device waits gave up", *count) : WVL_OK;
+}
+
 int wvl_device_count(void) {
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess) {
@@ -985,7 +1029,7 @@ wvl_status wvl_workspace_size(const wvl_grid* grid, int prec, int norb, size_t* 
     double hg[3];
     long long P;
     grid_dims(grid, n, Nf, hg, P);
-    *bytes = run_ws_bytes(Nf, std::max(norb, 1), prec == WVL_F64 ? 8 : 4);
+    *bytes = run_ws_bytes(Nf, std::max(norb, 1), prec != WVL_F32 ? 8 : 4);
     return WVL_OK;
 }
 
@@ -1096,7 +1140,7 @@ wvl_status wvl_precondition_workspace_size(const wvl_grid* grid, int prec, int n
     double hg[3];
     long long P;
     grid_dims(grid, n, Nf, hg, P);
-    *bytes = precond_ws_bytes(Nf, std::max(norb, 1), prec == WVL_F64 ? 8 : 4);
+    *bytes = precond_ws_bytes(Nf, std::max(norb, 1), prec != WVL_F32 ? 8 : 4);
     return WVL_OK;
 }
 
@@ -1111,11 +1155,12 @@ wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void
     if (ncg < 0 || ncg > 10000) return fail(WVL_EINVAL, "ncg = %d out of range", ncg);
     if (g == x) return fail(WVL_EINVAL, "g and x must not alias");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (prec == WVL_F64)
+    if (prec != WVL_F32)
         return run_precond<double>(grid, norb, static_cast<const double*>(g), eps, ncg,
-                                   static_cast<double*>(x), rr, ws, ws_bytes, st);
+                                   static_cast<double*>(x), rr, ws, ws_bytes, st,
+                                   prec == WVL_F64_EMU);
     return run_precond<float>(grid, norb, static_cast<const float*>(g), eps, ncg,
-                              static_cast<float*>(x), rr, ws, ws_bytes, st);
+                              static_cast<float*>(x), rr, ws, ws_bytes, st, false);
 }
 
 // ------------------------------------------------- free / surface boundaries
@@ -1156,11 +1201,11 @@ wvl_status wvl_hpsi_local_bc(const wvl_grid* grid, const int* free_axes, int pre
     WVL_TRY(check_ptr(rho, "rho", false));
     WVL_TRY(check_ptr(ekin, "ekin", true));
     WVL_TRY(check_ptr(epot, "epot", true));
-    if (prec == WVL_F64)
+    if (prec != WVL_F32)
         return bc_cell<double>(OP_HPSI, grid, free_axes, norb, psi_c, hpsi_c, V, occ, rho, ekin,
-                               epot, ws, ws_bytes, stream);
+                               epot, ws, ws_bytes, stream, prec == WVL_F64_EMU);
     return bc_cell<float>(OP_HPSI, grid, free_axes, norb, psi_c, hpsi_c, V, occ, rho, ekin, epot,
-                          ws, ws_bytes, stream);
+                          ws, ws_bytes, stream, false);
 }
 
 wvl_status wvl_density_bc(const wvl_grid* grid, const int* free_axes, int prec, int norb,
@@ -1171,11 +1216,11 @@ wvl_status wvl_density_bc(const wvl_grid* grid, const int* free_axes, int prec, 
     WVL_TRY(check_ptr(psi_c, "psi_c", true));
     WVL_TRY(check_ptr(occ, "occ", true));
     WVL_TRY(check_ptr(rho, "rho", true));
-    if (prec == WVL_F64)
+    if (prec != WVL_F32)
         return bc_cell<double>(OP_DENSITY, grid, free_axes, norb, psi_c, nullptr, nullptr, occ,
-                               rho, nullptr, nullptr, ws, ws_bytes, stream);
+                               rho, nullptr, nullptr, ws, ws_bytes, stream, prec == WVL_F64_EMU);
     return bc_cell<float>(OP_DENSITY, grid, free_axes, norb, psi_c, nullptr, nullptr, occ, rho,
-                          nullptr, nullptr, ws, ws_bytes, stream);
+                          nullptr, nullptr, ws, ws_bytes, stream, false);
 }
 
 wvl_status wvl_free_workspace_size(const wvl_grid* grid, int prec, int norb, size_t* bytes) {
@@ -1288,7 +1333,7 @@ wvl_status wvl_plan_create(const wvl_grid* cells, int ncell, const int* cell_of_
     p->cells.assign(cells, cells + ncell);
     p->cell_of_orb.assign(cell_of_orb, cell_of_orb + norb);
     p->norb = norb;
-    const size_t elt = prec == WVL_F64 ? 8 : 4;
+    const size_t elt = prec != WVL_F32 ? 8 : 4;
     size_t off = 0, wsoff = 0;
     for (int o = 0; o < norb;) {
         const int c = cell_of_orb[o];
@@ -1349,6 +1394,7 @@ static wvl_status plan_runs(wvl_plan* plan, const void* psi, const void* const* 
         r.occ = occ + pr.o0;
         r.ekin = ekin + pr.o0;
         r.epot = epot + pr.o0;
+        r.emu = plan->prec == WVL_F64_EMU;
         carve(r, static_cast<char*>(ws) + pr.ws_off);
         runs.push_back(r);
     }
@@ -1398,7 +1444,7 @@ static wvl_status plan_exec(wvl_plan* plan, const void* psi, const void* const* 
     const unsigned long long before = g_launches.load();
     // capture the enqueue sequence into a graph; the kernels' shared-memory
     // attributes are set before capture (host-only calls)
-    cudaError_t e = prepare_pass_kernels<T>();
+    cudaError_t e = (plan->prec == WVL_F64_EMU) ? prepare_emu_kernels() : prepare_pass_kernels<T>();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -1437,7 +1483,7 @@ wvl_status wvl_plan_hpsi(wvl_plan* plan, const void* psi, const void* const* V,
     if (plan->norb == 0) return WVL_OK;
     std::lock_guard<std::mutex> lk(plan->mu);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (plan->prec == WVL_F64) return plan_exec<double>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
+    if (plan->prec != WVL_F32) return plan_exec<double>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
     return plan_exec<float>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
 }
 
@@ -1451,6 +1497,12 @@ static wvl_status plan_tune(wvl_plan* plan, const void* psi, const void* const* 
     plan_runs<T>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, runs);
     // one full run leaves realistic values in every buffer
     WVL_TRY(run_op<T>(OP_HPSI, runs, &plan->tune, nullptr, st));
+    if (plan->prec == WVL_F64_EMU) {
+        // the emulated passes have one launch shape: nothing to tune
+        plan->tuned = true;
+        cudaError_t e = cudaStreamSynchronize(st);
+        return e == cudaSuccess ? WVL_OK : cuda_fail(e, "autotune");
+    }
     std::vector<PassCall<T>> calls = build_calls<T>(OP_HPSI, runs);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1513,7 +1565,7 @@ wvl_status wvl_plan_autotune(wvl_plan* plan, const void* psi, const void* const*
     if (plan->norb == 0) return WVL_OK;
     std::lock_guard<std::mutex> lk(plan->mu);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (plan->prec == WVL_F64) return plan_tune<double>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
+    if (plan->prec != WVL_F32) return plan_tune<double>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
     return plan_tune<float>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, st);
 }
 

@@ -1,0 +1,132 @@
+// FP64-accurate 1D passes on the FP16 tensor cores (Ozaki-style slicing).
+//
+// A pass computes out(I) = sum_t f_t x(I - hl + off + t) on every line (the
+// 1D convolutions of Eqs. 1dconvtrans and kinetic1d).  For a tile of M = 128
+// lines and a window of N = 32 consecutive outputs this is one small matrix
+// product D[line][j] = sum_k X[line][k] B[k][j] over the K = 48 (16-tap
+// filters) or 64 (kinetic) input positions the window reads, B being the
+// banded filter matrix.  Both operands are turned into integers on a common
+// scale -- per line for X (its largest exponent), per filter for B -- and
+// split into S = 6 signed base-1024 digits:
+//
+//     X = sum_q x_q 1024^(S-q),  F = sum_p f_p 1024^(S-p),  |x_q|, |f_p| <= 512.
+//
+// Every digit is exact in FP16, every digit product (<= 2^18) and every sum
+// the hardware forms on the way is an integer below 2^24, hence exact in the
+// FP32 accumulators; the pairs (p, q) of one diagonal d = p + q share an
+// accumulator while their summed worst-case bound stays below 2^24.  The
+// result is recombined in 64-bit integers,
+//
+//     sum_k F_k X_k ~ sum_{d=2}^{8} D_d 1024^(2S-d),
+//
+// dropping the diagonals d >= 9 (a relative contribution below 2^-62 of
+// max|f| max|x| per output), and scaled back to FP64.  The arithmetic of the
+// method is untouched: only the way each convolution sum is evaluated
+// changes, to an accuracy of the same order as FP64 rounding.
+#pragma once
+#include <cstdint>
+#include <cstring>
+
+#include "wvl_internal.h"
+
+namespace wvl {
+namespace emu {
+
+constexpr int M = 128;           // lines per tile (MMA M, TMEM lanes)
+constexpr int N = 32;            // outputs per window (MMA N)
+constexpr int S = 6;             // digits per operand
+constexpr int DBITS = 10;        // bits per digit
+constexpr int DMAX = 8;          // highest diagonal kept
+constexpr int MAXPAIR = 32;
+constexpr int MAXACC = 8;        // accumulators (TMEM columns: MAXACC * N)
+constexpr int TMEM_COLS = MAXACC * N;
+constexpr int QBITS = DBITS * S - 1;   // |X| < 2^QBITS
+// byte stride between the 8-position chunks of one operand plane: the MMA's
+// leading-dimension offset.  A: 128 rows of 16 B plus 16 B of bank skew.
+constexpr int LBOA = M * 16 + 16;
+constexpr int LBOB = N * 16;
+// T' = (sum of the kept diagonals) / 2^(DBITS (2S - DMAX) + TSHIFT): the
+// accumulator of diagonal d enters shifted by DBITS (DMAX - d) - TSHIFT
+// (right shifts rounded); the host checks that T' stays below 2^62
+constexpr int TSHIFT = 20;
+// sum_t f_t x_t = T' 2^(E_x + E_f - OUT_EXP)
+constexpr int OUT_EXP = 2 * QBITS - DBITS * (2 * S - DMAX) - TSHIFT;
+
+__host__ __device__ constexpr int window_k(int kind) { return kind == K_KIN ? 64 : 48; }
+__host__ __device__ constexpr int window_ha(int kind) { return kind == K_KIN ? 16 : 8; }
+__host__ __device__ constexpr int plane_a_bytes(int kind) { return window_k(kind) / 8 * LBOA; }
+__host__ __device__ constexpr int plane_b_bytes(int kind) { return window_k(kind) / 8 * LBOB; }
+__host__ __device__ constexpr int smem_bytes(int kind) {
+    return S * (plane_a_bytes(kind) + plane_b_bytes(kind));
+}
+
+// Schedule of one launch: which (filter digit p, data digit q) pairs go to
+// which accumulator, and each accumulator's weight (a shift of T').
+struct Sched {
+    int npairs;
+    int nacc;
+    unsigned char pp[MAXPAIR], pq[MAXPAIR], pacc[MAXPAIR];
+    int shift[MAXACC];
+};
+
+struct Params {
+    PassParams<double> p;
+    Sched s;
+};
+
+__host__ __device__ inline unsigned long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long u;
+    std::memcpy(&u, &x, 8);
+    return u;
+#endif
+}
+
+// biased exponent field of x (0 for zero)
+__host__ __device__ inline int bexp(double x) { return (int)((dbits(x) >> 52) & 0x7FF); }
+
+// E with |x| < 2^E for every x whose biased exponent is at most eb
+__host__ __device__ inline int scale_of(int eb) { return eb - 1022; }
+
+// X = round(x 2^(QBITS - E)) for |x| < 2^E, so |X| < 2^QBITS; integer
+// operations on the bit pattern only (subnormal inputs count as zero)
+__host__ __device__ inline long long quantize(double x, int E) {
+    const unsigned long long b = dbits(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0) return 0;
+    const long long m = (long long)((b & ((1ULL << 52) - 1)) | (1ULL << 52));
+    // x = m 2^(e - 1075) -> X = m 2^-(sh)
+    const int sh = E + 1075 - QBITS - e;
+    long long X;
+    if (sh <= 0) X = m << (-sh);                 // -sh <= 6 because e <= E + 1022
+    else if (sh >= 54) X = 0;                    // below half a unit
+    else X = (m + (1LL << (sh - 1))) >> sh;
+    return (b >> 63) ? -X : X;
+}
+
+// signed base-1024 digits, most significant first: d[0] in [-512, 512],
+// the others in [-512, 511]
+__host__ __device__ inline void digits(long long X, int (&d)[S]) {
+#pragma unroll
+    for (int q = S - 1; q > 0; --q) {
+        int lo = (int)(X & 1023);
+        lo -= (lo & 512) << 1;
+        d[q] = lo;
+        X = (X - lo) >> DBITS;
+    }
+    d[0] = (int)X;
+}
+
+}  // namespace emu
+
+// Launches one emulated pass (same parameters and outputs as launch_pass for
+// double; the segments carry tiles = line tiles x windows and nwin).
+cudaError_t launch_pass_emu(int kind, int mode, const PassParams<double>& p, long long nunits,
+                            cudaStream_t st);
+cudaError_t prepare_emu_kernels();
+// bounded waits of the emulated passes that ran out since the last call
+cudaError_t emu_take_timeouts(unsigned* count);
+
+}  // namespace wvl

@@ -1,0 +1,512 @@
+// The emulated FP64 pass (see emu.cuh for the arithmetic) as a tcgen05
+// kernel for sm_103a.
+//
+// Work unit: (orbital -- or orbital group for the potential pass --, tile of
+// 128 lines, window of 32 outputs).  A persistent CTA of 128 threads walks
+// its units; per orbital it
+//   1. reads the window's K input positions of its 128 lines (wrapped
+//      periodically, or gathered from the compressed layout in synthesis
+//      pass 1), one warp per line, takes the line's largest exponent with a
+//      warp reduction and writes the six FP16 digit planes into shared memory
+//      in the MMA's K-major layout (8 x 16 B core matrices);
+//   2. one thread issues the digit-pair MMAs (M = 128, N = 32, K = 16 each)
+//      into FP32 accumulators in tensor memory and commits them to an
+//      mbarrier;
+//   3. after a bounded wait, thread r (= TMEM lane r = line r) loads its
+//      accumulators, recombines them into 64-bit integers, scales to FP64
+//      and runs the pass's epilogue (transposed store, compressed scatter,
+//      V psi with density and Epot, kinetic K_p and Ekin) exactly as the
+//      FP64 pass does.
+// The filter digit planes are built once per CTA from the launch's taps.
+#include <cmath>
+
+#include <cuda_fp16.h>
+
+#include "emu.cuh"
+#include "pass_kernel.cuh"
+
+namespace wvl {
+
+__device__ unsigned int g_emu_timeouts = 0;
+
+namespace emu {
+
+constexpr long long WAIT_CYCLES = 4000000000LL;   // about two seconds
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor: no swizzle, K-major core matrices
+__device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// instruction descriptor: kind::f16, FP16 A and B (K-major), FP32 D, M x N
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t accumulate) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(mbar) : "memory");
+}
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+}
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tld8(uint32_t addr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void tld_wait() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t half2_bits(int lo, int hi) {
+    const __half2 h = __halves2half2(__int2half_rn(lo), __int2half_rn(hi));
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// input value at position x (0 <= x < n) of line a of orbital orb
+template <int MODE>
+__device__ __forceinline__ double load_in(const Seg<double>& S, int orb, int a, int x) {
+    if (MODE == M_UNCOMP) {
+        // line a = (x3, x2) of the interleaved coarse array: element x is
+        // c^mu[x3/2][x2/2][x/2], mu = (x & 1) + 2 (x2 & 1) + 4 (x3 & 1)
+        const int x3 = a / S.N2, x2 = a - x3 * S.N2;
+        const int mu = (x & 1) + 2 * (x2 & 1) + 4 * (x3 & 1);
+        const double* cc = S.in + (long long)orb * S.clen;
+        const long long ci = ((long long)(x3 >> 1) * S.n2 + (x2 >> 1)) * S.n1 + (x >> 1);
+        if (S.mapc == nullptr && S.bx1 == 0)
+            return (mu == 0) ? cc[ci] : cc[S.ncoarse + ci * 7 + mu - 1];
+        const int k = stored_index(S, ci, x >> 1, x2 >> 1, x3 >> 1, mu);
+        if (k < 0) return 0.0;
+        return (mu == 0) ? cc[k] : cc[S.ncoarse + (long long)k * 7 + mu - 1];
+    }
+    return S.in[(long long)orb * S.P + (long long)a * S.n + x];
+}
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(NTHREADS, 1) emu_pass_kernel(const __grid_constant__ Params ep) {
+    constexpr int K = window_k(KIND), HA = window_ha(KIND);
+    constexpr int APL = plane_a_bytes(KIND), BPL = plane_b_bytes(KIND);
+    constexpr int NT = KT<KIND>::NT;
+    constexpr bool KM = (MODE == M_KMID || MODE == M_KLAST);
+    static_assert(K <= 64 && K % 16 == 0, "window");
+    extern __shared__ __align__(128) unsigned char sm[];
+    unsigned char* const Asm = sm;
+    unsigned char* const Bsm = sm + S * APL;
+    __shared__ uint32_t tslot;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int rowE[M];
+    __shared__ double red[NWARPS];
+
+    const PassParams<double>& p = ep.p;
+    const Sched& sc = ep.s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // ---------------------------------------------- filter digit planes
+    int ebf = 0;
+    for (int e = 0; e < 2; ++e)
+        for (int t = 0; t < NT; ++t) ebf = max(ebf, bexp(p.f[e][t]));
+    const int Ef = scale_of(ebf);
+    for (int i = tid; i < N * K; i += NTHREADS) {
+        const int j = i / K, k = i - j * K;
+        const int e = j & 1;
+        const int t = k - j - (HA - p.hl) - (e ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
+        const double f = (t >= 0 && t < NT) ? p.f[e][t] : 0.0;
+        int d[S];
+        digits(quantize(f, Ef), d);
+#pragma unroll
+        for (int q = 0; q < S; ++q)
+            *reinterpret_cast<__half*>(Bsm + q * BPL + (k >> 3) * LBOB + j * 16 + (k & 7) * 2) =
+                __int2half_rn(d[q]);
+    }
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(su32(&tslot)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tm = tslot;
+    const uint32_t tlane = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t a_base = su32(Asm), b_base = su32(Bsm);
+    constexpr uint32_t IDESC = idesc_f16(M, N);
+    uint32_t phase = 0;
+    bool failed = false;
+
+#pragma unroll 1
+    for (long long u = blockIdx.x; u < p.nunits && !failed; u += gridDim.x) {
+        int si = 0;
+#pragma unroll 1
+        while (si + 1 < p.nseg && u >= p.seg[si + 1].blk0) ++si;
+        const Seg<double>& Sg = p.seg[si];
+        const long long loc = u - Sg.blk0;
+        const int grp = (int)(loc / Sg.tiles);
+        const int tt = (int)(loc - (long long)grp * Sg.tiles);
+        const int tile = tt / Sg.nwin, w = tt - tile * Sg.nwin;
+        const int a0 = tile * M, o = w * N;
+        const int n = Sg.n, NL = Sg.N;
+        const int lt = min(M, NL - a0);
+        int ob = grp, oe = grp + 1;
+        if (MODE == M_POT) {
+            ob = grp * Sg.opg;
+            oe = min(Sg.norb, ob + Sg.opg);
+        }
+        double racc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) racc[j] = 0.0;
+
+#pragma unroll 1
+        for (int orb = ob; orb < oe; ++orb) {
+            // ------------------------------------------ 1. slice the lines
+            const bool lane_on = 2 * lane < K;
+            // source positions of this lane's two window slots (periodic)
+            int x0 = (o - HA + 2 * lane) % n;
+            if (x0 < 0) x0 += n;
+            int x1 = x0 + 1;
+            if (x1 >= n) x1 -= n;
+#pragma unroll 1
+            for (int rb = 0; rb < M / NWARPS; rb += 8) {
+                double v[8][2];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = warp + NWARPS * (rb + i);
+                    v[i][0] = v[i][1] = 0.0;
+                    if (r < lt && lane_on) {
+                        v[i][0] = load_in<MODE>(Sg, orb, a0 + r, x0);
+                        v[i][1] = load_in<MODE>(Sg, orb, a0 + r, x1);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = warp + NWARPS * (rb + i);
+                    const int eb = __reduce_max_sync(0xffffffffu,
+                                                     (unsigned)max(bexp(v[i][0]), bexp(v[i][1])));
+                    const int E = scale_of(eb);
+                    if (lane == 0) rowE[r] = E;
+                    if (lane_on) {
+                        int d0[S], d1[S];
+                        digits(quantize(v[i][0], E), d0);
+                        digits(quantize(v[i][1], E), d1);
+                        unsigned char* dst = Asm + (lane >> 2) * LBOA + r * 16 + (lane & 3) * 4;
+#pragma unroll
+                        for (int q = 0; q < S; ++q)
+                            *reinterpret_cast<uint32_t*>(dst + q * APL) = half2_bits(d0[q], d1[q]);
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fence_before();
+            __syncthreads();
+
+            // ------------------------------------------ 2. digit-pair MMAs
+            if (tid == 0) {
+                fence_after();
+                uint32_t used = 0;
+#pragma unroll 1
+                for (int i = 0; i < sc.npairs; ++i) {
+                    const int fp = sc.pp[i], dq = sc.pq[i], ac = sc.pacc[i];
+#pragma unroll
+                    for (int s = 0; s < K / 16; ++s) {
+                        const uint64_t ad = mdesc(a_base + dq * APL + 2 * s * LBOA, LBOA, 128);
+                        const uint64_t bd = mdesc(b_base + fp * BPL + 2 * s * LBOB, LBOB, 128);
+                        mma(tm + ac * N, ad, bd, IDESC, ((used >> ac) & 1u) | (s > 0 ? 1u : 0u));
+                    }
+                    used |= 1u << ac;
+                }
+                commit(su32(&mbar));
+            }
+            __syncwarp();
+            const bool ok = wait_parity(su32(&mbar), phase);
+            failed = __syncthreads_or(!ok) != 0;
+            if (failed) break;
+            phase ^= 1u;
+            fence_after();
+
+            // ------------------------------------------ 3. epilogue
+            const int r = tid;
+            const bool row_ok = r < lt;
+            const int a = a0 + r;
+            const long long obase = (long long)orb * Sg.P;
+            int se = rowE[r] + Ef - OUT_EXP;
+            se = max(-1022, min(1023, se));
+            const double scale = __longlong_as_double((long long)(se + 1023) << 52);
+            double occ = 1.0;
+            if (MODE == M_POT) occ = Sg.occ ? Sg.occ[orb] : 1.0;
+            double eacc = 0.0;
+#pragma unroll
+            for (int c8 = 0; c8 < N / 8; ++c8) {
+                uint32_t dv[MAXACC][8];
+#pragma unroll
+                for (int ac = 0; ac < MAXACC; ++ac)
+                    if (ac < sc.nacc) tld8(tlane + ac * N + c8 * 8, dv[ac]);
+                tld_wait();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    long long tq = 0;
+#pragma unroll
+                    for (int ac = 0; ac < MAXACC; ++ac) {
+                        if (ac >= sc.nacc) continue;
+                        const long long dd = (long long)__float2int_rn(__uint_as_float(dv[ac][j]));
+                        const int sh = sc.shift[ac];
+                        tq += (sh >= 0) ? (dd << sh) : ((dd + (1LL << (-sh - 1))) >> (-sh));
+                    }
+                    const double val = (double)tq * scale;
+                    const int I = o + c8 * 8 + j;
+                    if (!row_ok || I >= n) continue;
+                    const long long oidx = (long long)I * NL + a;
+                    if (MODE == M_PLAIN || MODE == M_UNCOMP) {
+                        Sg.out[obase + oidx] = val;
+                    } else if (MODE == M_COMP) {
+                        const int X2 = a / Sg.N1, X1 = a - X2 * Sg.N1;
+                        const int mu = (X1 & 1) + 2 * (X2 & 1) + 4 * (I & 1);
+                        const long long ci =
+                            ((long long)(I >> 1) * Sg.n2 + (X2 >> 1)) * Sg.n1 + (X1 >> 1);
+                        double* cc0 = Sg.out + (long long)orb * Sg.clen;
+                        if (Sg.mapc == nullptr && Sg.bx1 == 0) {
+                            if (mu == 0) cc0[ci] = val;
+                            else cc0[Sg.ncoarse + ci * 7 + mu - 1] = val;
+                        } else {
+                            const int k = stored_index(Sg, ci, X1 >> 1, X2 >> 1, I >> 1, mu);
+                            if (k >= 0) {
+                                if (mu == 0) cc0[k] = val;
+                                else cc0[Sg.ncoarse + (long long)k * 7 + mu - 1] = val;
+                            }
+                        }
+                    } else if (KM) {
+                        const long long iidx = obase + (long long)a * n + I;
+                        const double g = Sg.in[iidx];
+                        double kin = 0.0;
+                        if (Sg.in2 != nullptr) kin = Sg.in2[iidx];
+                        else if (MODE == M_KMID && Sg.eps != nullptr) kin = -Sg.eps[orb] * g;
+                        const double acc = val + kin;
+                        if (MODE == M_KMID) {
+                            Sg.out[obase + oidx] = acc;
+                            Sg.out2[obase + oidx] = g;
+                        } else {
+                            if (Sg.out) Sg.out[obase + oidx] = acc;
+                            const double k0 = Sg.aux ? Sg.aux[obase + oidx] : 0.0;
+                            eacc = fma(g, acc - k0, eacc);
+                        }
+                    } else if (MODE == M_POT) {
+                        if (Sg.aux) {
+                            const double y = Sg.aux[oidx] * val;
+                            if (Sg.out) Sg.out[obase + oidx] = y;
+                            eacc = fma(y, val, eacc);
+                        }
+                        racc[c8 * 8 + j] = fma(occ * val, val, racc[c8 * 8 + j]);
+                    }
+                }
+            }
+            if ((MODE == M_POT && Sg.aux) || MODE == M_KLAST) {
+                const double t = block_sum(eacc, red);
+                if (tid == 0) Sg.part[(long long)orb * Sg.tiles + tt] = t;
+            }
+            fence_before();
+            __syncthreads();   // the next slicing overwrites the planes, the next MMAs the accumulators
+        }
+        if (failed) break;
+
+        if (MODE == M_POT && Sg.rho != nullptr && tid < lt) {
+            const int a = a0 + tid;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const int I = o + j;
+                if (I >= n) continue;
+                const long long oidx = (long long)I * NL + a;
+                if (Sg.rho_gstride == 0) Sg.rho[oidx] += racc[j];
+                else Sg.rho[(long long)grp * Sg.rho_gstride + oidx] = racc[j];
+            }
+        }
+    }
+
+    if (failed) {
+        // let the MMAs still in flight finish before the accumulators are freed
+        if (tid == 0) {
+            atomicAdd(&g_emu_timeouts, 1u);
+            wait_parity(su32(&mbar), phase);
+        }
+        __syncthreads();
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tm), "r"(TMEM_COLS));
+}
+
+// ------------------------------------------------------------------ host
+// Same digits as the kernel (same functions, same taps) -> exact bounds of
+// every pair's partial sums, and the accumulator grouping.
+static bool build_sched(int kind, const PassParams<double>& p, Sched& s) {
+    const KindGeom g = kind_geom(kind);
+    int ebf = 0;
+    for (int e = 0; e < 2; ++e)
+        for (int t = 0; t < g.nt; ++t) ebf = std::max(ebf, bexp(p.f[e][t]));
+    const int Ef = scale_of(ebf);
+    // sum over the taps of one output of |filter digit p|, worst parity
+    double sabs[S] = {0};
+    for (int e = 0; e < 2; ++e) {
+        double se[S] = {0};
+        for (int t = 0; t < g.nt; ++t) {
+            int d[S];
+            digits(quantize(p.f[e][t], Ef), d);
+            for (int q = 0; q < S; ++q) se[q] += std::abs(d[q]);
+        }
+        for (int q = 0; q < S; ++q) sabs[q] = std::max(sabs[q], se[q]);
+    }
+    const double lim = 16777216.0;   // 2^24: integers exact in FP32
+    double tbound = 0.0;             // bound of |T'|
+    std::memset(&s, 0, sizeof s);
+    for (int d = 2; d <= DMAX; ++d) {
+        double load = 0.0;
+        int cur = -1;
+        for (int fp = 0; fp < S; ++fp) {
+            const int dq = d - 2 - fp;   // digits are 0-based: (fp + 1) + (dq + 1) = d
+            if (dq < 0 || dq >= S) continue;
+            const double b = sabs[fp] * 512.0;
+            // diagonals that carry weight above 2^-50 must be exact
+            const bool exact = d <= 5;
+            if (cur < 0 || (exact && load + b > lim)) {
+                if (s.nacc >= MAXACC) return false;
+                cur = s.nacc++;
+                s.shift[cur] = DBITS * (DMAX - d) - TSHIFT;
+                load = 0.0;
+            }
+            load += b;
+            tbound += b * std::ldexp(1.0, s.shift[cur]);
+            if (s.npairs >= MAXPAIR) return false;
+            s.pp[s.npairs] = (unsigned char)fp;
+            s.pq[s.npairs] = (unsigned char)dq;
+            s.pacc[s.npairs] = (unsigned char)cur;
+            ++s.npairs;
+        }
+    }
+    return tbound < std::ldexp(1.0, 62);
+}
+
+template <int KIND, int MODE>
+static cudaError_t ensure_emu_attr() {
+    static unsigned long long done = 0;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(__atomic_load_n(&done, __ATOMIC_ACQUIRE) & bit)) {
+        err = cudaFuncSetAttribute(emu_pass_kernel<KIND, MODE>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(KIND));
+        if (err != cudaSuccess) return err;
+        __atomic_fetch_or(&done, bit, __ATOMIC_ACQ_REL);
+    }
+    return cudaSuccess;
+}
+
+template <int KIND, int MODE>
+static cudaError_t launch_emu(const Params& ep, long long nunits, cudaStream_t st) {
+    cudaError_t err = ensure_emu_attr<KIND, MODE>();
+    if (err != cudaSuccess) return err;
+    if (nunits <= 0) return cudaSuccess;
+    int dev = 0, nsm = 0, occ = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return err;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, emu_pass_kernel<KIND, MODE>,
+                                                        NTHREADS, smem_bytes(KIND));
+    if (err != cudaSuccess) return err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    // tensor memory: 512 columns per SM
+    occ = std::min(occ, 512 / TMEM_COLS);
+    long long grid = std::min<long long>((long long)occ * nsm, nunits);
+    emu_pass_kernel<KIND, MODE><<<dim3((unsigned)grid), dim3(NTHREADS), smem_bytes(KIND), st>>>(ep);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace emu
+
+cudaError_t launch_pass_emu(int kind, int mode, const PassParams<double>& p, long long nunits,
+                            cudaStream_t st) {
+    emu::Params ep;
+    std::memset(&ep, 0, sizeof ep);
+    ep.p = p;
+    if (!emu::build_sched(kind, p, ep.s)) return cudaErrorInvalidValue;
+    using namespace emu;
+    switch (kind) {
+    case K_SYN:
+        if (mode == M_UNCOMP) return launch_emu<K_SYN, M_UNCOMP>(ep, nunits, st);
+        if (mode == M_PLAIN) return launch_emu<K_SYN, M_PLAIN>(ep, nunits, st);
+        break;
+    case K_ANA:
+        if (mode == M_COMP) return launch_emu<K_ANA, M_COMP>(ep, nunits, st);
+        if (mode == M_PLAIN) return launch_emu<K_ANA, M_PLAIN>(ep, nunits, st);
+        break;
+    case K_MF:
+        if (mode == M_POT) return launch_emu<K_MF, M_POT>(ep, nunits, st);
+        if (mode == M_PLAIN) return launch_emu<K_MF, M_PLAIN>(ep, nunits, st);
+        break;
+    case K_MFT:
+        if (mode == M_PLAIN) return launch_emu<K_MFT, M_PLAIN>(ep, nunits, st);
+        break;
+    case K_KIN:
+        if (mode == M_KMID) return launch_emu<K_KIN, M_KMID>(ep, nunits, st);
+        if (mode == M_KLAST) return launch_emu<K_KIN, M_KLAST>(ep, nunits, st);
+        break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_emu_kernels() {
+    using namespace emu;
+    cudaError_t e;
+    if ((e = ensure_emu_attr<K_SYN, M_UNCOMP>()) != cudaSuccess) return e;
+    if ((e = ensure_emu_attr<K_SYN, M_PLAIN>()) != cudaSuccess) return e;
+    if ((e = ensure_emu_attr<K_ANA, M_COMP>()) != cudaSuccess) return e;
+    if ((e = ensure_emu_attr<K_ANA, M_PLAIN>()) != cudaSuccess) return e;
+    if ((e = ensure_emu_attr<K_MF, M_POT>()) != cudaSuccess) return e;
+    if ((e = ensure_emu_attr<K_MF, M_PLAIN>()) != cudaSuccess) return e;
+    if ((e = ensure_emu_attr<K_MFT, M_PLAIN>()) != cudaSuccess) return e;
+    if ((e = ensure_emu_attr<K_KIN, M_KMID>()) != cudaSuccess) return e;
+    return ensure_emu_attr<K_KIN, M_KLAST>();
+}
+
+cudaError_t emu_take_timeouts(unsigned* count) {
+    unsigned v = 0, z = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_emu_timeouts, sizeof v);
+    if (e != cudaSuccess) return e;
+    if (v) e = cudaMemcpyToSymbol(g_emu_timeouts, &z, sizeof z);
+    *count = v;
+    return e;
+}
+
+}  // namespace wvl

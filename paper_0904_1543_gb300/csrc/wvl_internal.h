@@ -69,7 +69,8 @@ struct Seg {
     int N1, N2;           // fine extents (index decoding)
     int n1, n2;           // coarse extents (compressed layout)
     int norb;
-    int tiles;            // ceil(N / LT)
+    int tiles;            // work units per orbital (group): ceil(N / LT), times nwin when emulated
+    int nwin;             // emulated FP64 passes: output windows per line
     int opg;              // M_POT: orbitals per group
     int rowlen;           // shared-memory row length in elements
 };
