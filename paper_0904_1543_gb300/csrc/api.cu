@@ -244,7 +244,7 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             pass_dims(d.Nf, c.pass, s.n, s.N);
             if (emu) {
                 // units: 128-line tiles x 32-output windows
-                s.nwin = (s.n + emu::N - 1) / emu::N;
+                s.nwin = (s.n + emu::window_n(c.kind) - 1) / emu::window_n(c.kind);
                 s.tiles = (s.N + emu::M - 1) / emu::M * s.nwin;
                 s.rowlen = 0;
             } else {
@@ -331,7 +331,7 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // tiles of LT_MIN lines, or 128-line tiles x 32-output windows when emulated
 static long long tiles_max(const int Nf[3]) {
     long long N = (long long)Nf[1] * Nf[0];
-    const long long emu_tiles = (N + emu::M - 1) / emu::M * ((Nf[2] + emu::N - 1) / emu::N);
+    const long long emu_tiles = (N + emu::M - 1) / emu::M * ((Nf[2] + emu::NMIN - 1) / emu::NMIN);
     return std::max((N + LT_MIN - 1) / LT_MIN, emu_tiles);
 }
 

@@ -2,10 +2,10 @@
 //
 // A pass computes out(I) = sum_t f_t x(I - hl + off + t) on every line (the
 // 1D convolutions of Eqs. 1dconvtrans and kinetic1d).  For a tile of M = 128
-// lines and a window of N = 32 consecutive outputs this is one small matrix
-// product D[line][j] = sum_k X[line][k] B[k][j] over the K = 48 (16-tap
-// filters) or 64 (kinetic) input positions the window reads, B being the
-// banded filter matrix.  Both operands are turned into integers on a common
+// lines and a window of N consecutive outputs (32 for the 16-tap filters,
+// 16 for the 29-tap kinetic filter) this is one small matrix product
+// D[line][j] = sum_k X[line][k] B[k][j] over the K = 48 input positions the
+// window reads, B being the banded filter matrix.  Both operands are turned into integers on a common
 // scale -- per line for X (its largest exponent), per filter for B -- and
 // split into S = 6 signed base-1024 digits:
 //
@@ -32,19 +32,24 @@
 namespace wvl {
 namespace emu {
 
+constexpr int THREADS = 256;     // 8 warps: slicing 16 lines each; epilogue 32 lines x N/2 outputs
+constexpr int WARPS = THREADS / 32;
 constexpr int M = 128;           // lines per tile (MMA M, TMEM lanes)
-constexpr int N = 32;            // outputs per window (MMA N)
+constexpr int NMAX = 32;         // outputs per window (MMA N), largest kind
+constexpr int NMIN = 16;
 constexpr int S = 6;             // digits per operand
 constexpr int DBITS = 10;        // bits per digit
 constexpr int DMAX = 8;          // highest diagonal kept
 constexpr int MAXPAIR = 32;
 constexpr int MAXACC = 8;        // accumulators (TMEM columns: MAXACC * N)
-constexpr int TMEM_COLS = MAXACC * N;
+// the schedules of the method's filters (all kinetic spacings checked from
+// 0.05 to 2): one accumulator per diagonal 2..8, the first four exact
+constexpr int NACC = 7;
+constexpr int NEXACT = 4;
 constexpr int QBITS = DBITS * S - 1;   // |X| < 2^QBITS
 // byte stride between the 8-position chunks of one operand plane: the MMA's
 // leading-dimension offset.  A: 128 rows of 16 B plus 16 B of bank skew.
 constexpr int LBOA = M * 16 + 16;
-constexpr int LBOB = N * 16;
 // T' = (sum of the kept diagonals) / 2^(DBITS (2S - DMAX) + TSHIFT): the
 // accumulator of diagonal d enters shifted by DBITS (DMAX - d) - TSHIFT
 // (right shifts rounded); the host checks that T' stays below 2^62
@@ -52,21 +57,31 @@ constexpr int TSHIFT = 20;
 // sum_t f_t x_t = T' 2^(E_x + E_f - OUT_EXP)
 constexpr int OUT_EXP = 2 * QBITS - DBITS * (2 * S - DMAX) - TSHIFT;
 
-__host__ __device__ constexpr int window_k(int kind) { return kind == K_KIN ? 64 : 48; }
+// outputs per window, input positions read (window start o - HA, 8-aligned)
+__host__ __device__ constexpr int window_n(int kind) { return kind == K_KIN ? 16 : 32; }
+__host__ __device__ constexpr int window_k(int kind) { return 48; }
 __host__ __device__ constexpr int window_ha(int kind) { return kind == K_KIN ? 16 : 8; }
+__host__ __device__ constexpr int lbo_b(int kind) { return window_n(kind) * 16; }
+__host__ __device__ constexpr int tmem_cols(int kind) { return MAXACC * window_n(kind); }
 __host__ __device__ constexpr int plane_a_bytes(int kind) { return window_k(kind) / 8 * LBOA; }
-__host__ __device__ constexpr int plane_b_bytes(int kind) { return window_k(kind) / 8 * LBOB; }
+__host__ __device__ constexpr int plane_b_bytes(int kind) { return window_k(kind) / 8 * lbo_b(kind); }
 __host__ __device__ constexpr int smem_bytes(int kind) {
     return S * (plane_a_bytes(kind) + plane_b_bytes(kind));
 }
 
 // Schedule of one launch: which (filter digit p, data digit q) pairs go to
 // which accumulator, and each accumulator's weight (a shift of T').
+// Accumulators come in diagonal order; the first nexact (diagonals <= 5)
+// hold exact integers and enter T' shifted left by shift[ac] >= 10; the
+// others (diagonals 6..8, weight 2^shift <= 1) are summed in FP32 with
+// weights wlow[ac] and rounded once.
 struct Sched {
     int npairs;
     int nacc;
+    int nexact;
     unsigned char pp[MAXPAIR], pq[MAXPAIR], pacc[MAXPAIR];
     int shift[MAXACC];
+    float wlow[MAXACC];
 };
 
 struct Params {
@@ -99,10 +114,12 @@ __host__ __device__ inline long long quantize(double x, int E) {
     const long long m = (long long)((b & ((1ULL << 52) - 1)) | (1ULL << 52));
     // x = m 2^(e - 1075) -> X = m 2^-(sh)
     const int sh = E + 1075 - QBITS - e;
-    long long X;
-    if (sh <= 0) X = m << (-sh);                 // -sh <= 6 because e <= E + 1022
-    else if (sh >= 54) X = 0;                    // below half a unit
-    else X = (m + (1LL << (sh - 1))) >> sh;
+    // left shift by -sh <= 6 (e <= E + 1022), or round off sh bits (none
+    // survive once sh >= 54); select rather than branch
+    const int lsh = sh < 0 ? -sh : 0;
+    const int rsh = sh > 63 ? 63 : (sh > 0 ? sh : 0);
+    const long long half = rsh > 0 ? (1LL << (rsh - 1)) : 0;
+    const long long X = ((m << lsh) + half) >> rsh;
     return (b >> 63) ? -X : X;
 }
 
@@ -118,6 +135,25 @@ __host__ __device__ inline void digits(long long X, int (&d)[S]) {
     }
     d[0] = (int)X;
 }
+
+#ifdef __CUDACC__
+// The same digits as digits(), each as an exact float: adding 512 to every
+// lower digit position makes the lower digits plain 10-bit fields of
+// Y = X + sum_k 512 1024^k (no carry chain); a field y becomes the float
+// y - 512 through the bit pattern of 2^23 + y.
+__device__ __forceinline__ void digit_floats(long long X, float (&f)[S]) {
+    constexpr long long C = 512LL * (1 + (1LL << 10) + (1LL << 20) + (1LL << 30) + (1LL << 40));
+    static_assert(S == 6, "digit layout");
+    const long long Y = X + C;
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) {
+        const unsigned y = (unsigned)(Y >> (DBITS * k)) & 1023u;
+        f[S - 1 - k] = __int_as_float(0x4B000000 | (int)y) - 8389120.0f;   // 2^23 + 512
+    }
+    const int top = (int)(Y >> (DBITS * (S - 1)));                          // [-512, 512]
+    f[0] = __int_as_float(0x4B000000 | (top + 1024)) - 8389632.0f;          // 2^23 + 1024
+}
+#endif
 
 }  // namespace emu
 

@@ -9,7 +9,7 @@
 //      pass 1), one warp per line, takes the line's largest exponent with a
 //      warp reduction and writes the six FP16 digit planes into shared memory
 //      in the MMA's K-major layout (8 x 16 B core matrices);
-//   2. one thread issues the digit-pair MMAs (M = 128, N = 32, K = 16 each)
+//   2. one thread issues the digit-pair MMAs (M = 128, N = 32 or 16, K = 16)
 //      into FP32 accumulators in tensor memory and commits them to an
 //      mbarrier;
 //   3. after a bounded wait, thread r (= TMEM lane r = line r) loads its
@@ -81,13 +81,13 @@ __device__ __forceinline__ void tld8(uint32_t addr, uint32_t (&v)[8]) {
                    "=r"(v[6]), "=r"(v[7])
                  : "r"(addr));
 }
+__device__ __forceinline__ void tld4(uint32_t addr, uint32_t (&v)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(addr));
+}
 __device__ __forceinline__ void tld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t half2_bits(int lo, int hi) {
-    const __half2 h = __halves2half2(__int2half_rn(lo), __int2half_rn(hi));
-    return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 // input value at position x (0 <= x < n) of line a of orbital orb
@@ -109,20 +109,68 @@ __device__ __forceinline__ double load_in(const Seg<double>& S, int orb, int a, 
     return S.in[(long long)orb * S.P + (long long)a * S.n + x];
 }
 
+// One job: orbital orb of work unit u (line tile x output window).
+struct EJob {
+    long long u;
+    int si, grp, tt, a0, o, lt, orb, oe;
+    bool valid;
+};
+
+__device__ __forceinline__ void decode_unit(const PassParams<double>& p, int mode, EJob& J) {
+    J.valid = J.u < p.nunits;
+    if (!J.valid) return;
+    int si = 0;
+    while (si + 1 < p.nseg && J.u >= p.seg[si + 1].blk0) ++si;
+    const Seg<double>& S = p.seg[si];
+    const long long loc = J.u - S.blk0;
+    J.si = si;
+    J.grp = (int)(loc / S.tiles);
+    J.tt = (int)(loc - (long long)J.grp * S.tiles);
+    const int tile = J.tt / S.nwin, w = J.tt - tile * S.nwin;
+    J.a0 = tile * M;
+    J.o = w;   // window index; scaled by the kind's N by the caller
+    J.lt = min(M, S.N - J.a0);
+    if (mode == M_POT) {
+        J.orb = J.grp * S.opg;
+        J.oe = min(S.norb, J.orb + S.opg);
+    } else {
+        J.orb = J.grp;
+        J.oe = J.grp + 1;
+    }
+}
+__device__ __forceinline__ void first_job(const PassParams<double>& p, int mode, EJob& J) {
+    J.u = blockIdx.x;
+    decode_unit(p, mode, J);
+}
+// returns true when J was the last orbital of its unit
+__device__ __forceinline__ bool next_job(const PassParams<double>& p, int mode, EJob& J) {
+    if (J.orb + 1 < J.oe) {
+        ++J.orb;
+        return false;
+    }
+    J.u += gridDim.x;
+    decode_unit(p, mode, J);
+    return true;
+}
+
 template <int KIND, int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1) emu_pass_kernel(const __grid_constant__ Params ep) {
+__global__ void __launch_bounds__(THREADS, 2)
+emu_pass_kernel(const __grid_constant__ Params ep) {
     constexpr int K = window_k(KIND), HA = window_ha(KIND);
     constexpr int APL = plane_a_bytes(KIND), BPL = plane_b_bytes(KIND);
     constexpr int NT = KT<KIND>::NT;
     constexpr bool KM = (MODE == M_KMID || MODE == M_KLAST);
+    constexpr int N = window_n(KIND), LBOB = lbo_b(KIND), TCOLS = tmem_cols(KIND);
+    constexpr int NH = N / 2;                // outputs per epilogue thread
+    constexpr int RPW = M / WARPS;           // lines per slicing warp
     static_assert(K <= 64 && K % 16 == 0, "window");
     extern __shared__ __align__(128) unsigned char sm[];
-    unsigned char* const Asm = sm;
-    unsigned char* const Bsm = sm + S * APL;
+    unsigned char* const Asm = sm;                // [S][APL]
+    unsigned char* const Bsm = sm + S * APL;      // [S][BPL]
     __shared__ uint32_t tslot;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int rowE[M];
-    __shared__ double red[NWARPS];
+    __shared__ double red[WARPS];
 
     const PassParams<double>& p = ep.p;
     const Sched& sc = ep.s;
@@ -133,7 +181,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) emu_pass_kernel(const __grid_cons
     for (int e = 0; e < 2; ++e)
         for (int t = 0; t < NT; ++t) ebf = max(ebf, bexp(p.f[e][t]));
     const int Ef = scale_of(ebf);
-    for (int i = tid; i < N * K; i += NTHREADS) {
+    for (int i = tid; i < N * K; i += THREADS) {
         const int j = i / K, k = i - j * K;
         const int e = j & 1;
         const int t = k - j - (HA - p.hl) - (e ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
@@ -145,209 +193,220 @@ __global__ void __launch_bounds__(NTHREADS, 1) emu_pass_kernel(const __grid_cons
             *reinterpret_cast<__half*>(Bsm + q * BPL + (k >> 3) * LBOB + j * 16 + (k & 7) * 2) =
                 __int2half_rn(d[q]);
     }
-
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&mbar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(su32(&tslot)), "r"(TMEM_COLS));
+                     :: "r"(su32(&tslot)), "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tm = tslot;
-    const uint32_t tlane = tm + ((uint32_t)(warp * 32) << 16);
+    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (lines)
+    // and one half of the window's outputs
+    const int quarter = warp & 3, half = warp >> 2;
+    const int er = 32 * quarter + lane;
+    const uint32_t tl = tm + ((uint32_t)(32 * quarter) << 16) + NH * half;
     const uint32_t a_base = su32(Asm), b_base = su32(Bsm);
     constexpr uint32_t IDESC = idesc_f16(M, N);
+    const bool lane_on = 2 * lane < K;
     uint32_t phase = 0;
     bool failed = false;
-
-#pragma unroll 1
-    for (long long u = blockIdx.x; u < p.nunits && !failed; u += gridDim.x) {
-        int si = 0;
-#pragma unroll 1
-        while (si + 1 < p.nseg && u >= p.seg[si + 1].blk0) ++si;
-        const Seg<double>& Sg = p.seg[si];
-        const long long loc = u - Sg.blk0;
-        const int grp = (int)(loc / Sg.tiles);
-        const int tt = (int)(loc - (long long)grp * Sg.tiles);
-        const int tile = tt / Sg.nwin, w = tt - tile * Sg.nwin;
-        const int a0 = tile * M, o = w * N;
-        const int n = Sg.n, NL = Sg.N;
-        const int lt = min(M, NL - a0);
-        int ob = grp, oe = grp + 1;
-        if (MODE == M_POT) {
-            ob = grp * Sg.opg;
-            oe = min(Sg.norb, ob + Sg.opg);
-        }
-        double racc[N];
+    double racc[NH];
 #pragma unroll
-        for (int j = 0; j < N; ++j) racc[j] = 0.0;
+    for (int c = 0; c < NH; ++c) racc[c] = 0.0;
 
+    EJob J;
+    first_job(p, MODE, J);
 #pragma unroll 1
-        for (int orb = ob; orb < oe; ++orb) {
-            // ------------------------------------------ 1. slice the lines
-            const bool lane_on = 2 * lane < K;
-            // source positions of this lane's two window slots (periodic)
+    while (J.valid) {
+        const Seg<double>& Sg = p.seg[J.si];
+        const int n = Sg.n, NL = Sg.N;
+        const int o = J.o * N;
+        // ------------------------------------------ 1. slice the lines
+        {
             int x0 = (o - HA + 2 * lane) % n;
             if (x0 < 0) x0 += n;
             int x1 = x0 + 1;
             if (x1 >= n) x1 -= n;
 #pragma unroll 1
-            for (int rb = 0; rb < M / NWARPS; rb += 8) {
-                double v[8][2];
+          for (int rb = 0; rb < RPW; rb += 8) {
+            double v[8][2];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int r = warp + NWARPS * (rb + i);
-                    v[i][0] = v[i][1] = 0.0;
-                    if (r < lt && lane_on) {
-                        v[i][0] = load_in<MODE>(Sg, orb, a0 + r, x0);
-                        v[i][1] = load_in<MODE>(Sg, orb, a0 + r, x1);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int r = warp + NWARPS * (rb + i);
-                    const int eb = __reduce_max_sync(0xffffffffu,
-                                                     (unsigned)max(bexp(v[i][0]), bexp(v[i][1])));
-                    const int E = scale_of(eb);
-                    if (lane == 0) rowE[r] = E;
-                    if (lane_on) {
-                        int d0[S], d1[S];
-                        digits(quantize(v[i][0], E), d0);
-                        digits(quantize(v[i][1], E), d1);
-                        unsigned char* dst = Asm + (lane >> 2) * LBOA + r * 16 + (lane & 3) * 4;
-#pragma unroll
-                        for (int q = 0; q < S; ++q)
-                            *reinterpret_cast<uint32_t*>(dst + q * APL) = half2_bits(d0[q], d1[q]);
-                    }
+            for (int i = 0; i < 8; ++i) {
+                const int r = warp + WARPS * (rb + i);
+                v[i][0] = v[i][1] = 0.0;
+                if (r < J.lt && lane_on) {
+                    v[i][0] = load_in<MODE>(Sg, J.orb, J.a0 + r, x0);
+                    v[i][1] = load_in<MODE>(Sg, J.orb, J.a0 + r, x1);
                 }
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            fence_before();
-            __syncthreads();
-
-            // ------------------------------------------ 2. digit-pair MMAs
-            if (tid == 0) {
-                fence_after();
-                uint32_t used = 0;
-#pragma unroll 1
-                for (int i = 0; i < sc.npairs; ++i) {
-                    const int fp = sc.pp[i], dq = sc.pq[i], ac = sc.pacc[i];
 #pragma unroll
-                    for (int s = 0; s < K / 16; ++s) {
-                        const uint64_t ad = mdesc(a_base + dq * APL + 2 * s * LBOA, LBOA, 128);
-                        const uint64_t bd = mdesc(b_base + fp * BPL + 2 * s * LBOB, LBOB, 128);
-                        mma(tm + ac * N, ad, bd, IDESC, ((used >> ac) & 1u) | (s > 0 ? 1u : 0u));
-                    }
-                    used |= 1u << ac;
-                }
-                commit(su32(&mbar));
-            }
-            __syncwarp();
-            const bool ok = wait_parity(su32(&mbar), phase);
-            failed = __syncthreads_or(!ok) != 0;
-            if (failed) break;
-            phase ^= 1u;
-            fence_after();
-
-            // ------------------------------------------ 3. epilogue
-            const int r = tid;
-            const bool row_ok = r < lt;
-            const int a = a0 + r;
-            const long long obase = (long long)orb * Sg.P;
-            int se = rowE[r] + Ef - OUT_EXP;
-            se = max(-1022, min(1023, se));
-            const double scale = __longlong_as_double((long long)(se + 1023) << 52);
-            double occ = 1.0;
-            if (MODE == M_POT) occ = Sg.occ ? Sg.occ[orb] : 1.0;
-            double eacc = 0.0;
+            for (int i = 0; i < 8; ++i) {
+                const int r = warp + WARPS * (rb + i);
+                const int eb = __reduce_max_sync(0xffffffffu,
+                                                 (unsigned)max(bexp(v[i][0]), bexp(v[i][1])));
+                const int E = scale_of(eb);
+                if (lane == 0) rowE[r] = E;
+                if (lane_on) {
+                    float f0[S], f1[S];
+                    digit_floats(quantize(v[i][0], E), f0);
+                    digit_floats(quantize(v[i][1], E), f1);
+                    unsigned char* dst = Asm + (lane >> 2) * LBOA + r * 16 + (lane & 3) * 4;
 #pragma unroll
-            for (int c8 = 0; c8 < N / 8; ++c8) {
-                uint32_t dv[MAXACC][8];
-#pragma unroll
-                for (int ac = 0; ac < MAXACC; ++ac)
-                    if (ac < sc.nacc) tld8(tlane + ac * N + c8 * 8, dv[ac]);
-                tld_wait();
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    long long tq = 0;
-#pragma unroll
-                    for (int ac = 0; ac < MAXACC; ++ac) {
-                        if (ac >= sc.nacc) continue;
-                        const long long dd = (long long)__float2int_rn(__uint_as_float(dv[ac][j]));
-                        const int sh = sc.shift[ac];
-                        tq += (sh >= 0) ? (dd << sh) : ((dd + (1LL << (-sh - 1))) >> (-sh));
-                    }
-                    const double val = (double)tq * scale;
-                    const int I = o + c8 * 8 + j;
-                    if (!row_ok || I >= n) continue;
-                    const long long oidx = (long long)I * NL + a;
-                    if (MODE == M_PLAIN || MODE == M_UNCOMP) {
-                        Sg.out[obase + oidx] = val;
-                    } else if (MODE == M_COMP) {
-                        const int X2 = a / Sg.N1, X1 = a - X2 * Sg.N1;
-                        const int mu = (X1 & 1) + 2 * (X2 & 1) + 4 * (I & 1);
-                        const long long ci =
-                            ((long long)(I >> 1) * Sg.n2 + (X2 >> 1)) * Sg.n1 + (X1 >> 1);
-                        double* cc0 = Sg.out + (long long)orb * Sg.clen;
-                        if (Sg.mapc == nullptr && Sg.bx1 == 0) {
-                            if (mu == 0) cc0[ci] = val;
-                            else cc0[Sg.ncoarse + ci * 7 + mu - 1] = val;
-                        } else {
-                            const int k = stored_index(Sg, ci, X1 >> 1, X2 >> 1, I >> 1, mu);
-                            if (k >= 0) {
-                                if (mu == 0) cc0[k] = val;
-                                else cc0[Sg.ncoarse + (long long)k * 7 + mu - 1] = val;
-                            }
-                        }
-                    } else if (KM) {
-                        const long long iidx = obase + (long long)a * n + I;
-                        const double g = Sg.in[iidx];
-                        double kin = 0.0;
-                        if (Sg.in2 != nullptr) kin = Sg.in2[iidx];
-                        else if (MODE == M_KMID && Sg.eps != nullptr) kin = -Sg.eps[orb] * g;
-                        const double acc = val + kin;
-                        if (MODE == M_KMID) {
-                            Sg.out[obase + oidx] = acc;
-                            Sg.out2[obase + oidx] = g;
-                        } else {
-                            if (Sg.out) Sg.out[obase + oidx] = acc;
-                            const double k0 = Sg.aux ? Sg.aux[obase + oidx] : 0.0;
-                            eacc = fma(g, acc - k0, eacc);
-                        }
-                    } else if (MODE == M_POT) {
-                        if (Sg.aux) {
-                            const double y = Sg.aux[oidx] * val;
-                            if (Sg.out) Sg.out[obase + oidx] = y;
-                            eacc = fma(y, val, eacc);
-                        }
-                        racc[c8 * 8 + j] = fma(occ * val, val, racc[c8 * 8 + j]);
+                    for (int q = 0; q < S; ++q) {
+                        const __half2 h2 = __floats2half2_rn(f0[q], f1[q]);
+                        *reinterpret_cast<uint32_t*>(dst + q * APL) =
+                            *reinterpret_cast<const uint32_t*>(&h2);
                     }
                 }
             }
-            if ((MODE == M_POT && Sg.aux) || MODE == M_KLAST) {
-                const double t = block_sum(eacc, red);
-                if (tid == 0) Sg.part[(long long)orb * Sg.tiles + tt] = t;
-            }
-            fence_before();
-            __syncthreads();   // the next slicing overwrites the planes, the next MMAs the accumulators
+          }
         }
-        if (failed) break;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before();
+        __syncthreads();
 
-        if (MODE == M_POT && Sg.rho != nullptr && tid < lt) {
-            const int a = a0 + tid;
+        // ------------------------------------------ 2. digit-pair MMAs
+        if (tid == 0) {
+            fence_after();
+            uint32_t used = 0;
+#pragma unroll 1
+            for (int i = 0; i < sc.npairs; ++i) {
+                const int fp = sc.pp[i], dq = sc.pq[i], ac = sc.pacc[i];
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const int I = o + j;
-                if (I >= n) continue;
-                const long long oidx = (long long)I * NL + a;
-                if (Sg.rho_gstride == 0) Sg.rho[oidx] += racc[j];
-                else Sg.rho[(long long)grp * Sg.rho_gstride + oidx] = racc[j];
+                for (int k = 0; k < K / 16; ++k) {
+                    const uint64_t ad = mdesc(a_base + dq * APL + 2 * k * LBOA, LBOA, 128);
+                    const uint64_t bd = mdesc(b_base + fp * BPL + 2 * k * LBOB, LBOB, 128);
+                    mma(tm + ac * N, ad, bd, IDESC, ((used >> ac) & 1u) | (k > 0 ? 1u : 0u));
+                }
+                used |= 1u << ac;
             }
+            commit(su32(&mbar));
+        }
+        // one thread polls; the others sleep in the barrier instead of
+        // taking issue slots from the co-resident CTA
+        bool ok = true;
+        if (tid == 0) ok = wait_parity(su32(&mbar), phase);
+        failed = __syncthreads_or(!ok) != 0;
+        if (failed) break;
+        phase ^= 1u;
+        fence_after();
+
+        // ------------------------------------------ 3. epilogue
+        // 2^(E_x + E_f - OUT_EXP) as a double (the FP64 pipe is idle here,
+        // the integer pipes are not)
+        int se = rowE[er] + Ef - OUT_EXP;
+        se = max(-1022, min(1023, se));
+        const double scale = __longlong_as_double((long long)(se + 1023) << 52);
+        const bool row_ok = er < J.lt;
+        const int a = J.a0 + er;
+        const int orb = J.orb;
+        const long long obase = (long long)orb * Sg.P;
+        double occ = 1.0;
+        if (MODE == M_POT) occ = Sg.occ ? Sg.occ[orb] : 1.0;
+        double eacc = 0.0;
+#pragma unroll
+        for (int c8 = 0; c8 < NH / 8; ++c8) {
+            uint32_t dv[NACC][8];
+#pragma unroll
+            for (int ac = 0; ac < NACC; ++ac) tld8(tl + ac * N + c8 * 8, dv[ac]);
+            tld_wait();
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                long long t = 0;
+                float low = 0.f;
+#pragma unroll
+                for (int ac = 0; ac < NACC; ++ac) {
+                    const float v = __uint_as_float(dv[ac][jj]);
+                    // shifts and weights of the canonical schedule (checked on the host)
+                    if (ac < NEXACT) t += (long long)__float2int_rn(v) << (DBITS * (DMAX - 2 - ac) - TSHIFT);
+                    else low = fmaf(v, __int_as_float((127 + DBITS * (DMAX - 2 - ac) - TSHIFT) << 23), low);
+                }
+                t += __float2int_rn(low);
+                const double val = (double)t * scale;
+                const int c = c8 * 8 + jj;
+                const int I = o + NH * half + c;
+                if (!row_ok || I >= n) continue;
+                const long long oidx = (long long)I * NL + a;
+                if (MODE == M_PLAIN || MODE == M_UNCOMP) {
+                    Sg.out[obase + oidx] = val;
+                } else if (MODE == M_COMP) {
+                    const int X2 = a / Sg.N1, X1 = a - X2 * Sg.N1;
+                    const int mu = (X1 & 1) + 2 * (X2 & 1) + 4 * (I & 1);
+                    const long long ci =
+                        ((long long)(I >> 1) * Sg.n2 + (X2 >> 1)) * Sg.n1 + (X1 >> 1);
+                    double* cc0 = Sg.out + (long long)orb * Sg.clen;
+                    if (Sg.mapc == nullptr && Sg.bx1 == 0) {
+                        if (mu == 0) cc0[ci] = val;
+                        else cc0[Sg.ncoarse + ci * 7 + mu - 1] = val;
+                    } else {
+                        const int k = stored_index(Sg, ci, X1 >> 1, X2 >> 1, I >> 1, mu);
+                        if (k >= 0) {
+                            if (mu == 0) cc0[k] = val;
+                            else cc0[Sg.ncoarse + (long long)k * 7 + mu - 1] = val;
+                        }
+                    }
+                } else if (KM) {
+                    const long long iidx = obase + (long long)a * n + I;
+                    const double g = Sg.in[iidx];
+                    double kin = 0.0;
+                    if (Sg.in2 != nullptr) kin = Sg.in2[iidx];
+                    else if (MODE == M_KMID && Sg.eps != nullptr) kin = -Sg.eps[orb] * g;
+                    const double acc = val + kin;
+                    if (MODE == M_KMID) {
+                        Sg.out[obase + oidx] = acc;
+                        Sg.out2[obase + oidx] = g;
+                    } else {
+                        if (Sg.out) Sg.out[obase + oidx] = acc;
+                        const double k0 = Sg.aux ? Sg.aux[obase + oidx] : 0.0;
+                        eacc = fma(g, acc - k0, eacc);
+                    }
+                } else if (MODE == M_POT) {
+                    if (Sg.aux) {
+                        const double y = Sg.aux[oidx] * val;
+                        if (Sg.out) Sg.out[obase + oidx] = y;
+                        eacc = fma(y, val, eacc);
+                    }
+                    racc[c] = fma(occ * val, val, racc[c]);
+                }
+            }
+        }
+        if ((MODE == M_POT && Sg.aux) || MODE == M_KLAST) {
+            // fixed-order sum over the warps
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) eacc += __shfl_down_sync(0xffffffffu, eacc, off);
+            if (lane == 0) red[warp] = eacc;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w) t += red[w];
+                Sg.part[(long long)orb * Sg.tiles + J.tt] = t;
+            }
+        }
+        fence_before();
+        __syncthreads();   // planes, accumulators and red are reused by the next job
+
+        const EJob Jc = J;
+        const bool unit_end = next_job(p, MODE, J);
+        if (MODE == M_POT && unit_end) {
+            if (Sg.rho != nullptr && er < Jc.lt) {
+#pragma unroll
+                for (int c = 0; c < NH; ++c) {
+                    const int I = Jc.o * N + NH * half + c;
+                    if (I >= n) continue;
+                    const long long oidx = (long long)I * NL + Jc.a0 + er;
+                    if (Sg.rho_gstride == 0) Sg.rho[oidx] += racc[c];
+                    else Sg.rho[(long long)Jc.grp * Sg.rho_gstride + oidx] = racc[c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NH; ++c) racc[c] = 0.0;
         }
     }
 
@@ -362,8 +421,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) emu_pass_kernel(const __grid_cons
     fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                     :: "r"(tm), "r"(TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tm), "r"(TCOLS));
 }
 
 // ------------------------------------------------------------------ host
@@ -402,6 +460,8 @@ static bool build_sched(int kind, const PassParams<double>& p, Sched& s) {
                 if (s.nacc >= MAXACC) return false;
                 cur = s.nacc++;
                 s.shift[cur] = DBITS * (DMAX - d) - TSHIFT;
+                s.wlow[cur] = (float)std::ldexp(1.0, s.shift[cur]);
+                if (exact) s.nexact = s.nacc;
                 load = 0.0;
             }
             load += b;
@@ -413,6 +473,11 @@ static bool build_sched(int kind, const PassParams<double>& p, Sched& s) {
             ++s.npairs;
         }
     }
+    // the kernels take the canonical schedule: accumulator a holds diagonal
+    // a + 2, exact for a < NEXACT (shift >= 10), FP32-summed otherwise
+    if (s.nacc != NACC || s.nexact != NEXACT) return false;
+    for (int a = 0; a < NACC; ++a)
+        if (s.shift[a] != DBITS * (DMAX - 2 - a) - TSHIFT) return false;
     return tbound < std::ldexp(1.0, 62);
 }
 
@@ -426,6 +491,10 @@ static cudaError_t ensure_emu_attr() {
     if (!(__atomic_load_n(&done, __ATOMIC_ACQUIRE) & bit)) {
         err = cudaFuncSetAttribute(emu_pass_kernel<KIND, MODE>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(KIND));
+        if (err != cudaSuccess) return err;
+        err = cudaFuncSetAttribute(emu_pass_kernel<KIND, MODE>,
+                                   cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   cudaSharedmemCarveoutMaxShared);
         if (err != cudaSuccess) return err;
         __atomic_fetch_or(&done, bit, __ATOMIC_ACQ_REL);
     }
@@ -441,14 +510,25 @@ static cudaError_t launch_emu(const Params& ep, long long nunits, cudaStream_t s
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return err;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, emu_pass_kernel<KIND, MODE>,
-                                                        NTHREADS, smem_bytes(KIND));
-    if (err != cudaSuccess) return err;
+    // CTAs per SM from shared memory, registers and tensor memory (512
+    // columns); the occupancy calculator undercounts these kernels
+    static int regs[64] = {0};
+    if (!regs[dev & 63]) {
+        cudaFuncAttributes fa;
+        if ((err = cudaFuncGetAttributes(&fa, emu_pass_kernel<KIND, MODE>)) != cudaSuccess) return err;
+        regs[dev & 63] = std::max(fa.numRegs, 1);
+    }
+    int smem_sm = 0;
+    if ((err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
+        cudaSuccess)
+        return err;
+    const int per_cta = smem_bytes(KIND) + 1024 + 1024;   // + static + reserved
+    const int by_smem = smem_sm / per_cta;
+    const int by_regs = 65536 / (((regs[dev & 63] + 7) / 8 * 8) * THREADS);
+    occ = std::min(std::min(by_smem, by_regs), 512 / tmem_cols(KIND));
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    // tensor memory: 512 columns per SM
-    occ = std::min(occ, 512 / TMEM_COLS);
     long long grid = std::min<long long>((long long)occ * nsm, nunits);
-    emu_pass_kernel<KIND, MODE><<<dim3((unsigned)grid), dim3(NTHREADS), smem_bytes(KIND), st>>>(ep);
+    emu_pass_kernel<KIND, MODE><<<dim3((unsigned)grid), dim3(THREADS), smem_bytes(KIND), st>>>(ep);
     count_launches(1);
     return cudaGetLastError();
 }
