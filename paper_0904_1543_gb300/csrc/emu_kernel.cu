@@ -173,7 +173,6 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
     __shared__ double red[WARPS];
 
     const PassParams<double>& p = ep.p;
-    const Sched& sc = ep.s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // ---------------------------------------------- filter digit planes
@@ -274,17 +273,24 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
         // ------------------------------------------ 2. digit-pair MMAs
         if (tid == 0) {
             fence_after();
-            uint32_t used = 0;
-#pragma unroll 1
-            for (int i = 0; i < sc.npairs; ++i) {
-                const int fp = sc.pp[i], dq = sc.pq[i], ac = sc.pacc[i];
+            // the canonical schedule, unrolled: diagonal d = 2..8 accumulates in
+            // tensor-memory columns (d - 2) N.., pairs (filter digit fp, data
+            // digit d - 2 - fp); descriptors are compile-time offsets
+            const uint64_t a0d = mdesc(a_base, LBOA, 128), b0d = mdesc(b_base, LBOB, 128);
 #pragma unroll
-                for (int k = 0; k < K / 16; ++k) {
-                    const uint64_t ad = mdesc(a_base + dq * APL + 2 * k * LBOA, LBOA, 128);
-                    const uint64_t bd = mdesc(b_base + fp * BPL + 2 * k * LBOB, LBOB, 128);
-                    mma(tm + ac * N, ad, bd, IDESC, ((used >> ac) & 1u) | (k > 0 ? 1u : 0u));
+            for (int d = 2; d <= DMAX; ++d) {
+#pragma unroll
+                for (int fp = 0; fp < S; ++fp) {
+                    const int dq = d - 2 - fp;
+                    if (dq < 0 || dq >= S) continue;
+                    const bool first = fp == (d - 2 - (S - 1) > 0 ? d - 2 - (S - 1) : 0);
+#pragma unroll
+                    for (int k = 0; k < K / 16; ++k)
+                        mma(tm + (d - 2) * N,
+                            a0d + (uint64_t)((dq * APL + 2 * k * LBOA) >> 4),
+                            b0d + (uint64_t)((fp * BPL + 2 * k * LBOB) >> 4), IDESC,
+                            (first && k == 0) ? 0u : 1u);
                 }
-                used |= 1u << ac;
             }
             commit(su32(&mbar));
         }
