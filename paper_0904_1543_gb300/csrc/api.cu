@@ -283,6 +283,8 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
         p.nunits = blk;
         if (emu) {
             cudaError_t e = launch_emu_t(c.kind, c.mode, p, blk, st);
+            if (e == cudaErrorInvalidValue)
+                return fail(WVL_EUNSUPPORTED, "tensor-core pass: filter digit schedule not supported");
             if (e != cudaSuccess) return cuda_fail(e, "emulated pass launch");
             continue;
         }
