@@ -163,6 +163,39 @@ def oracle_sample(cell_of_orb, psi, Vs, occ, offsets, norb_per_cell=1):
     return done, time.perf_counter() - t0
 
 
+def _oracle_task(task):
+    """One orbital of one cell through the oracle in a worker process: inputs
+    from the seeded generators (not timed), then the timed oracle call."""
+    import oracle.wavelet as O
+    from paper_0904_1543_gb300 import inputs
+    c, o = task
+    psi = inputs.orbital(CFG, o, SIZES[c])
+    V = inputs.gaussian_potential(CFG, c, SIZES[c])
+    t0 = time.perf_counter()
+    O.hpsi_local(psi, V, 2.0, SIZES[c])
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(seconds=10.0):
+    """The oracle on every host core: one spawned worker process per core,
+    each taking orbitals of the three cells in turn (every worker single
+    threaded).  Returns (orbital-applications/s, workers, orbitals)."""
+    import multiprocessing as mp
+    n = max(1, os.cpu_count() or 1)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    times = []
+    with ctx.Pool(n) as pool:
+        pool.map(_oracle_task, [(2, o) for o in range(n)])      # start-up, not timed
+        t0 = time.perf_counter()
+        r = 0
+        while time.perf_counter() - t0 < seconds:
+            times += pool.map(_oracle_task, [((r + w) % 3, w) for w in range(n)])
+            r += 1
+    return n * len(times) / sum(times), n, len(times)
+
+
 def offsets_of(cell_of_orb):
     off = [0]
     for c in cell_of_orb:
@@ -632,6 +665,11 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
             "value": done / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} orbitals (one of each cell per round), FP64 numpy oracle, "
                       f"single thread, {secs:.1f} s"}
+        par, nw, ndone = oracle_all_cores()
+        line["cpu_baseline_all_cores"] = {
+            "value": par, "unit": UNIT, "cores": nw, "kind": "oracle",
+            "sample": f"{ndone} orbitals over the three cells, one single-threaded oracle "
+                      f"process per core ({nw}), value = cores / mean seconds per orbital"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
