@@ -243,9 +243,10 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             Seg<T>& s = d.s;
             pass_dims(d.Nf, c.pass, s.n, s.N);
             if (emu) {
-                // units: 128-line tiles x 32-output windows
+                // units: 128-line tiles (the kernel walks their output
+                // windows); in the potential pass tiles x windows
                 s.nwin = (s.n + emu::window_n(c.kind) - 1) / emu::window_n(c.kind);
-                s.tiles = (s.N + emu::M - 1) / emu::M * s.nwin;
+                s.tiles = (s.N + emu::M - 1) / emu::M * (c.mode == M_POT ? s.nwin : 1);
                 s.rowlen = 0;
             } else {
                 s.nwin = 1;

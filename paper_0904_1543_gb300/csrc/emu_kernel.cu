@@ -126,9 +126,11 @@ __device__ __forceinline__ void decode_unit(const PassParams<double>& p, int mod
     J.si = si;
     J.grp = (int)(loc / S.tiles);
     J.tt = (int)(loc - (long long)J.grp * S.tiles);
-    const int tile = J.tt / S.nwin, w = J.tt - tile * S.nwin;
+    // potential pass: unit = (orbital group, tile, window); otherwise the
+    // unit is a whole tile of lines and the kernel walks its windows
+    const int tile = (mode == M_POT) ? J.tt / S.nwin : J.tt;
     J.a0 = tile * M;
-    J.o = w;   // window index; scaled by the kind's N by the caller
+    J.o = (mode == M_POT) ? J.tt - tile * S.nwin : 0;   // window index
     J.lt = min(M, S.N - J.a0);
     if (mode == M_POT) {
         J.orb = J.grp * S.opg;
@@ -153,19 +155,224 @@ __device__ __forceinline__ bool next_job(const PassParams<double>& p, int mode, 
     return true;
 }
 
+// The 26 digit pairs x 3 K-steps of one window, unrolled (the canonical
+// schedule: diagonal d = 2..8 accumulates in tensor-memory columns
+// (d - 2) N.., pairs (filter digit fp, data digit d - 2 - fp)).  K-step k
+// reads the data planes' slab slot (slot0 + k) mod 3, the filter planes'
+// K-step k.  Shared-memory descriptors are base + compile-time offsets.
+template <int KIND>
+__device__ __forceinline__ void issue_window_mmas(uint32_t tm, uint32_t a_base, uint32_t b_base,
+                                                  int slot0) {
+    constexpr int APL = plane_a_bytes(KIND), BPL = plane_b_bytes(KIND);
+    constexpr int N = window_n(KIND), LBOB = lbo_b(KIND), K = window_k(KIND);
+    constexpr uint32_t IDESC = idesc_f16(M, N);
+    const uint64_t a0d = mdesc(a_base, LBOA, 128), b0d = mdesc(b_base, LBOB, 128);
+    uint32_t aoff[K / 16];
+#pragma unroll
+    for (int k = 0; k < K / 16; ++k) {
+        int sl = slot0 + k;
+        sl -= (sl >= K / 16) ? K / 16 : 0;
+        aoff[k] = (uint32_t)(sl * 2 * LBOA) >> 4;
+    }
+#pragma unroll
+    for (int d = 2; d <= DMAX; ++d) {
+#pragma unroll
+        for (int fp = 0; fp < S; ++fp) {
+            const int dq = d - 2 - fp;
+            if (dq < 0 || dq >= S) continue;
+            const bool first = fp == (d - 2 - (S - 1) > 0 ? d - 2 - (S - 1) : 0);
+#pragma unroll
+            for (int k = 0; k < K / 16; ++k)
+                mma(tm + (d - 2) * N, a0d + (uint64_t)(((uint32_t)(dq * APL) >> 4) + aoff[k]),
+                    b0d + (uint64_t)((fp * BPL + 2 * k * LBOB) >> 4), IDESC,
+                    (first && k == 0) ? 0u : 1u);
+        }
+    }
+}
+
+// digits of two consecutive inputs of line r into the data planes at the
+// given chunk (8 positions) and pair within it
+__device__ __forceinline__ void store_pair_digits(unsigned char* Asm, int apl, int chunk, int r,
+                                                  int pair4, double v0, double v1, int E) {
+    float f0[S], f1[S];
+    digit_floats(quantize(v0, E), f0);
+    digit_floats(quantize(v1, E), f1);
+    unsigned char* dst = Asm + chunk * LBOA + r * 16 + pair4 * 4;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        const __half2 h2 = __floats2half2_rn(f0[q], f1[q]);
+        *reinterpret_cast<uint32_t*>(dst + q * apl) = *reinterpret_cast<const uint32_t*>(&h2);
+    }
+}
+
+// The epilogue's other inputs for this thread's outputs (line er, outputs
+// o0 .. o0 + N/2 - 1), loaded while the MMAs run: the kinetic passes' G and
+// K_{p-1} (line-major, 16-byte loads) and K_0, the potential pass's V.
+template <int KIND, int MODE>
+__device__ __forceinline__ void prefetch_epilogue(const Seg<double>& Sg, int o0, int er, int lt,
+                                                  int a0, int orb, double (&pa)[window_n(KIND) / 2],
+                                                  double (&pb)[window_n(KIND) / 2],
+                                                  double (&pc)[window_n(KIND) / 2]) {
+    constexpr int NH = window_n(KIND) / 2;
+    constexpr bool KM = (MODE == M_KMID || MODE == M_KLAST);
+    if (!(KM || MODE == M_POT)) return;
+    const int n = Sg.n, NL = Sg.N;
+    const int a = a0 + er;
+    const long long obase = (long long)orb * Sg.P;
+    const bool full = er < lt && o0 + NH <= n;   // all outputs exist: vector loads
+#pragma unroll
+    for (int c = 0; c < NH; ++c) pa[c] = pb[c] = pc[c] = 0.0;
+    if (er >= lt) return;
+    if (KM) {
+        const double* gi = Sg.in + obase + (long long)a * n + o0;
+        const double* ki = Sg.in2 ? Sg.in2 + obase + (long long)a * n + o0 : nullptr;
+        if (full) {
+#pragma unroll
+            for (int c = 0; c < NH; c += 2) {
+                const double2 g2 = *reinterpret_cast<const double2*>(gi + c);
+                pa[c] = g2.x;
+                pa[c + 1] = g2.y;
+                if (ki) {
+                    const double2 k2 = *reinterpret_cast<const double2*>(ki + c);
+                    pb[c] = k2.x;
+                    pb[c + 1] = k2.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NH; ++c)
+                if (o0 + c < n) {
+                    pa[c] = gi[c];
+                    if (ki) pb[c] = ki[c];
+                }
+        }
+        if (MODE == M_KLAST && Sg.aux)
+#pragma unroll
+            for (int c = 0; c < NH; ++c)
+                if (o0 + c < n) pc[c] = Sg.aux[obase + (long long)(o0 + c) * NL + a];
+    } else if (MODE == M_POT && Sg.aux) {
+#pragma unroll
+        for (int c = 0; c < NH; ++c)
+            if (o0 + c < n) pa[c] = Sg.aux[(long long)(o0 + c) * NL + a];
+    }
+}
+
+// one window's outputs of this thread (line er, outputs o0 .. o0 + N/2 - 1):
+// accumulators -> FP64 -> the pass's epilogue; returns the energy partial
+template <int KIND, int MODE>
+__device__ __forceinline__ double window_epilogue(const Seg<double>& Sg, uint32_t tl, int o0,
+                                                  int er, int lt, int a0, int orb, int se,
+                                                  double (&racc)[window_n(KIND) / 2],
+                                                  const double (&pa)[window_n(KIND) / 2],
+                                                  const double (&pb)[window_n(KIND) / 2],
+                                                  const double (&pc)[window_n(KIND) / 2]) {
+    constexpr int N = window_n(KIND), NH = N / 2;
+    constexpr bool KM = (MODE == M_KMID || MODE == M_KLAST);
+    const int n = Sg.n, NL = Sg.N;
+    se = max(-1022, min(1023, se));
+    // 2^se as a double: the FP64 pipe is idle here, the integer pipes are not
+    const double scale = __longlong_as_double((long long)(se + 1023) << 52);
+    const bool row_ok = er < lt;
+    const int a = a0 + er;
+    const long long obase = (long long)orb * Sg.P;
+    double occ = 1.0;
+    if (MODE == M_POT) occ = Sg.occ ? Sg.occ[orb] : 1.0;
+    double eacc = 0.0;
+#pragma unroll
+    for (int c8 = 0; c8 < NH / 8; ++c8) {
+        uint32_t dv[NACC][8];
+#pragma unroll
+        for (int ac = 0; ac < NACC; ++ac) tld8(tl + ac * N + c8 * 8, dv[ac]);
+        tld_wait();
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            long long t = 0;
+            float low = 0.f;
+#pragma unroll
+            for (int ac = 0; ac < NACC; ++ac) {
+                const float v = __uint_as_float(dv[ac][jj]);
+                // shifts and weights of the canonical schedule (checked on the host)
+                if (ac < NEXACT) t += (long long)__float2int_rn(v) << (DBITS * (DMAX - 2 - ac) - TSHIFT);
+                else low = fmaf(v, __int_as_float((127 + DBITS * (DMAX - 2 - ac) - TSHIFT) << 23), low);
+            }
+            t += __float2int_rn(low);
+            const double val = (double)t * scale;
+            const int c = c8 * 8 + jj;
+            const int I = o0 + c;
+            if (!row_ok || I >= n) continue;
+            const long long oidx = (long long)I * NL + a;
+            if (MODE == M_PLAIN || MODE == M_UNCOMP) {
+                Sg.out[obase + oidx] = val;
+            } else if (MODE == M_COMP) {
+                const int X2 = a / Sg.N1, X1 = a - X2 * Sg.N1;
+                const int mu = (X1 & 1) + 2 * (X2 & 1) + 4 * (I & 1);
+                const long long ci = ((long long)(I >> 1) * Sg.n2 + (X2 >> 1)) * Sg.n1 + (X1 >> 1);
+                double* cc0 = Sg.out + (long long)orb * Sg.clen;
+                if (Sg.mapc == nullptr && Sg.bx1 == 0) {
+                    if (mu == 0) cc0[ci] = val;
+                    else cc0[Sg.ncoarse + ci * 7 + mu - 1] = val;
+                } else {
+                    const int k = stored_index(Sg, ci, X1 >> 1, X2 >> 1, I >> 1, mu);
+                    if (k >= 0) {
+                        if (mu == 0) cc0[k] = val;
+                        else cc0[Sg.ncoarse + (long long)k * 7 + mu - 1] = val;
+                    }
+                }
+            } else if (KM) {
+                const double g = pa[c];
+                double kin = pb[c];
+                if (MODE == M_KMID && Sg.in2 == nullptr && Sg.eps != nullptr) kin = -Sg.eps[orb] * g;
+                const double acc = val + kin;
+                if (MODE == M_KMID) {
+                    Sg.out[obase + oidx] = acc;
+                    Sg.out2[obase + oidx] = g;
+                } else {
+                    if (Sg.out) Sg.out[obase + oidx] = acc;
+                    eacc = fma(g, acc - pc[c], eacc);
+                }
+            } else if (MODE == M_POT) {
+                if (Sg.aux) {
+                    const double y = pa[c] * val;
+                    if (Sg.out) Sg.out[obase + oidx] = y;
+                    eacc = fma(y, val, eacc);
+                }
+                racc[c] = fma(occ * val, val, racc[c]);
+            }
+        }
+    }
+    return eacc;
+}
+
+// fixed-order CTA sum of one value per thread
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) t += red[w];
+    return t;
+}
+
 template <int KIND, int MODE>
 __global__ void __launch_bounds__(THREADS, 2)
 emu_pass_kernel(const __grid_constant__ Params ep) {
     constexpr int K = window_k(KIND), HA = window_ha(KIND);
     constexpr int APL = plane_a_bytes(KIND), BPL = plane_b_bytes(KIND);
     constexpr int NT = KT<KIND>::NT;
-    constexpr bool KM = (MODE == M_KMID || MODE == M_KLAST);
     constexpr int N = window_n(KIND), LBOB = lbo_b(KIND), TCOLS = tmem_cols(KIND);
     constexpr int NH = N / 2;                // outputs per epilogue thread
     constexpr int RPW = M / WARPS;           // lines per slicing warp
-    static_assert(K <= 64 && K % 16 == 0, "window");
+    constexpr int NSLOT = K / 16;            // 16-position slabs per window (3)
+    // a line unit (all windows of 128 lines of one orbital) slices every
+    // input once; the potential pass keeps one unit per window so that its
+    // density sums stay in registers across the orbitals of a group
+    constexpr bool LINE = MODE != M_POT;
+    static_assert(K == 48 && N % 16 == 0 && (HA - (KIND == K_KIN ? 0 : 8)) % 16 == 0, "window");
     extern __shared__ __align__(128) unsigned char sm[];
-    unsigned char* const Asm = sm;                // [S][APL]
+    unsigned char* const Asm = sm;                // [S][APL]: NSLOT slab slots of 2 chunks
     unsigned char* const Bsm = sm + S * APL;      // [S][BPL]
     __shared__ uint32_t tslot;
     __shared__ __align__(8) uint64_t mbar;
@@ -211,208 +418,193 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
     const int er = 32 * quarter + lane;
     const uint32_t tl = tm + ((uint32_t)(32 * quarter) << 16) + NH * half;
     const uint32_t a_base = su32(Asm), b_base = su32(Bsm);
-    constexpr uint32_t IDESC = idesc_f16(M, N);
-    const bool lane_on = 2 * lane < K;
     uint32_t phase = 0;
     bool failed = false;
     double racc[NH];
 #pragma unroll
     for (int c = 0; c < NH; ++c) racc[c] = 0.0;
 
+    // MMAs of one window, then the wait: one thread polls, the others sleep
+    // in the barrier instead of taking issue slots from the co-resident CTA
+    auto issue_mmas = [&](int slot0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            issue_window_mmas<KIND>(tm, a_base, b_base, slot0);
+            commit(su32(&mbar));
+        }
+    };
+    auto wait_mmas = [&]() -> bool {
+        bool ok = true;
+        if (tid == 0) ok = wait_parity(su32(&mbar), phase);
+        if (__syncthreads_or(!ok)) return false;
+        phase ^= 1u;
+        fence_after();
+        return true;
+    };
+
     EJob J;
     first_job(p, MODE, J);
 #pragma unroll 1
     while (J.valid) {
         const Seg<double>& Sg = p.seg[J.si];
-        const int n = Sg.n, NL = Sg.N;
-        const int o = J.o * N;
-        // ------------------------------------------ 1. slice the lines
-        {
+        const int n = Sg.n;
+        if constexpr (LINE) {
+            // ---------------------------- one exponent per line (whole line)
+#pragma unroll 1
+            for (int i = 0; i < RPW; i += 4) {
+                int eb[4] = {0, 0, 0, 0};
+#pragma unroll 1
+                for (int x = 2 * lane; x < n; x += 64) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int r = warp + WARPS * (i + k);
+                        if (r >= J.lt) continue;
+                        if (MODE == M_UNCOMP) {
+                            eb[k] = max(eb[k], bexp(load_in<MODE>(Sg, J.orb, J.a0 + r, x)));
+                            eb[k] = max(eb[k], bexp(load_in<MODE>(Sg, J.orb, J.a0 + r, x + 1)));
+                        } else {
+                            // n is even: x, x + 1 are in the line and 16-byte aligned
+                            const double2 v = *reinterpret_cast<const double2*>(
+                                Sg.in + (long long)J.orb * Sg.P + (long long)(J.a0 + r) * n + x);
+                            eb[k] = max(eb[k], max(bexp(v.x), bexp(v.y)));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = (int)__reduce_max_sync(0xffffffffu, (unsigned)eb[k]);
+                    if (lane == 0) rowE[warp + WARPS * (i + k)] = scale_of(e);
+                }
+            }
+            __syncthreads();
+            // ---------------------------- windows; each slab sliced once
+            // slab s covers positions 16 s + P0 .. + 15; window w reads slabs
+            // s0(w) .. s0(w) + 2 from slots (slab mod 3)
+            constexpr int P0 = (KIND == K_KIN) ? 0 : -8;
+            const int nwin = Sg.nwin;
+            int next_slab = 0x7fffffff;
+            double eacc = 0.0;
+#pragma unroll 1
+            for (int w = 0; w < nwin && !failed; ++w) {
+                const int o = w * N;
+                const int s0 = (o - HA - P0) / 16;
+                int sfrom = (w == 0) ? s0 : next_slab;
+                const int sto = s0 + NSLOT;
+                // slice slabs [sfrom, sto): lane -> (line of 4, pair of 8)
+#pragma unroll 1
+                for (int sb = sfrom; sb < sto; ++sb) {
+                    const int slot = ((sb % NSLOT) + NSLOT) % NSLOT;
+                    const int pair = lane & 7;
+                    int x = (16 * sb + P0 + 2 * pair) % n;
+                    if (x < 0) x += n;
+                    int x1 = x + 1;
+                    if (x1 >= n) x1 -= n;
+#pragma unroll
+                    for (int g4 = 0; g4 < RPW / 4; ++g4) {
+                        const int r = warp * RPW + 4 * g4 + (lane >> 3);
+                        double v0 = 0.0, v1 = 0.0;
+                        if (r < J.lt) {
+                            if (MODE == M_UNCOMP) {
+                                v0 = load_in<MODE>(Sg, J.orb, J.a0 + r, x);
+                                v1 = load_in<MODE>(Sg, J.orb, J.a0 + r, x1);
+                            } else {
+                                // x is even and n is even: x1 = x + 1, 16-byte aligned
+                                const double2 v = *reinterpret_cast<const double2*>(
+                                    Sg.in + (long long)J.orb * Sg.P + (long long)(J.a0 + r) * n + x);
+                                v0 = v.x;
+                                v1 = v.y;
+                            }
+                        }
+                        store_pair_digits(Asm, APL, 2 * slot + (pair >> 2), r, pair & 3, v0, v1,
+                                          rowE[r]);
+                    }
+                }
+                next_slab = sto;
+                issue_mmas(((s0 % NSLOT) + NSLOT) % NSLOT);
+                double pa[NH], pb[NH], pc[NH];
+                prefetch_epilogue<KIND, MODE>(Sg, o + NH * half, er, J.lt, J.a0, J.orb, pa, pb, pc);
+                if (!wait_mmas()) {
+                    failed = true;
+                    break;
+                }
+                eacc += window_epilogue<KIND, MODE>(Sg, tl, o + NH * half, er, J.lt, J.a0, J.orb,
+                                                    rowE[er] + Ef - OUT_EXP, racc, pa, pb, pc);
+                fence_before();
+                __syncthreads();   // accumulators are rewritten by the next window's MMAs
+            }
+            if (failed) break;
+            if (MODE == M_KLAST) {
+                const double t = cta_sum(eacc, red);
+                if (tid == 0) Sg.part[(long long)J.orb * Sg.tiles + J.tt] = t;
+                __syncthreads();
+            }
+            __syncthreads();   // rowE and the slab ring are reused by the next unit
+            next_job(p, MODE, J);
+        } else {
+            // ---------------------------- one window of one orbital
+            const int o = J.o * N;
+            const bool lane_on = 2 * lane < K;
             int x0 = (o - HA + 2 * lane) % n;
             if (x0 < 0) x0 += n;
             int x1 = x0 + 1;
             if (x1 >= n) x1 -= n;
 #pragma unroll 1
-          for (int rb = 0; rb < RPW; rb += 8) {
-            double v[8][2];
+            for (int rb = 0; rb < RPW; rb += 8) {
+                double v[8][2];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = warp + WARPS * (rb + i);
-                v[i][0] = v[i][1] = 0.0;
-                if (r < J.lt && lane_on) {
-                    v[i][0] = load_in<MODE>(Sg, J.orb, J.a0 + r, x0);
-                    v[i][1] = load_in<MODE>(Sg, J.orb, J.a0 + r, x1);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = warp + WARPS * (rb + i);
-                const int eb = __reduce_max_sync(0xffffffffu,
-                                                 (unsigned)max(bexp(v[i][0]), bexp(v[i][1])));
-                const int E = scale_of(eb);
-                if (lane == 0) rowE[r] = E;
-                if (lane_on) {
-                    float f0[S], f1[S];
-                    digit_floats(quantize(v[i][0], E), f0);
-                    digit_floats(quantize(v[i][1], E), f1);
-                    unsigned char* dst = Asm + (lane >> 2) * LBOA + r * 16 + (lane & 3) * 4;
-#pragma unroll
-                    for (int q = 0; q < S; ++q) {
-                        const __half2 h2 = __floats2half2_rn(f0[q], f1[q]);
-                        *reinterpret_cast<uint32_t*>(dst + q * APL) =
-                            *reinterpret_cast<const uint32_t*>(&h2);
+                for (int i = 0; i < 8; ++i) {
+                    const int r = warp + WARPS * (rb + i);
+                    v[i][0] = v[i][1] = 0.0;
+                    if (r < J.lt && lane_on) {
+                        v[i][0] = load_in<MODE>(Sg, J.orb, J.a0 + r, x0);
+                        v[i][1] = load_in<MODE>(Sg, J.orb, J.a0 + r, x1);
                     }
                 }
-            }
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        fence_before();
-        __syncthreads();
-
-        // ------------------------------------------ 2. digit-pair MMAs
-        if (tid == 0) {
-            fence_after();
-            // the canonical schedule, unrolled: diagonal d = 2..8 accumulates in
-            // tensor-memory columns (d - 2) N.., pairs (filter digit fp, data
-            // digit d - 2 - fp); descriptors are compile-time offsets
-            const uint64_t a0d = mdesc(a_base, LBOA, 128), b0d = mdesc(b_base, LBOB, 128);
 #pragma unroll
-            for (int d = 2; d <= DMAX; ++d) {
-#pragma unroll
-                for (int fp = 0; fp < S; ++fp) {
-                    const int dq = d - 2 - fp;
-                    if (dq < 0 || dq >= S) continue;
-                    const bool first = fp == (d - 2 - (S - 1) > 0 ? d - 2 - (S - 1) : 0);
-#pragma unroll
-                    for (int k = 0; k < K / 16; ++k)
-                        mma(tm + (d - 2) * N,
-                            a0d + (uint64_t)((dq * APL + 2 * k * LBOA) >> 4),
-                            b0d + (uint64_t)((fp * BPL + 2 * k * LBOB) >> 4), IDESC,
-                            (first && k == 0) ? 0u : 1u);
+                for (int i = 0; i < 8; ++i) {
+                    const int r = warp + WARPS * (rb + i);
+                    const int eb = __reduce_max_sync(0xffffffffu,
+                                                     (unsigned)max(bexp(v[i][0]), bexp(v[i][1])));
+                    const int E = scale_of(eb);
+                    if (lane == 0) rowE[r] = E;
+                    if (lane_on) store_pair_digits(Asm, APL, lane >> 2, r, lane & 3, v[i][0], v[i][1], E);
                 }
             }
-            commit(su32(&mbar));
-        }
-        // one thread polls; the others sleep in the barrier instead of
-        // taking issue slots from the co-resident CTA
-        bool ok = true;
-        if (tid == 0) ok = wait_parity(su32(&mbar), phase);
-        failed = __syncthreads_or(!ok) != 0;
-        if (failed) break;
-        phase ^= 1u;
-        fence_after();
-
-        // ------------------------------------------ 3. epilogue
-        // 2^(E_x + E_f - OUT_EXP) as a double (the FP64 pipe is idle here,
-        // the integer pipes are not)
-        int se = rowE[er] + Ef - OUT_EXP;
-        se = max(-1022, min(1023, se));
-        const double scale = __longlong_as_double((long long)(se + 1023) << 52);
-        const bool row_ok = er < J.lt;
-        const int a = J.a0 + er;
-        const int orb = J.orb;
-        const long long obase = (long long)orb * Sg.P;
-        double occ = 1.0;
-        if (MODE == M_POT) occ = Sg.occ ? Sg.occ[orb] : 1.0;
-        double eacc = 0.0;
+            issue_mmas(0);
+            double pa[NH], pb[NH], pc[NH];
+            prefetch_epilogue<KIND, MODE>(Sg, o + NH * half, er, J.lt, J.a0, J.orb, pa, pb, pc);
+            if (!wait_mmas()) {
+                failed = true;
+                break;
+            }
+            const double eacc = window_epilogue<KIND, MODE>(Sg, tl, o + NH * half, er, J.lt, J.a0,
+                                                            J.orb, rowE[er] + Ef - OUT_EXP, racc,
+                                                            pa, pb, pc);
+            if (Sg.aux) {
+                const double t = cta_sum(eacc, red);
+                if (tid == 0) Sg.part[(long long)J.orb * Sg.tiles + J.tt] = t;
+            }
+            fence_before();
+            __syncthreads();   // planes, accumulators and red are reused by the next job
+            const EJob Jc = J;
+            const bool unit_end = next_job(p, MODE, J);
+            if (unit_end) {
+                if (Sg.rho != nullptr && er < Jc.lt) {
 #pragma unroll
-        for (int c8 = 0; c8 < NH / 8; ++c8) {
-            uint32_t dv[NACC][8];
-#pragma unroll
-            for (int ac = 0; ac < NACC; ++ac) tld8(tl + ac * N + c8 * 8, dv[ac]);
-            tld_wait();
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                long long t = 0;
-                float low = 0.f;
-#pragma unroll
-                for (int ac = 0; ac < NACC; ++ac) {
-                    const float v = __uint_as_float(dv[ac][jj]);
-                    // shifts and weights of the canonical schedule (checked on the host)
-                    if (ac < NEXACT) t += (long long)__float2int_rn(v) << (DBITS * (DMAX - 2 - ac) - TSHIFT);
-                    else low = fmaf(v, __int_as_float((127 + DBITS * (DMAX - 2 - ac) - TSHIFT) << 23), low);
-                }
-                t += __float2int_rn(low);
-                const double val = (double)t * scale;
-                const int c = c8 * 8 + jj;
-                const int I = o + NH * half + c;
-                if (!row_ok || I >= n) continue;
-                const long long oidx = (long long)I * NL + a;
-                if (MODE == M_PLAIN || MODE == M_UNCOMP) {
-                    Sg.out[obase + oidx] = val;
-                } else if (MODE == M_COMP) {
-                    const int X2 = a / Sg.N1, X1 = a - X2 * Sg.N1;
-                    const int mu = (X1 & 1) + 2 * (X2 & 1) + 4 * (I & 1);
-                    const long long ci =
-                        ((long long)(I >> 1) * Sg.n2 + (X2 >> 1)) * Sg.n1 + (X1 >> 1);
-                    double* cc0 = Sg.out + (long long)orb * Sg.clen;
-                    if (Sg.mapc == nullptr && Sg.bx1 == 0) {
-                        if (mu == 0) cc0[ci] = val;
-                        else cc0[Sg.ncoarse + ci * 7 + mu - 1] = val;
-                    } else {
-                        const int k = stored_index(Sg, ci, X1 >> 1, X2 >> 1, I >> 1, mu);
-                        if (k >= 0) {
-                            if (mu == 0) cc0[k] = val;
-                            else cc0[Sg.ncoarse + (long long)k * 7 + mu - 1] = val;
-                        }
+                    for (int c = 0; c < NH; ++c) {
+                        const int I = Jc.o * N + NH * half + c;
+                        if (I >= n) continue;
+                        const long long oidx = (long long)I * Sg.N + Jc.a0 + er;
+                        if (Sg.rho_gstride == 0) Sg.rho[oidx] += racc[c];
+                        else Sg.rho[(long long)Jc.grp * Sg.rho_gstride + oidx] = racc[c];
                     }
-                } else if (KM) {
-                    const long long iidx = obase + (long long)a * n + I;
-                    const double g = Sg.in[iidx];
-                    double kin = 0.0;
-                    if (Sg.in2 != nullptr) kin = Sg.in2[iidx];
-                    else if (MODE == M_KMID && Sg.eps != nullptr) kin = -Sg.eps[orb] * g;
-                    const double acc = val + kin;
-                    if (MODE == M_KMID) {
-                        Sg.out[obase + oidx] = acc;
-                        Sg.out2[obase + oidx] = g;
-                    } else {
-                        if (Sg.out) Sg.out[obase + oidx] = acc;
-                        const double k0 = Sg.aux ? Sg.aux[obase + oidx] : 0.0;
-                        eacc = fma(g, acc - k0, eacc);
-                    }
-                } else if (MODE == M_POT) {
-                    if (Sg.aux) {
-                        const double y = Sg.aux[oidx] * val;
-                        if (Sg.out) Sg.out[obase + oidx] = y;
-                        eacc = fma(y, val, eacc);
-                    }
-                    racc[c] = fma(occ * val, val, racc[c]);
                 }
+#pragma unroll
+                for (int c = 0; c < NH; ++c) racc[c] = 0.0;
             }
-        }
-        if ((MODE == M_POT && Sg.aux) || MODE == M_KLAST) {
-            // fixed-order sum over the warps
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) eacc += __shfl_down_sync(0xffffffffu, eacc, off);
-            if (lane == 0) red[warp] = eacc;
-            __syncthreads();
-            if (tid == 0) {
-                double t = 0.0;
-#pragma unroll
-                for (int w = 0; w < WARPS; ++w) t += red[w];
-                Sg.part[(long long)orb * Sg.tiles + J.tt] = t;
-            }
-        }
-        fence_before();
-        __syncthreads();   // planes, accumulators and red are reused by the next job
-
-        const EJob Jc = J;
-        const bool unit_end = next_job(p, MODE, J);
-        if (MODE == M_POT && unit_end) {
-            if (Sg.rho != nullptr && er < Jc.lt) {
-#pragma unroll
-                for (int c = 0; c < NH; ++c) {
-                    const int I = Jc.o * N + NH * half + c;
-                    if (I >= n) continue;
-                    const long long oidx = (long long)I * NL + Jc.a0 + er;
-                    if (Sg.rho_gstride == 0) Sg.rho[oidx] += racc[c];
-                    else Sg.rho[(long long)Jc.grp * Sg.rho_gstride + oidx] = racc[c];
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < NH; ++c) racc[c] = 0.0;
         }
     }
 
