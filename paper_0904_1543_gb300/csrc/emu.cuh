@@ -48,8 +48,11 @@ constexpr int NACC = 7;
 constexpr int NEXACT = 4;
 constexpr int QBITS = DBITS * S - 1;   // |X| < 2^QBITS
 // byte stride between the 8-position chunks of one operand plane: the MMA's
-// leading-dimension offset.  A: 128 rows of 16 B plus 16 B of bank skew.
-constexpr int LBOA = M * 16 + 16;
+// leading-dimension offset.  A: 128 rows of 16 B plus a bank skew that keeps
+// the digit stores conflict-free for the way each pass slices (a whole
+// window per line in the potential pass: 16 B; 16-position slabs of four
+// lines per warp instruction otherwise: 64 B).
+__host__ __device__ constexpr int lboa(int mode) { return M * 16 + (mode == M_POT ? 16 : 64); }
 // T' = (sum of the kept diagonals) / 2^(DBITS (2S - DMAX) + TSHIFT): the
 // accumulator of diagonal d enters shifted by DBITS (DMAX - d) - TSHIFT
 // (right shifts rounded); the host checks that T' stays below 2^62
@@ -63,10 +66,10 @@ __host__ __device__ constexpr int window_k(int kind) { return 48; }
 __host__ __device__ constexpr int window_ha(int kind) { return kind == K_KIN ? 16 : 8; }
 __host__ __device__ constexpr int lbo_b(int kind) { return window_n(kind) * 16; }
 __host__ __device__ constexpr int tmem_cols(int kind) { return MAXACC * window_n(kind); }
-__host__ __device__ constexpr int plane_a_bytes(int kind) { return window_k(kind) / 8 * LBOA; }
+__host__ __device__ constexpr int plane_a_bytes(int kind, int mode) { return window_k(kind) / 8 * lboa(mode); }
 __host__ __device__ constexpr int plane_b_bytes(int kind) { return window_k(kind) / 8 * lbo_b(kind); }
-__host__ __device__ constexpr int smem_bytes(int kind) {
-    return S * (plane_a_bytes(kind) + plane_b_bytes(kind));
+__host__ __device__ constexpr int smem_bytes(int kind, int mode) {
+    return S * (plane_a_bytes(kind, mode) + plane_b_bytes(kind));
 }
 
 // Schedule of one launch: which (filter digit p, data digit q) pairs go to

@@ -160,10 +160,11 @@ __device__ __forceinline__ bool next_job(const PassParams<double>& p, int mode, 
 // (d - 2) N.., pairs (filter digit fp, data digit d - 2 - fp)).  K-step k
 // reads the data planes' slab slot (slot0 + k) mod 3, the filter planes'
 // K-step k.  Shared-memory descriptors are base + compile-time offsets.
-template <int KIND>
+template <int KIND, int MODE>
 __device__ __forceinline__ void issue_window_mmas(uint32_t tm, uint32_t a_base, uint32_t b_base,
                                                   int slot0) {
-    constexpr int APL = plane_a_bytes(KIND), BPL = plane_b_bytes(KIND);
+    constexpr int LBOA = lboa(MODE);
+    constexpr int APL = plane_a_bytes(KIND, MODE), BPL = plane_b_bytes(KIND);
     constexpr int N = window_n(KIND), LBOB = lbo_b(KIND), K = window_k(KIND);
     constexpr uint32_t IDESC = idesc_f16(M, N);
     const uint64_t a0d = mdesc(a_base, LBOA, 128), b0d = mdesc(b_base, LBOB, 128);
@@ -192,6 +193,7 @@ __device__ __forceinline__ void issue_window_mmas(uint32_t tm, uint32_t a_base, 
 
 // digits of two consecutive inputs of line r into the data planes at the
 // given chunk (8 positions) and pair within it
+template <int LBOA>
 __device__ __forceinline__ void store_pair_digits(unsigned char* Asm, int apl, int chunk, int r,
                                                   int pair4, double v0, double v1, int E) {
     float f0[S], f1[S];
@@ -360,7 +362,8 @@ template <int KIND, int MODE>
 __global__ void __launch_bounds__(THREADS, 2)
 emu_pass_kernel(const __grid_constant__ Params ep) {
     constexpr int K = window_k(KIND), HA = window_ha(KIND);
-    constexpr int APL = plane_a_bytes(KIND), BPL = plane_b_bytes(KIND);
+    constexpr int LBOA = lboa(MODE);
+    constexpr int APL = plane_a_bytes(KIND, MODE), BPL = plane_b_bytes(KIND);
     constexpr int NT = KT<KIND>::NT;
     constexpr int N = window_n(KIND), LBOB = lbo_b(KIND), TCOLS = tmem_cols(KIND);
     constexpr int NH = N / 2;                // outputs per epilogue thread
@@ -432,7 +435,7 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
         __syncthreads();
         if (tid == 0) {
             fence_after();
-            issue_window_mmas<KIND>(tm, a_base, b_base, slot0);
+            issue_window_mmas<KIND, MODE>(tm, a_base, b_base, slot0);
             commit(su32(&mbar));
         }
     };
@@ -485,47 +488,66 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
             // s0(w) .. s0(w) + 2 from slots (slab mod 3)
             constexpr int P0 = (KIND == K_KIN) ? 0 : -8;
             const int nwin = Sg.nwin;
-            int next_slab = 0x7fffffff;
+            constexpr int NEW = N / 16;          // new slabs per window after the first
+            // raw inputs of one slab for this lane: lines warp * RPW + 4 g + lane / 8,
+            // positions 2 (lane % 8), + 1 of the slab
+            auto load_slab = [&](int sb, double (&v)[RPW / 4][2]) {
+                const int pair = lane & 7;
+                int x = (16 * sb + P0 + 2 * pair) % n;
+                if (x < 0) x += n;
+                int x1 = x + 1;
+                if (x1 >= n) x1 -= n;
+#pragma unroll
+                for (int g4 = 0; g4 < RPW / 4; ++g4) {
+                    const int r = warp * RPW + 4 * g4 + (lane >> 3);
+                    v[g4][0] = v[g4][1] = 0.0;
+                    if (r >= J.lt) continue;
+                    if (MODE == M_UNCOMP) {
+                        v[g4][0] = load_in<MODE>(Sg, J.orb, J.a0 + r, x);
+                        v[g4][1] = load_in<MODE>(Sg, J.orb, J.a0 + r, x1);
+                    } else {
+                        // x is even and n is even: x1 = x + 1, 16-byte aligned
+                        const double2 d2 = *reinterpret_cast<const double2*>(
+                            Sg.in + (long long)J.orb * Sg.P + (long long)(J.a0 + r) * n + x);
+                        v[g4][0] = d2.x;
+                        v[g4][1] = d2.y;
+                    }
+                }
+            };
+            auto slice_slab = [&](int sb, const double (&v)[RPW / 4][2]) {
+                const int slot = ((sb % NSLOT) + NSLOT) % NSLOT;
+                const int pair = lane & 7;
+#pragma unroll
+                for (int g4 = 0; g4 < RPW / 4; ++g4) {
+                    const int r = warp * RPW + 4 * g4 + (lane >> 3);
+                    store_pair_digits<LBOA>(Asm, APL, 2 * slot + (pair >> 2), r, pair & 3, v[g4][0],
+                                            v[g4][1], rowE[r]);
+                }
+            };
             double eacc = 0.0;
 #pragma unroll 1
             for (int w = 0; w < nwin && !failed; ++w) {
                 const int o = w * N;
                 const int s0 = (o - HA - P0) / 16;
-                int sfrom = (w == 0) ? s0 : next_slab;
-                const int sto = s0 + NSLOT;
-                // slice slabs [sfrom, sto): lane -> (line of 4, pair of 8)
+                if (w == 0) {
 #pragma unroll 1
-                for (int sb = sfrom; sb < sto; ++sb) {
-                    const int slot = ((sb % NSLOT) + NSLOT) % NSLOT;
-                    const int pair = lane & 7;
-                    int x = (16 * sb + P0 + 2 * pair) % n;
-                    if (x < 0) x += n;
-                    int x1 = x + 1;
-                    if (x1 >= n) x1 -= n;
-#pragma unroll
-                    for (int g4 = 0; g4 < RPW / 4; ++g4) {
-                        const int r = warp * RPW + 4 * g4 + (lane >> 3);
-                        double v0 = 0.0, v1 = 0.0;
-                        if (r < J.lt) {
-                            if (MODE == M_UNCOMP) {
-                                v0 = load_in<MODE>(Sg, J.orb, J.a0 + r, x);
-                                v1 = load_in<MODE>(Sg, J.orb, J.a0 + r, x1);
-                            } else {
-                                // x is even and n is even: x1 = x + 1, 16-byte aligned
-                                const double2 v = *reinterpret_cast<const double2*>(
-                                    Sg.in + (long long)J.orb * Sg.P + (long long)(J.a0 + r) * n + x);
-                                v0 = v.x;
-                                v1 = v.y;
-                            }
-                        }
-                        store_pair_digits(Asm, APL, 2 * slot + (pair >> 2), r, pair & 3, v0, v1,
-                                          rowE[r]);
+                    for (int sb = s0; sb < s0 + NSLOT; ++sb) {
+                        double v[RPW / 4][2];
+                        load_slab(sb, v);
+                        slice_slab(sb, v);
+                    }
+                } else {
+#pragma unroll 1
+                    for (int k = 0; k < NEW; ++k) {
+                        double v[RPW / 4][2];
+                        load_slab(s0 + NSLOT - NEW + k, v);
+                        slice_slab(s0 + NSLOT - NEW + k, v);
                     }
                 }
-                next_slab = sto;
                 issue_mmas(((s0 % NSLOT) + NSLOT) % NSLOT);
                 double pa[NH], pb[NH], pc[NH];
                 prefetch_epilogue<KIND, MODE>(Sg, o + NH * half, er, J.lt, J.a0, J.orb, pa, pb, pc);
+
                 if (!wait_mmas()) {
                     failed = true;
                     break;
@@ -570,7 +592,8 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
                                                      (unsigned)max(bexp(v[i][0]), bexp(v[i][1])));
                     const int E = scale_of(eb);
                     if (lane == 0) rowE[r] = E;
-                    if (lane_on) store_pair_digits(Asm, APL, lane >> 2, r, lane & 3, v[i][0], v[i][1], E);
+                    if (lane_on)
+                        store_pair_digits<LBOA>(Asm, APL, lane >> 2, r, lane & 3, v[i][0], v[i][1], E);
                 }
             }
             issue_mmas(0);
@@ -688,7 +711,7 @@ static cudaError_t ensure_emu_attr() {
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(__atomic_load_n(&done, __ATOMIC_ACQUIRE) & bit)) {
         err = cudaFuncSetAttribute(emu_pass_kernel<KIND, MODE>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(KIND));
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(KIND, MODE));
         if (err != cudaSuccess) return err;
         err = cudaFuncSetAttribute(emu_pass_kernel<KIND, MODE>,
                                    cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -720,13 +743,13 @@ static cudaError_t launch_emu(const Params& ep, long long nunits, cudaStream_t s
     if ((err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
         cudaSuccess)
         return err;
-    const int per_cta = smem_bytes(KIND) + 1024 + 1024;   // + static + reserved
+    const int per_cta = smem_bytes(KIND, MODE) + 1024 + 1024;   // + static + reserved
     const int by_smem = smem_sm / per_cta;
     const int by_regs = 65536 / (((regs[dev & 63] + 7) / 8 * 8) * THREADS);
     occ = std::min(std::min(by_smem, by_regs), 512 / tmem_cols(KIND));
     if (occ < 1) return cudaErrorInvalidConfiguration;
     long long grid = std::min<long long>((long long)occ * nsm, nunits);
-    emu_pass_kernel<KIND, MODE><<<dim3((unsigned)grid), dim3(THREADS), smem_bytes(KIND), st>>>(ep);
+    emu_pass_kernel<KIND, MODE><<<dim3((unsigned)grid), dim3(THREADS), smem_bytes(KIND, MODE), st>>>(ep);
     count_launches(1);
     return cudaGetLastError();
 }
