@@ -24,7 +24,10 @@
 // method is untouched: only the way each convolution sum is evaluated
 // changes, to an accuracy of the same order as FP64 rounding.
 #pragma once
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "wvl_internal.h"
@@ -137,6 +140,65 @@ __host__ __device__ inline void digits(long long X, int (&d)[S]) {
         X = (X - lo) >> DBITS;
     }
     d[0] = (int)X;
+}
+
+// The digit-pair schedule for one filter (taps f[parity][t], t < nt), from
+// the same digits the kernel builds: each pair's partial sums are bounded by
+// sum_t |filter digit| x 512 (the largest data digit); the pairs of a
+// diagonal <= 5 share an accumulator while their bounds add up to less than
+// 2^24 (exact in FP32); diagonals 6..8 take one accumulator each.  False
+// when the result is not the canonical schedule the kernels are built for,
+// or when |T'| could reach 2^62.
+inline bool build_sched(const double (&f)[2][32], int nt, Sched& s) {
+    int ebf = 0;
+    for (int e = 0; e < 2; ++e)
+        for (int t = 0; t < nt; ++t) ebf = std::max(ebf, bexp(f[e][t]));
+    const int Ef = scale_of(ebf);
+    // sum over the taps of one output of |filter digit p|, worst parity
+    double sabs[S] = {0};
+    for (int e = 0; e < 2; ++e) {
+        double se[S] = {0};
+        for (int t = 0; t < nt; ++t) {
+            int d[S];
+            digits(quantize(f[e][t], Ef), d);
+            for (int q = 0; q < S; ++q) se[q] += std::abs(d[q]);
+        }
+        for (int q = 0; q < S; ++q) sabs[q] = std::max(sabs[q], se[q]);
+    }
+    const double lim = 16777216.0;   // 2^24: integers exact in FP32
+    double tbound = 0.0;             // bound of |T'|
+    std::memset(&s, 0, sizeof s);
+    for (int d = 2; d <= DMAX; ++d) {
+        double load = 0.0;
+        int cur = -1;
+        for (int fp = 0; fp < S; ++fp) {
+            const int dq = d - 2 - fp;   // digits are 0-based: (fp + 1) + (dq + 1) = d
+            if (dq < 0 || dq >= S) continue;
+            const double b = sabs[fp] * 512.0;
+            const bool exact = d <= 5;   // weight above 2^-40 of the top diagonal
+            if (cur < 0 || (exact && load + b > lim)) {
+                if (s.nacc >= MAXACC) return false;
+                cur = s.nacc++;
+                s.shift[cur] = DBITS * (DMAX - d) - TSHIFT;
+                s.wlow[cur] = (float)std::ldexp(1.0, s.shift[cur]);
+                if (exact) s.nexact = s.nacc;
+                load = 0.0;
+            }
+            load += b;
+            tbound += b * std::ldexp(1.0, s.shift[cur]);
+            if (s.npairs >= MAXPAIR) return false;
+            s.pp[s.npairs] = (unsigned char)fp;
+            s.pq[s.npairs] = (unsigned char)dq;
+            s.pacc[s.npairs] = (unsigned char)cur;
+            ++s.npairs;
+        }
+    }
+    // the kernels take the canonical schedule: accumulator a holds diagonal
+    // a + 2, exact for a < NEXACT (shift >= 10), FP32-summed otherwise
+    if (s.nacc != NACC || s.nexact != NEXACT) return false;
+    for (int a = 0; a < NACC; ++a)
+        if (s.shift[a] != DBITS * (DMAX - 2 - a) - TSHIFT) return false;
+    return tbound < std::ldexp(1.0, 62);
 }
 
 #ifdef __CUDACC__

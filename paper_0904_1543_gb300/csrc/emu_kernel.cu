@@ -646,60 +646,9 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
 }
 
 // ------------------------------------------------------------------ host
-// Same digits as the kernel (same functions, same taps) -> exact bounds of
-// every pair's partial sums, and the accumulator grouping.
+// The kernel's schedule for a launch's taps (emu.cuh: build_sched).
 static bool build_sched(int kind, const PassParams<double>& p, Sched& s) {
-    const KindGeom g = kind_geom(kind);
-    int ebf = 0;
-    for (int e = 0; e < 2; ++e)
-        for (int t = 0; t < g.nt; ++t) ebf = std::max(ebf, bexp(p.f[e][t]));
-    const int Ef = scale_of(ebf);
-    // sum over the taps of one output of |filter digit p|, worst parity
-    double sabs[S] = {0};
-    for (int e = 0; e < 2; ++e) {
-        double se[S] = {0};
-        for (int t = 0; t < g.nt; ++t) {
-            int d[S];
-            digits(quantize(p.f[e][t], Ef), d);
-            for (int q = 0; q < S; ++q) se[q] += std::abs(d[q]);
-        }
-        for (int q = 0; q < S; ++q) sabs[q] = std::max(sabs[q], se[q]);
-    }
-    const double lim = 16777216.0;   // 2^24: integers exact in FP32
-    double tbound = 0.0;             // bound of |T'|
-    std::memset(&s, 0, sizeof s);
-    for (int d = 2; d <= DMAX; ++d) {
-        double load = 0.0;
-        int cur = -1;
-        for (int fp = 0; fp < S; ++fp) {
-            const int dq = d - 2 - fp;   // digits are 0-based: (fp + 1) + (dq + 1) = d
-            if (dq < 0 || dq >= S) continue;
-            const double b = sabs[fp] * 512.0;
-            // diagonals that carry weight above 2^-50 must be exact
-            const bool exact = d <= 5;
-            if (cur < 0 || (exact && load + b > lim)) {
-                if (s.nacc >= MAXACC) return false;
-                cur = s.nacc++;
-                s.shift[cur] = DBITS * (DMAX - d) - TSHIFT;
-                s.wlow[cur] = (float)std::ldexp(1.0, s.shift[cur]);
-                if (exact) s.nexact = s.nacc;
-                load = 0.0;
-            }
-            load += b;
-            tbound += b * std::ldexp(1.0, s.shift[cur]);
-            if (s.npairs >= MAXPAIR) return false;
-            s.pp[s.npairs] = (unsigned char)fp;
-            s.pq[s.npairs] = (unsigned char)dq;
-            s.pacc[s.npairs] = (unsigned char)cur;
-            ++s.npairs;
-        }
-    }
-    // the kernels take the canonical schedule: accumulator a holds diagonal
-    // a + 2, exact for a < NEXACT (shift >= 10), FP32-summed otherwise
-    if (s.nacc != NACC || s.nexact != NEXACT) return false;
-    for (int a = 0; a < NACC; ++a)
-        if (s.shift[a] != DBITS * (DMAX - 2 - a) - TSHIFT) return false;
-    return tbound < std::ldexp(1.0, 62);
+    return emu::build_sched(p.f, kind_geom(kind).nt, s);
 }
 
 template <int KIND, int MODE>
