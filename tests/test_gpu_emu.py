@@ -260,3 +260,26 @@ def test_emu_precondition(W):
     x, rr = W.precondition(cuda(G), cuda(eps), g, 3, emu=True)
     ref = PC.precondition_batch(G, eps, n, 3, g.h)
     assert float(np.abs(host(x) - ref).max() / np.abs(ref).max()) < 1e-11
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("emu", [False, True])
+def test_longest_lines(W, axis, emu):
+    """Lines of the largest fine extent (1024 points) along each axis, with
+    the other two axes at their smallest (2 fine points): the native FP64
+    kernels and the tensor-core form against the oracle."""
+    n = [1, 1, 1]
+    n[axis] = 512
+    n = tuple(n)
+    g = W.Grid(n, (0.3, 0.25, 0.35))
+    psi = inputs.orbitals(371, 2, n)
+    V = inputs.gaussian_potential(371, 0, n)
+    occ = np.array([2.0, 1.0])
+    rho = cuda(np.zeros(g.fine))
+    hp, ek, ep = W.hpsi_local(cuda(psi), cuda(V), cuda(occ), g, rho=rho, emu=emu)
+    hp_r, rho_r, ek_r, ep_r = O.hpsi_batch(psi, V, occ, n, g.h)
+    for o in range(2):
+        close(host(hp[o]), hp_r[o], RTOL64, f"hpsi axis {axis} emu {emu}")
+        assert rel(float(ek[o]), ek_r[o]) < RTOL64
+        assert rel(float(ep[o]), ep_r[o]) < RTOL64
+    close(host(rho), rho_r, RTOL64, "rho")
