@@ -143,9 +143,23 @@ struct PassCall {
     bool emu = false;        // FP64 convolutions on the tensor cores (emu.cuh)
 };
 
-static int rowlen_of(int n, int R, const KindGeom& g) {
+// shared-memory row length of a staged line, in elements
+static int rowlen_of(int n, int R, const KindGeom& g, size_t elt) {
     int nch = (n + R - 1) / R;
     int rl = nch * R + g.hl + g.hr;
+    if (elt == 4) {
+        // FP32: the left halo is rounded up to 4 words (16-byte staging of the
+        // interior), windows are read as 16-byte vectors from the chunk start
+        // (past the window by up to 3 words); rows 16-byte aligned, stride
+        // = 4 mod 8 words so the 8 lanes of a 16-byte load phase hit
+        // distinct banks
+        const int hla = (g.hl + 3) / 4 * 4;
+        const int w4 = (R + g.nt - 1 + g.extra + (hla - g.hl) + 3) / 4 * 4;
+        rl = std::max(nch * R + hla + g.hr, nch * R - R + w4);
+        rl = (rl + 3) / 4 * 4;
+        if ((rl & 7) == 0) rl += 4;
+        return rl;
+    }
     if ((rl & 1) == 0) rl += 1;   // odd stride: conflict-free lane-per-line reads
     return rl;
 }
@@ -157,7 +171,7 @@ static bool tune_valid(const PassCall<T>& c, const Tune& t) {
         int n, N;
         pass_dims(d.Nf, c.pass, n, N);
         // the staging buffers must fit
-        if (nbuf(c.mode, t) * ((size_t)t.LT * rowlen_of(n, t.R, g) + 2) * sizeof(T) > 200 * 1024)
+        if (nbuf(c.mode, t) * ((size_t)t.LT * rowlen_of(n, t.R, g, sizeof(T)) + 2) * sizeof(T) > 200 * 1024)
             return false;
         if (c.mode == M_POT) {
             const int nslots = (NTHREADS / 32) * (32 / t.LT);
@@ -225,6 +239,9 @@ static cudaError_t launch_emu_t(int, int, const PassParams<float>&, long long, c
 template <typename T>
 static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
     const KindGeom g = kind_geom(c.kind);
+    // the kernels fix the left halos at compile time (magic filter k0 = -7)
+    if (kind_geom(K_MF).hl != 8 || kind_geom(K_MFT).hl != 7)
+        return fail(WVL_EUNSUPPORTED, "magic filter offset k0 = %d, kernels assume -7", filters().k0);
     const bool emu = c.emu;
     size_t i = 0;
     while (i < c.segs.size()) {
@@ -251,7 +268,7 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             } else {
                 s.nwin = 1;
                 s.tiles = (s.N + tn.LT - 1) / tn.LT;
-                s.rowlen = rowlen_of(s.n, tn.R, g);
+                s.rowlen = rowlen_of(s.n, tn.R, g, sizeof(T));
             }
             long long units = s.norb;
             if (c.mode == M_POT) {

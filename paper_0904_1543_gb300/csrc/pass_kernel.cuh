@@ -24,12 +24,22 @@ namespace wvl {
 
 constexpr int NWARPS = NTHREADS / 32;
 
+// taps, parity offsets, extra window word, left halo (kind_geom on the host
+// gives the same halos; the magic filter's follows from k0 = -7)
 template <int KIND> struct KT;
-template <> struct KT<K_MF>  { static constexpr int NT = 16, OFF0 = 0, OFF1 = 0, EXTRA = 0; };
-template <> struct KT<K_MFT> { static constexpr int NT = 16, OFF0 = 0, OFF1 = 0, EXTRA = 0; };
-template <> struct KT<K_KIN> { static constexpr int NT = 29, OFF0 = 0, OFF1 = 0, EXTRA = 0; };
-template <> struct KT<K_SYN> { static constexpr int NT = 16, OFF0 = 0, OFF1 = 1, EXTRA = 1; };
-template <> struct KT<K_ANA> { static constexpr int NT = 16, OFF0 = 1, OFF1 = 0, EXTRA = 1; };
+template <> struct KT<K_MF>  { static constexpr int NT = 16, OFF0 = 0, OFF1 = 0, EXTRA = 0, HL = 8; };
+template <> struct KT<K_MFT> { static constexpr int NT = 16, OFF0 = 0, OFF1 = 0, EXTRA = 0, HL = 7; };
+template <> struct KT<K_KIN> { static constexpr int NT = 29, OFF0 = 0, OFF1 = 0, EXTRA = 0, HL = 14; };
+template <> struct KT<K_SYN> { static constexpr int NT = 16, OFF0 = 0, OFF1 = 1, EXTRA = 1, HL = 8; };
+template <> struct KT<K_ANA> { static constexpr int NT = 16, OFF0 = 1, OFF1 = 0, EXTRA = 1, HL = 8; };
+
+// Row slot of input position 0: the left halo, rounded up to a 16-byte
+// boundary for FP32 so that the line's interior is staged with 16-byte
+// copies; the window of a chunk then starts D = row_hl - HL words later.
+template <typename T, int KIND>
+__host__ __device__ constexpr int row_hl() {
+    return sizeof(T) == 4 ? (KT<KIND>::HL + 3) / 4 * 4 : KT<KIND>::HL;
+}
 
 // compensated single-precision accumulation (Knuth two-sum)
 struct FF { float hi, lo; };
@@ -93,6 +103,15 @@ __device__ __forceinline__ void cp_async_or_zero(T* smem_dst, const T* gsrc, boo
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gsrc),
                      "r"(nbytes) : "memory");
 }
+// 16 or 8 bytes, both addresses aligned to the size
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -104,6 +123,31 @@ __device__ __forceinline__ void conv_chunk(const T* __restrict__ srow,
                                            const PassParams<T>& p, T (&acc)[R]) {
     constexpr int NT = KT<KIND>::NT;
     constexpr int W = R + NT - 1 + KT<KIND>::EXTRA;
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the window in 16-byte loads from the chunk's aligned start
+        // (rows and chunks are 16-byte aligned, and the row stride keeps the
+        // 8 lanes of a phase on distinct banks); the taps begin D words in
+        constexpr int D = row_hl<T, KIND>() - KT<KIND>::HL;
+        constexpr int W4 = (W + D + 3) / 4 * 4;
+        float win[W4];
+        #pragma unroll
+        for (int q = 0; q < W4 / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(srow)[q];
+            win[4 * q] = v.x;
+            win[4 * q + 1] = v.y;
+            win[4 * q + 2] = v.z;
+            win[4 * q + 3] = v.w;
+        }
+        #pragma unroll
+        for (int j = 0; j < W; ++j) {
+            #pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int t = j - r - ((r & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
+                if (t >= 0 && t < NT) acc[r] = fmaf(p.f[r & 1][t], win[j + D], acc[r]);
+            }
+        }
+        return;
+    }
     #pragma unroll
     for (int j = 0; j < W; ++j) {
         const T v = srow[j];
@@ -178,10 +222,11 @@ __device__ __forceinline__ Job next_job(const PassParams<T>& p, const Job& J) {
 }
 
 // Issue the copies of job J's lines (and wrapped halos) into buf.
-template <typename T, int MODE>
+template <typename T, int KIND, int MODE>
 __device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* buf) {
     const Seg<T>& S = p.seg[J.si];
-    const int n = S.n, rowlen = S.rowlen, hl = p.hl, LT = p.LT;
+    constexpr int hl = row_hl<T, KIND>();
+    const int n = S.n, rowlen = S.rowlen, LT = p.LT;
     const int a0 = J.tile * LT;
     const int lt = min(LT, S.N - a0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -228,6 +273,30 @@ __device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* b
                     while (x >= n) x -= n;
                 }
             }
+        } else if (sizeof(T) == 4) {
+            // FP32: groups of four row slots; 16-byte copies where the source
+            // is 16-byte aligned and does not wrap, 8-byte where it is even
+            const T* src = S.in + (long long)J.orb * P + (long long)a * n;
+            const bool lines4 = (n & 3) == 0;   // every line starts 16-byte aligned
+            #pragma unroll 1
+            for (int j = 4 * lane; j < rowlen; j += 128) {
+                int x4 = (j - hl) % n;
+                if (x4 < 0) x4 += n;
+                if (lines4 && (x4 & 3) == 0 && x4 + 3 < n && j + 3 < rowlen) {
+                    cp_async16(row + j, src + x4);
+                } else if ((n & 1) == 0 && (x4 & 1) == 0 && x4 + 3 < n && j + 3 < rowlen) {
+                    cp_async8(row + j, src + x4);
+                    cp_async8(row + j + 2, src + x4 + 2);
+                } else {
+                    #pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (j + e >= rowlen) break;
+                        int xe = x4 + e;
+                        while (xe >= n) xe -= n;
+                        cp_async(row + j + e, src + xe);
+                    }
+                }
+            }
         } else {
             const T* src = S.in + (long long)J.orb * P + (long long)a * n;
             #pragma unroll 1
@@ -248,7 +317,8 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
     __shared__ double red[NWARPS];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int LT = p.LT, hl = p.hl;
+    const int LT = p.LT;
+    constexpr int hl = row_hl<T, KIND>();   // row slot of input position 0
     const int spw = 32 / LT;
     const int line = lane & (LT - 1);
     const int slot = warp * spw + lane / LT;
@@ -258,7 +328,7 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
 
     Job cur = make_job<T, MODE>(p, blockIdx.x);
     if (!cur.valid) return;
-    stage<T, MODE>(p, cur, bufs);
+    stage<T, KIND, MODE>(p, cur, bufs);
     cp_commit();
 
     Acc<T> racc[CPT][R];   // M_POT: density per owned output, across a unit's orbitals
@@ -268,7 +338,7 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
     while (true) {
         const Job nxt = next_job<T, MODE>(p, cur);
         if (nxt.valid) {
-            stage<T, MODE>(p, nxt, bufs + (b ^ 1) * p.bufelems);
+            stage<T, KIND, MODE>(p, nxt, bufs + (b ^ 1) * p.bufelems);
             cp_commit();
             cp_wait<1>();
         } else {
