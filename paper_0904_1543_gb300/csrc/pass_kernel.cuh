@@ -278,10 +278,11 @@ __device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* b
             // is 16-byte aligned and does not wrap, 8-byte where it is even
             const T* src = S.in + (long long)J.orb * P + (long long)a * n;
             const bool lines4 = (n & 3) == 0;   // every line starts 16-byte aligned
+            int x4 = (4 * lane - hl) % n;         // source of row slot j, kept in [0, n)
+            if (x4 < 0) x4 += n;
             #pragma unroll 1
-            for (int j = 4 * lane; j < rowlen; j += 128) {
-                int x4 = (j - hl) % n;
-                if (x4 < 0) x4 += n;
+            for (int j = 4 * lane; j < rowlen; j += 128, x4 += 128) {
+                while (x4 >= n) x4 -= n;
                 if (lines4 && (x4 & 3) == 0 && x4 + 3 < n && j + 3 < rowlen) {
                     cp_async16(row + j, src + x4);
                 } else if ((n & 1) == 0 && (x4 & 1) == 0 && x4 + 3 < n && j + 3 < rowlen) {
@@ -399,6 +400,19 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                 }
                 conv_chunk<T, KIND, R>(srow_line + i0, p, acc);
                 if (!line_ok) continue;
+                if (MODE == M_PLAIN || MODE == M_UNCOMP) {
+                    // transposed store: output I of this line at I * N
+                    T* op = S.out + obase + (long long)i0 * N + a0 + line;
+                    if (i0 + R <= n) {
+                        #pragma unroll
+                        for (int r = 0; r < R; ++r) op[(long long)r * N] = acc[r];
+                    } else {
+                        #pragma unroll
+                        for (int r = 0; r < R; ++r)
+                            if (i0 + r < n) op[(long long)r * N] = acc[r];
+                    }
+                    continue;
+                }
                 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int I = i0 + r;
