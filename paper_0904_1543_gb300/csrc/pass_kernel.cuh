@@ -116,6 +116,30 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// R consecutive elements of one line from global memory; 16-byte loads when
+// all R exist and the line start is 16-byte aligned (vec)
+template <typename T, int R>
+__device__ __forceinline__ void load_run(const T* __restrict__ src, int i, int n, bool vec,
+                                         T (&v)[R]) {
+    if (vec && i + R <= n) {
+        constexpr int PER = 16 / (int)sizeof(T);
+        #pragma unroll
+        for (int q = 0; q < R / PER; ++q) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 f = reinterpret_cast<const float4*>(src + i)[q];
+                v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+            } else {
+                const double2 d = reinterpret_cast<const double2*>(src + i)[q];
+                v[2 * q] = d.x; v[2 * q + 1] = d.y;
+            }
+        }
+        return;
+    }
+    #pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (i + r < n) v[r] = src[i + r];
+}
+
 // R outputs of one line from the shared-memory row (srow[j] <-> position
 // i0 - HL + j); acc must hold the initial values.
 template <typename T, int KIND, int R>
@@ -367,11 +391,11 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
         #pragma unroll
         for (int r = 0; r < R; ++r) kv[r] = T(0);
         const T* kline = nullptr;
+        // line starts 16-byte aligned: the orbital stride P is a multiple of 8
+        const bool kvec = (n % (16 / (int)sizeof(T))) == 0;
         if (KM && S.in2 != nullptr && line_ok) {
             kline = S.in2 + obase + (long long)(a0 + line) * n;
-            #pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (slot * R + r < n) kv[r] = kline[slot * R + r];
+            load_run<T, R>(kline, slot * R, n, kvec, kv);
         }
 
         // M_POT: CPT * nslots >= nchunks (launcher guarantees), so the outer
@@ -392,12 +416,7 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                     #pragma unroll
                     for (int r = 0; r < R; ++r) acc[r] = me * srow_line[hl + i0 + r];
                 }
-                if (KM && kline != nullptr) {
-                    const int i1 = (c + nslots) * R;
-                    #pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (i1 + r < n) kv[r] = kline[i1 + r];
-                }
+                if (KM && kline != nullptr) load_run<T, R>(kline, (c + nslots) * R, n, kvec, kv);
                 conv_chunk<T, KIND, R>(srow_line + i0, p, acc);
                 if (!line_ok) continue;
                 if (MODE == M_PLAIN || MODE == M_UNCOMP) {
@@ -413,11 +432,12 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                     }
                     continue;
                 }
+                const long long oidx0 = (long long)i0 * N + a0 + line;
                 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int I = i0 + r;
                     if (I >= n) continue;
-                    const long long oidx = (long long)I * N + a0 + line;
+                    const long long oidx = oidx0 + (long long)r * N;
                     if (MODE == M_PLAIN || MODE == M_UNCOMP) {
                         S.out[obase + oidx] = acc[r];
                     } else if (MODE == M_COMP) {
