@@ -54,7 +54,7 @@ def workload(per_cell):
 
 
 WORKLOAD = workload(PER_CELL)
-# FP64-pipe operations per fine point of the chain (FMA = 1 op)
+# FP64-pipe operations per fine point of one kinetic pass (an FMA counts as one)
 KIN_OPS_PER_POINT_PER_PASS = 29
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of GB300 (2 flops per DFMA)
 
