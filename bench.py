@@ -624,8 +624,8 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     kin_avg_s = kin_ms * 1e-3 / max(kin_launches * 3, 1)
     achieved = flops_per_launch / kin_avg_s / 1e12 if kin_launches else None
     # DRAM bytes of one kinetic pass-1 launch from an ncu capture of the small
-    # profiling case (profiles/kinetic_pass_fp64_small36.md), scaled to this
-    # launch by the fine points processed; null for any other workload.
+    # profiling case (36 orbitals, 33.6 M fine points, --per-cell 12), scaled
+    # to this launch by the fine points processed; null for any other workload.
     traffic = (1030.6e6 * pts / 33619968) if (args.per_cell == PER_CELL and args.prec == "f64") else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
