@@ -96,6 +96,13 @@ unsigned long long wvl_kernel_launches(void);
  * Returns WVL_ETIMEOUT when the count is nonzero, WVL_OK otherwise. */
 wvl_status wvl_wait_timeouts(unsigned* count);
 
+/* Self-test of that expiry path: enqueues one kernel whose bounded wait (an
+ * mbarrier nothing arrives on) gives up after about `ms` milliseconds of
+ * SM clock and counts one expiry, so that wvl_wait_timeouts() then reports
+ * WVL_ETIMEOUT with count 1.  No fault, no hang; the context stays usable.
+ * No counterpart in the paper.  WVL_EINVAL unless 0 < ms <= 10000. */
+wvl_status wvl_selftest_timeout(double ms, void* stream);
+
 /*
  * Filters derived by the library (host computation, no GPU needed), FP64.
  *  h[16], g[16]: h_j, g_j for j = -7..8 (Eq. refinement, g_j = (-1)^j h_{1-j});

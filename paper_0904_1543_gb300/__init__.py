@@ -78,6 +78,7 @@ def _declare(L):
         "wvl_device_count": (ctypes.c_int, []),
         "wvl_kernel_launches": (ctypes.c_ulonglong, []),
         "wvl_wait_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
+        "wvl_selftest_timeout": (ctypes.c_int, [ctypes.c_double, _vp]),
         "wvl_filters": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
         "wvl_workspace_size": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_sz)]),
         "wvl_synthesis": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
@@ -139,6 +140,13 @@ def device_count():
 def kernel_launches():
     """Kernels enqueued by the library so far in this process."""
     return lib().wvl_kernel_launches()
+
+
+def selftest_timeout(ms=5.0, device=None):
+    """Enqueue one kernel whose bounded wait cannot be satisfied: it gives up
+    after about ms and counts one expiry (see wait_timeouts)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    _check(lib().wvl_selftest_timeout(float(ms), _stream(dev)))
 
 
 def wait_timeouts():

@@ -1009,6 +1009,13 @@ int wvl_version(void) { return 10000; }
 
 unsigned long long wvl_kernel_launches(void) { return g_launches.load(); }
 
+wvl_status wvl_selftest_timeout(double ms, void* stream) {
+    g_err[0] = 0;
+    if (!(ms > 0.0) || ms > 10000.0) return fail(WVL_EINVAL, "ms must be in (0, 10000]");
+    cudaError_t e = emu_wait_probe(ms, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? WVL_OK : cuda_fail(e, "timeout self-test");
+}
+
 wvl_status wvl_wait_timeouts(unsigned* count) {
     g_err[0] = 0;
     if (!count) return fail(WVL_EINVAL, "count is NULL");

@@ -229,5 +229,7 @@ cudaError_t launch_pass_emu(int kind, int mode, const PassParams<double>& p, lon
 cudaError_t prepare_emu_kernels();
 // bounded waits of the emulated passes that ran out since the last call
 cudaError_t emu_take_timeouts(unsigned* count);
+// one bounded wait that cannot be satisfied, given up after about ms
+cudaError_t emu_wait_probe(double ms, cudaStream_t st);
 
 }  // namespace wvl

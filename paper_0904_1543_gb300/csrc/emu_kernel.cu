@@ -750,6 +750,40 @@ cudaError_t prepare_emu_kernels() {
     return ensure_emu_attr<K_KIN, M_KLAST>();
 }
 
+namespace emu {
+// An mbarrier that nothing arrives on, waited for with a bound of `cycles`:
+// the expiry path of the bounded waits, exercised without a fault.
+__global__ void wait_probe_kernel(long long cycles) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&bar)), "r"(1));
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(su32(&bar)), "r"(0u) : "memory");
+        if (ok) return;
+        if (clock64() - t0 > cycles) {
+            atomicAdd(&g_emu_timeouts, 1u);
+            return;
+        }
+    }
+}
+}  // namespace emu
+
+cudaError_t emu_wait_probe(double ms, cudaStream_t st) {
+    int dev = 0, khz = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0)
+        khz = 2000000;   // SM clock unknown: assume 2 GHz
+    const long long cycles = (long long)(ms * (double)khz);
+    emu::wait_probe_kernel<<<1, 32, 0, st>>>(cycles);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t emu_take_timeouts(unsigned* count) {
     unsigned v = 0, z = 0;
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_emu_timeouts, sizeof v);
