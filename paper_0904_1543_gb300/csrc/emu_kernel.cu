@@ -1,22 +1,25 @@
 // The emulated FP64 pass (see emu.cuh for the arithmetic) as a tcgen05
 // kernel for sm_103a.
 //
-// Work unit: (orbital -- or orbital group for the potential pass --, tile of
-// 128 lines, window of 32 outputs).  A persistent CTA of 128 threads walks
-// its units; per orbital it
-//   1. reads the window's K input positions of its 128 lines (wrapped
-//      periodically, or gathered from the compressed layout in synthesis
-//      pass 1), one warp per line, takes the line's largest exponent with a
-//      warp reduction and writes the six FP16 digit planes into shared memory
-//      in the MMA's K-major layout (8 x 16 B core matrices);
-//   2. one thread issues the digit-pair MMAs (M = 128, N = 32 or 16, K = 16)
-//      into FP32 accumulators in tensor memory and commits them to an
-//      mbarrier;
-//   3. after a bounded wait, thread r (= TMEM lane r = line r) loads its
-//      accumulators, recombines them into 64-bit integers, scales to FP64
-//      and runs the pass's epilogue (transposed store, compressed scatter,
-//      V psi with density and Epot, kinetic K_p and Ekin) exactly as the
-//      FP64 pass does.
+// A window is 128 lines x N outputs (N = 32, or 16 for the kinetic filter)
+// reading 48 input positions, three 16-position slabs.  A work unit is a
+// whole 128-line tile of one orbital, walked window by window (in the
+// potential pass: one window of an orbital group, so that the density sums
+// stay in registers across the group's orbitals).  A persistent CTA of 256
+// threads, two per SM, per window
+//   1. slices the window's new slabs: reads them (wrapped periodically, or
+//      gathered from the compressed layout in synthesis pass 1), scales every
+//      line by its largest exponent (taken once per unit), and writes six
+//      FP16 digit planes into a ring of three slab slots in shared memory, in
+//      the MMA's K-major layout (8 x 16 B core matrices);
+//   2. issues, from one thread, the 26 digit-pair x 3 K-step MMAs
+//      (M = 128, N, K = 16) into seven FP32 accumulators in tensor memory and
+//      commits them to an mbarrier, polled with a bound; meanwhile every
+//      thread loads the epilogue's other inputs;
+//   3. reads the accumulators (warp w: lines 32 (w % 4) + lane, half of the
+//      outputs), recombines them into 64-bit integers, scales to FP64 and
+//      runs the pass's epilogue (transposed store, compressed scatter, V psi
+//      with density and Epot, kinetic K_p and Ekin) as the FP64 pass does.
 // The filter digit planes are built once per CTA from the launch's taps.
 #include <cmath>
 
@@ -79,11 +82,6 @@ __device__ __forceinline__ void tld8(uint32_t addr, uint32_t (&v)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
                    "=r"(v[6]), "=r"(v[7])
-                 : "r"(addr));
-}
-__device__ __forceinline__ void tld4(uint32_t addr, uint32_t (&v)[4]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
                  : "r"(addr));
 }
 __device__ __forceinline__ void tld_wait() {
