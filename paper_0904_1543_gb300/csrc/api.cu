@@ -260,10 +260,9 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             Seg<T>& s = d.s;
             pass_dims(d.Nf, c.pass, s.n, s.N);
             if (emu) {
-                // units: 128-line tiles (the kernel walks their output
-                // windows); in the potential pass tiles x windows
+                // units: 128-line tiles (the kernel walks their output windows)
                 s.nwin = (s.n + emu::window_n(c.kind) - 1) / emu::window_n(c.kind);
-                s.tiles = (s.N + emu::M - 1) / emu::M * (c.mode == M_POT ? s.nwin : 1);
+                s.tiles = (s.N + emu::M - 1) / emu::M;
                 s.rowlen = 0;
             } else {
                 s.nwin = 1;

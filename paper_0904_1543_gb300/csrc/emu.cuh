@@ -51,11 +51,10 @@ constexpr int NACC = 7;
 constexpr int NEXACT = 4;
 constexpr int QBITS = DBITS * S - 1;   // |X| < 2^QBITS
 // byte stride between the 8-position chunks of one operand plane: the MMA's
-// leading-dimension offset.  A: 128 rows of 16 B plus a bank skew that keeps
-// the digit stores conflict-free for the way each pass slices (a whole
-// window per line in the potential pass: 16 B; 16-position slabs of four
-// lines per warp instruction otherwise: 64 B).
-__host__ __device__ constexpr int lboa(int mode) { return M * 16 + (mode == M_POT ? 16 : 64); }
+// leading-dimension offset.  A: 128 rows of 16 B plus a 64 B bank skew that
+// keeps the digit stores (16-position slabs, four lines per warp
+// instruction) conflict-free.
+__host__ __device__ constexpr int lboa(int) { return M * 16 + 64; }
 // T' = (sum of the kept diagonals) / 2^(DBITS (2S - DMAX) + TSHIFT): the
 // accumulator of diagonal d enters shifted by DBITS (DMAX - d) - TSHIFT
 // (right shifts rounded); the host checks that T' stays below 2^62

@@ -124,11 +124,10 @@ __device__ __forceinline__ void decode_unit(const PassParams<double>& p, int mod
     J.si = si;
     J.grp = (int)(loc / S.tiles);
     J.tt = (int)(loc - (long long)J.grp * S.tiles);
-    // potential pass: unit = (orbital group, tile, window); otherwise the
-    // unit is a whole tile of lines and the kernel walks its windows
-    const int tile = (mode == M_POT) ? J.tt / S.nwin : J.tt;
-    J.a0 = tile * M;
-    J.o = (mode == M_POT) ? J.tt - tile * S.nwin : 0;   // window index
+    // unit = (orbital, or orbital group in the potential pass) x a whole
+    // tile of lines; the kernel walks the tile's windows
+    J.a0 = J.tt * M;
+    J.o = 0;
     J.lt = min(M, S.N - J.a0);
     if (mode == M_POT) {
         J.orb = J.grp * S.opg;
@@ -207,10 +206,12 @@ __device__ __forceinline__ void store_pair_digits(unsigned char* Asm, int apl, i
 
 // The epilogue's other inputs for this thread's outputs (line er, outputs
 // o0 .. o0 + N/2 - 1), loaded while the MMAs run: the kinetic passes' G and
-// K_{p-1} (line-major, 16-byte loads) and K_0, the potential pass's V.
+// K_{p-1} (line-major, 16-byte loads) and K_0; the potential pass's V and
+// the density accumulated so far.
 template <int KIND, int MODE>
 __device__ __forceinline__ void prefetch_epilogue(const Seg<double>& Sg, int o0, int er, int lt,
-                                                  int a0, int orb, double (&pa)[window_n(KIND) / 2],
+                                                  int a0, int orb, int grp,
+                                                  double (&pa)[window_n(KIND) / 2],
                                                   double (&pb)[window_n(KIND) / 2],
                                                   double (&pc)[window_n(KIND) / 2]) {
     constexpr int NH = window_n(KIND) / 2;
@@ -250,10 +251,19 @@ __device__ __forceinline__ void prefetch_epilogue(const Seg<double>& Sg, int o0,
 #pragma unroll
             for (int c = 0; c < NH; ++c)
                 if (o0 + c < n) pc[c] = Sg.aux[obase + (long long)(o0 + c) * NL + a];
-    } else if (MODE == M_POT && Sg.aux) {
+    } else if (MODE == M_POT) {
+        if (Sg.aux)
 #pragma unroll
-        for (int c = 0; c < NH; ++c)
-            if (o0 + c < n) pa[c] = Sg.aux[(long long)(o0 + c) * NL + a];
+            for (int c = 0; c < NH; ++c)
+                if (o0 + c < n) pa[c] = Sg.aux[(long long)(o0 + c) * NL + a];
+        // the density so far: the caller's rho, or this group's partial
+        // after the group's first orbital
+        if (Sg.rho != nullptr && (Sg.rho_gstride == 0 || orb != grp * Sg.opg)) {
+            const double* rp = Sg.rho + (long long)grp * Sg.rho_gstride;
+#pragma unroll
+            for (int c = 0; c < NH; ++c)
+                if (o0 + c < n) pc[c] = rp[(long long)(o0 + c) * NL + a];
+        }
     }
 }
 
@@ -261,8 +271,7 @@ __device__ __forceinline__ void prefetch_epilogue(const Seg<double>& Sg, int o0,
 // accumulators -> FP64 -> the pass's epilogue; returns the energy partial
 template <int KIND, int MODE>
 __device__ __forceinline__ double window_epilogue(const Seg<double>& Sg, uint32_t tl, int o0,
-                                                  int er, int lt, int a0, int orb, int se,
-                                                  double (&racc)[window_n(KIND) / 2],
+                                                  int er, int lt, int a0, int orb, int grp, int se,
                                                   const double (&pa)[window_n(KIND) / 2],
                                                   const double (&pb)[window_n(KIND) / 2],
                                                   const double (&pc)[window_n(KIND) / 2]) {
@@ -336,7 +345,10 @@ __device__ __forceinline__ double window_epilogue(const Seg<double>& Sg, uint32_
                     if (Sg.out) Sg.out[obase + oidx] = y;
                     eacc = fma(y, val, eacc);
                 }
-                racc[c] = fma(occ * val, val, racc[c]);
+                // the unit owns these density elements: one thread updates
+                // each, orbital after orbital, in a fixed order
+                if (Sg.rho != nullptr)
+                    Sg.rho[(long long)grp * Sg.rho_gstride + oidx] = fma(occ * val, val, pc[c]);
             }
         }
     }
@@ -367,10 +379,6 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
     constexpr int NH = N / 2;                // outputs per epilogue thread
     constexpr int RPW = M / WARPS;           // lines per slicing warp
     constexpr int NSLOT = K / 16;            // 16-position slabs per window (3)
-    // a line unit (all windows of 128 lines of one orbital) slices every
-    // input once; the potential pass keeps one unit per window so that its
-    // density sums stay in registers across the orbitals of a group
-    constexpr bool LINE = MODE != M_POT;
     static_assert(K == 48 && N % 16 == 0 && (HA - (KIND == K_KIN ? 0 : 8)) % 16 == 0, "window");
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* const Asm = sm;                // [S][APL]: NSLOT slab slots of 2 chunks
@@ -421,9 +429,6 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
     const uint32_t a_base = su32(Asm), b_base = su32(Bsm);
     uint32_t phase = 0;
     bool failed = false;
-    double racc[NH];
-#pragma unroll
-    for (int c = 0; c < NH; ++c) racc[c] = 0.0;
 
     // MMAs of one window, then the wait: one thread polls, the others sleep
     // in the barrier instead of taking issue slots from the co-resident CTA
@@ -452,7 +457,7 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
     while (J.valid) {
         const Seg<double>& Sg = p.seg[J.si];
         const int n = Sg.n;
-        if constexpr (LINE) {
+        {
             // ---------------------------- one exponent per line (whole line)
 #pragma unroll 1
             for (int i = 0; i < RPW; i += 4) {
@@ -544,88 +549,26 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
                 }
                 issue_mmas(((s0 % NSLOT) + NSLOT) % NSLOT);
                 double pa[NH], pb[NH], pc[NH];
-                prefetch_epilogue<KIND, MODE>(Sg, o + NH * half, er, J.lt, J.a0, J.orb, pa, pb, pc);
+                prefetch_epilogue<KIND, MODE>(Sg, o + NH * half, er, J.lt, J.a0, J.orb, J.grp, pa,
+                                              pb, pc);
 
                 if (!wait_mmas()) {
                     failed = true;
                     break;
                 }
                 eacc += window_epilogue<KIND, MODE>(Sg, tl, o + NH * half, er, J.lt, J.a0, J.orb,
-                                                    rowE[er] + Ef - OUT_EXP, racc, pa, pb, pc);
+                                                    J.grp, rowE[er] + Ef - OUT_EXP, pa, pb, pc);
                 fence_before();
                 __syncthreads();   // accumulators are rewritten by the next window's MMAs
             }
             if (failed) break;
-            if (MODE == M_KLAST) {
+            if (MODE == M_KLAST || (MODE == M_POT && Sg.aux)) {
                 const double t = cta_sum(eacc, red);
                 if (tid == 0) Sg.part[(long long)J.orb * Sg.tiles + J.tt] = t;
                 __syncthreads();
             }
-            __syncthreads();   // rowE and the slab ring are reused by the next unit
+            __syncthreads();   // rowE and the slab ring are reused by the next job
             next_job(p, MODE, J);
-        } else {
-            // ---------------------------- one window of one orbital
-            const int o = J.o * N;
-            const bool lane_on = 2 * lane < K;
-            int x0 = (o - HA + 2 * lane) % n;
-            if (x0 < 0) x0 += n;
-            int x1 = x0 + 1;
-            if (x1 >= n) x1 -= n;
-#pragma unroll 1
-            for (int rb = 0; rb < RPW; rb += 8) {
-                double v[8][2];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int r = warp + WARPS * (rb + i);
-                    v[i][0] = v[i][1] = 0.0;
-                    if (r < J.lt && lane_on) {
-                        v[i][0] = load_in<MODE>(Sg, J.orb, J.a0 + r, x0);
-                        v[i][1] = load_in<MODE>(Sg, J.orb, J.a0 + r, x1);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int r = warp + WARPS * (rb + i);
-                    const int eb = __reduce_max_sync(0xffffffffu,
-                                                     (unsigned)max(bexp(v[i][0]), bexp(v[i][1])));
-                    const int E = scale_of(eb);
-                    if (lane == 0) rowE[r] = E;
-                    if (lane_on)
-                        store_pair_digits<LBOA>(Asm, APL, lane >> 2, r, lane & 3, v[i][0], v[i][1], E);
-                }
-            }
-            issue_mmas(0);
-            double pa[NH], pb[NH], pc[NH];
-            prefetch_epilogue<KIND, MODE>(Sg, o + NH * half, er, J.lt, J.a0, J.orb, pa, pb, pc);
-            if (!wait_mmas()) {
-                failed = true;
-                break;
-            }
-            const double eacc = window_epilogue<KIND, MODE>(Sg, tl, o + NH * half, er, J.lt, J.a0,
-                                                            J.orb, rowE[er] + Ef - OUT_EXP, racc,
-                                                            pa, pb, pc);
-            if (Sg.aux) {
-                const double t = cta_sum(eacc, red);
-                if (tid == 0) Sg.part[(long long)J.orb * Sg.tiles + J.tt] = t;
-            }
-            fence_before();
-            __syncthreads();   // planes, accumulators and red are reused by the next job
-            const EJob Jc = J;
-            const bool unit_end = next_job(p, MODE, J);
-            if (unit_end) {
-                if (Sg.rho != nullptr && er < Jc.lt) {
-#pragma unroll
-                    for (int c = 0; c < NH; ++c) {
-                        const int I = Jc.o * N + NH * half + c;
-                        if (I >= n) continue;
-                        const long long oidx = (long long)I * Sg.N + Jc.a0 + er;
-                        if (Sg.rho_gstride == 0) Sg.rho[oidx] += racc[c];
-                        else Sg.rho[(long long)Jc.grp * Sg.rho_gstride + oidx] = racc[c];
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < NH; ++c) racc[c] = 0.0;
-            }
         }
     }
 
