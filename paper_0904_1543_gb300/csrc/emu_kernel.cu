@@ -3,10 +3,9 @@
 //
 // A window is 128 lines x N outputs (N = 32, or 16 for the kinetic filter)
 // reading 48 input positions, three 16-position slabs.  A work unit is a
-// whole 128-line tile of one orbital, walked window by window (in the
-// potential pass: one window of an orbital group, so that the density sums
-// stay in registers across the group's orbitals).  A persistent CTA of 256
-// threads, two per SM, per window
+// whole 128-line tile of one orbital (of each orbital of a group in turn in
+// the potential pass, whose density partial it updates in place), walked
+// window by window.  A persistent CTA of 256 threads, two per SM, per window
 //   1. slices the window's new slabs: reads them (wrapped periodically, or
 //      gathered from the compressed layout in synthesis pass 1), scales every
 //      line by its largest exponent (taken once per unit), and writes six
