@@ -59,6 +59,20 @@ KIN_OPS_PER_POINT_PER_PASS = 29
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of GB300 (2 flops per DFMA)
 
 
+def _measured_hbm_gbs(default=6758.5):
+    """Copy bandwidth measured on this GPU type (MEASURED_PEAKS.json beside
+    this file), else the value it held when this file was written."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return default
+
+
+HBM_GBS = _measured_hbm_gbs()
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -299,6 +313,7 @@ def measure_variants(args, W, torch, dev):
         res[name] = (ms, hp, ek, ep, rho[0])
         del plan
     ms32, hp32, ek32, ep32, rho32 = res["f32"]
+    pts32 = norb * 8 * n[0] * n[1] * n[2]
     ms64, hp64, ek64, ep64, rho64 = res["f64"]
     mse, hpe, eke, epe, rhoe = res["emu"]
     # oracle on two sampled orbitals (FP64 arithmetic on the FP32-rounded inputs)
@@ -320,6 +335,12 @@ def measure_variants(args, W, torch, dev):
         "value": norb / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
         "fp64_same_workload": {"value": norb / (ms64 * 1e-3), "ms_per_step": ms64},
         "speedup_over_fp64": ms64 / ms32,
+        # HBM-bound: 140 B per orbital-point moved by the 15 FP32 passes (4 B
+        # in and out per pass; the kinetic passes also carry K and G, 44 B)
+        "roofline": {"bound": "hbm", "achieved": 140.0 * pts32 / (ms32 * 1e-3) / 1e9,
+                     "peak": HBM_GBS, "unit": "GB/s",
+                     "frac": 140.0 * pts32 / (ms32 * 1e-3) / 1e9 / HBM_GBS,
+                     "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"},
         "rel_err_hpsi_vs_oracle": err_h, "rel_err_energies_vs_oracle": err_e,
         "rel_err_rho_vs_fp64_gpu": err_rho,
         "error_sample": "H psi and energies: orbitals 0 and 255 against the FP64 oracle; "
