@@ -117,3 +117,24 @@ def test_plan_creation_and_offsets():
         W.Plan(cells, [0, 2], prec=0)
     with pytest.raises(W.WvlError):
         W.Plan(cells, [0], prec=3)
+
+
+def test_tensor_core_form_validation():
+    """WVL_F64_EMU takes FP64 arrays: the same workspace as WVL_F64, and the
+    same argument checks; other precision codes are refused."""
+    g = W.Grid((8, 6, 4))
+    assert W.workspace_size(g, W.WVL_F64_EMU, 3) == W.workspace_size(g, W.WVL_F64, 3)
+    L = W.lib()
+    sz = ctypes.c_size_t(0)
+    assert L.wvl_workspace_size(ctypes.byref(g.c()), 3, 1, ctypes.byref(sz)) == 1   # EINVAL
+    st = L.wvl_hpsi_local(ctypes.byref(g.c()), W.WVL_F64_EMU, 1, None, None, None, None, None,
+                          None, None, None, 0, None)
+    assert st == 1                                                             # EINVAL (NULL)
+
+
+def test_timeout_selftest_arguments():
+    L = W.lib()
+    assert L.wvl_selftest_timeout(-1.0, None) == 1
+    assert L.wvl_selftest_timeout(0.0, None) == 1
+    assert L.wvl_selftest_timeout(1e9, None) == 1
+    assert L.wvl_wait_timeouts(None) == 1
