@@ -110,6 +110,13 @@ struct Tune {
     bool persist = false;   // persistent double-buffered grid vs one CTA per job
 };
 
+// FP32 potential pass: compensated density sums in shared memory, one float
+// pair per (output, line) of a tile
+template <typename T>
+static size_t pot_smem(int mode, int LT, int n) {
+    return (mode == M_POT && sizeof(T) == 4) ? (size_t)LT * n * 8 : 0;
+}
+
 // one staging buffer per CTA unless it prefetches (persistent grid, or the
 // orbital walk of the potential pass)
 static int nbuf(int mode, const Tune& t) { return (t.persist || mode == M_POT) ? 2 : 1; }
@@ -170,10 +177,11 @@ static bool tune_valid(const PassCall<T>& c, const Tune& t) {
     for (const auto& d : c.segs) {
         int n, N;
         pass_dims(d.Nf, c.pass, n, N);
-        // the staging buffers must fit
-        if (nbuf(c.mode, t) * ((size_t)t.LT * rowlen_of(n, t.R, g, sizeof(T)) + 2) * sizeof(T) > 200 * 1024)
+        // the staging buffers (and the FP32 potential pass's density sums) must fit
+        if (nbuf(c.mode, t) * ((size_t)t.LT * rowlen_of(n, t.R, g, sizeof(T)) + 2) * sizeof(T) +
+                pot_smem<T>(c.mode, t.LT, n) > 200 * 1024)
             return false;
-        if (c.mode == M_POT) {
+        if (c.mode == M_POT && sizeof(T) == 8) {
             const int nslots = (NTHREADS / 32) * (32 / t.LT);
             const int cpt = pot_out<T>() / t.R;
             if ((long long)cpt * nslots < (n + t.R - 1) / t.R) return false;
@@ -252,6 +260,7 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
         p.LT = emu ? emu::M : tn.LT;
         long long blk = 0;
         size_t smem = 0;
+        int nmax = 0;
         int k = 0;
         const size_t first = i;
         for (; i < c.segs.size() && k < MAXSEG; ++i, ++k) {
@@ -271,7 +280,10 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             }
             long long units = s.norb;
             if (c.mode == M_POT) {
-                const long long want = 4LL * num_sms();
+                // orbital groups: enough units to fill the SMs (the FP32 pass
+                // is latency-bound and fits more CTAs per SM); each group adds
+                // one density partial of P doubles
+                const long long want = (sizeof(T) == 4 ? 16LL : 4LL) * num_sms();
                 int gmax = s.norb;
                 if (d.user_rho) gmax = d.rho_part ? std::min(GMAX, s.norb) : 1;
                 long long G = (want + s.tiles - 1) / s.tiles;
@@ -294,6 +306,7 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             s.blk0 = blk;
             blk += units * s.tiles;
             if (!emu) smem = std::max(smem, (size_t)tn.LT * s.rowlen);
+            nmax = std::max(nmax, s.n);
             p.seg[k] = s;
         }
         p.nseg = k;
@@ -308,7 +321,7 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
         // two staging buffers, each rounded to 16 bytes
         const size_t per16 = 16 / sizeof(T);
         p.bufelems = (int)((smem + per16 - 1) / per16 * per16);
-        smem = nbuf(c.mode, tn) * (size_t)p.bufelems * sizeof(T);
+        smem = nbuf(c.mode, tn) * (size_t)p.bufelems * sizeof(T) + pot_smem<T>(c.mode, tn.LT, nmax);
         cudaError_t e = launch_pass<T>(c.kind, c.mode, tn.R, p, blk, smem, st, tn.persist);
         if (e != cudaSuccess) return cuda_fail(e, "pass launch");
     }

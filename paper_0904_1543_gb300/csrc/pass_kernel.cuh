@@ -349,14 +349,21 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
     const int slot = warp * spw + lane / LT;
     const int nslots = NWARPS * spw;
     constexpr bool KM = (MODE == M_KMID || MODE == M_KLAST);
-    constexpr int CPT = (MODE == M_POT) ? pot_out<T>() / R : 1;
+    // FP32 potential pass: the density sums (compensated pairs) live in
+    // shared memory after the two staging buffers, slot [I][line] owned by
+    // the thread computing output I of that line, which keeps the kernel's
+    // registers (and so its occupancy) at the level of the plain passes; the
+    // FP64 pass keeps them in registers
+    constexpr bool RSM = (MODE == M_POT) && sizeof(T) == 4;
+    constexpr int CPT = (MODE == M_POT && !RSM) ? pot_out<T>() / R : 1;
+    float2* const rsm = reinterpret_cast<float2*>(smem_raw + 2 * (size_t)p.bufelems * sizeof(T));
 
     Job cur = make_job<T, MODE>(p, blockIdx.x);
     if (!cur.valid) return;
     stage<T, KIND, MODE>(p, cur, bufs);
     cp_commit();
 
-    Acc<T> racc[CPT][R];   // M_POT: density per owned output, across a unit's orbitals
+    Acc<T> racc[RSM ? 1 : CPT][RSM ? 1 : R];   // M_POT (FP64): density per owned output
     int b = 0;
 
     #pragma unroll 1
@@ -385,6 +392,8 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
         Acc<T> e;   // energy partial of this orbital
         double occ = 0.0;
         if (MODE == M_POT) occ = S.occ ? S.occ[orb] : 1.0;
+        // FP32 potential pass: the first orbital of the unit starts the sums
+        const bool first_orb = RSM && orb == (int)((cur.unit - S.blk0) / S.tiles) * S.opg;
 
         // K_{p-1} of the thread's next chunk, fetched one chunk ahead
         T kv[R];
@@ -473,7 +482,16 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                             if (S.out) S.out[obase + oidx] = y;
                             e.fma_add(y, psi);
                         }
-                        if (S.rho) racc[cc][r].add((T)occ * psi * psi);
+                        if (RSM) {
+                            if (S.rho) {
+                                float2& q = rsm[I * LT + line];
+                                FF f = first_orb ? FF{0.f, 0.f} : FF{q.x, q.y};
+                                ff_add(f, (float)occ * (float)psi * (float)psi);
+                                q = make_float2(f.hi, f.lo);
+                            }
+                        } else if (S.rho) {
+                            racc[RSM ? 0 : cc][RSM ? 0 : r].add((T)occ * psi * psi);
+                        }
                     }
                 }
             }
@@ -486,7 +504,22 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
 
         // M_POT: the unit ends -> flush its density
         if (MODE == M_POT && (!nxt.valid || nxt.unit != cur.unit)) {
-            if (S.rho != nullptr && line_ok) {
+            if (RSM && S.rho != nullptr && line_ok) {
+                const long long grp = (cur.unit - S.blk0) / S.tiles;
+                #pragma unroll 1
+                for (int c = slot; c < nchunks; c += nslots)
+                    #pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int I = c * R + r;
+                        if (I >= n) continue;
+                        const float2 q = rsm[I * LT + line];
+                        const double v = (double)q.x + (double)q.y;
+                        const long long oidx = (long long)I * N + a0 + line;
+                        if (S.rho_gstride == 0) S.rho[oidx] += v;
+                        else S.rho[grp * S.rho_gstride + oidx] = v;
+                    }
+            }
+            if (!RSM && S.rho != nullptr && line_ok) {
                 const long long grp = (cur.unit - S.blk0) / S.tiles;
                 #pragma unroll
                 for (int cc = 0; cc < CPT; ++cc) {
@@ -496,16 +529,17 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                         const int I = c * R + r;
                         if (c < nchunks && I < n) {
                             const long long oidx = (long long)I * N + a0 + line;
-                            if (S.rho_gstride == 0) S.rho[oidx] += racc[cc][r].get();
-                            else S.rho[grp * S.rho_gstride + oidx] = racc[cc][r].get();
+                            if (S.rho_gstride == 0) S.rho[oidx] += racc[RSM ? 0 : cc][RSM ? 0 : r].get();
+                            else S.rho[grp * S.rho_gstride + oidx] = racc[RSM ? 0 : cc][RSM ? 0 : r].get();
                         }
                     }
                 }
             }
-            #pragma unroll
-            for (int cc = 0; cc < CPT; ++cc)
+            if (!RSM)
                 #pragma unroll
-                for (int r = 0; r < R; ++r) racc[cc][r].reset();
+                for (int cc = 0; cc < CPT; ++cc)
+                    #pragma unroll
+                    for (int r = 0; r < R; ++r) racc[RSM ? 0 : cc][RSM ? 0 : r].reset();
         }
 
         __syncthreads();   // buffer b is refilled by the next iteration's copies
