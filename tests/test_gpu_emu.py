@@ -283,3 +283,44 @@ def test_longest_lines(W, axis, emu):
         assert rel(float(ek[o]), ek_r[o]) < RTOL64
         assert rel(float(ep[o]), ep_r[o]) < RTOL64
     close(host(rho), rho_r, RTOL64, "rho")
+
+
+def test_emu_full_size_sampled(W):
+    """The 192 orbitals of the benchmark workload (coarse 56^3, 48^3, 40^3
+    cells) through a graph-captured WVL_F64_EMU plan, as bench.py times it:
+    one orbital of each cell element by element against the oracle, and
+    sum_I V rho = sum_o occ_o Epot_o on every cell."""
+    import torch
+    sizes = [(56, 56, 56), (48, 48, 48), (40, 40, 40)]
+    cells = [W.Grid(s) for s in sizes]
+    cell_of_orb = [c for c in range(3) for _ in range(64)]
+    plan = W.Plan(cells, cell_of_orb, prec=W.WVL_F64_EMU, graph=True)
+    psi_h = np.concatenate([inputs.orbital(2, o, sizes[c]) for o, c in enumerate(cell_of_orb)])
+    Vs = [inputs.gaussian_potential(2, c, sizes[c]) for c in range(3)]
+    psi = cuda(psi_h)
+    V = [cuda(v) for v in Vs]
+    occ = cuda(np.full(192, 2.0))
+    rho = [torch.zeros(c.fine, dtype=torch.float64, device="cuda") for c in cells]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        hp = torch.empty_like(psi)
+        ek = torch.empty(192, dtype=torch.float64, device="cuda")
+        ep = torch.empty_like(ek)
+        for _ in range(2):         # capture, then replay
+            for r in rho:
+                r.zero_()
+            plan.hpsi(psi, V, occ, hpsi=hp, rho=rho, ekin=ek, epot=ep)
+    torch.cuda.synchronize()
+    ekh, eph = host(ek), host(ep)
+    for o in (7, 64 + 30, 128 + 63):
+        c = cell_of_orb[o]
+        a, b = plan.offsets[o], plan.offsets[o + 1]
+        r = O.hpsi_local(psi_h[a:b], Vs[c], 2.0, sizes[c])
+        close(host(hp[a:b]), r["hpsi_c"], RTOL64, f"orbital {o}")
+        assert rel(ekh[o], r["ekin"]) < RTOL64
+        assert rel(eph[o], r["epot"]) < RTOL64
+    for c in range(3):
+        rh = host(rho[c])
+        assert rh.min() >= 0
+        assert rel(float(np.sum(Vs[c] * rh)), float(np.sum(2.0 * eph[64 * c: 64 * (c + 1)]))) < 1e-11

@@ -209,6 +209,45 @@ def test_hpsi_local_f32(W, n, norb):
     assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < 1e-5
 
 
+def test_f32_full_size_sampled(W):
+    """256 orbitals on a coarse 48^3 cell in FP32 through an autotuned,
+    graph-captured plan (the bench's FP32 form): two orbitals against the
+    oracle (run in FP64 on the FP32-rounded inputs), the density of all 256
+    against the FP64 GPU form, at the FP32 bounds."""
+    import torch
+    n = (48, 48, 48)
+    g = W.Grid(n)
+    norb = 256
+    psi = np.concatenate([inputs.orbital(3, o, n) for o in range(norb)]).astype(np.float32)
+    V = inputs.gaussian_potential(3, 0, n).astype(np.float32)
+    occ = cuda(np.full(norb, 2.0))
+    out = {}
+    for prec, p_, v_ in ((W.WVL_F32, cuda(psi), cuda(V)),
+                         (W.WVL_F64, cuda(psi.astype(np.float64)), cuda(V.astype(np.float64)))):
+        plan = W.Plan([g], [0] * norb, prec=prec, graph=True, autotune=True)
+        rho = [torch.zeros(g.fine, dtype=torch.float64, device="cuda")]
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            plan.autotune(p_, [v_], occ, rho=rho)
+            hp = torch.empty_like(p_)
+            ek = torch.empty(norb, dtype=torch.float64, device="cuda")
+            ep = torch.empty_like(ek)
+            for _ in range(2):
+                rho[0].zero_()
+                plan.hpsi(p_, [v_], occ, hpsi=hp, rho=rho, ekin=ek, epot=ep)
+        torch.cuda.synchronize()
+        out[prec] = (hp, ek, ep, rho[0], plan)
+    hp, ek, ep, rho32, plan = out[W.WVL_F32]
+    for o in (0, norb - 1):
+        a, b = plan.offsets[o], plan.offsets[o + 1]
+        r = O.hpsi_local(psi[a:b].astype(np.float64), V.astype(np.float64), 2.0, n)
+        close(host(hp[a:b]), r["hpsi_c"], 2e-5, f"f32 orbital {o}")
+        assert rel(float(ek[o]), r["ekin"]) < 1e-5
+        assert rel(float(ep[o]), r["epot"]) < 1e-5
+    close(host(rho32), host(out[W.WVL_F64][3]), 1e-5, "f32 rho")
+
+
 @pytest.mark.parametrize("n", [(4, 4, 4), (9, 7, 5)])
 def test_single_ops_f32(W, n):
     g = W.Grid(n)
