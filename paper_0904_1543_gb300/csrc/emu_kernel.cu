@@ -457,14 +457,14 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
         const Seg<double>& Sg = p.seg[J.si];
         const int n = Sg.n;
         {
-            // ---------------------------- one exponent per line (whole line)
+            // ---------------------------- one exponent per line (whole line, 8 lines in flight per warp)
 #pragma unroll 1
-            for (int i = 0; i < RPW; i += 4) {
-                int eb[4] = {0, 0, 0, 0};
+            for (int i = 0; i < RPW; i += 8) {
+                int eb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 1
                 for (int x = 2 * lane; x < n; x += 64) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < 8; ++k) {
                         const int r = warp + WARPS * (i + k);
                         if (r >= J.lt) continue;
                         if (MODE == M_UNCOMP) {
@@ -479,7 +479,7 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < 8; ++k) {
                     const int e = (int)__reduce_max_sync(0xffffffffu, (unsigned)eb[k]);
                     if (lane == 0) rowE[warp + WARPS * (i + k)] = scale_of(e);
                 }
