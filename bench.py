@@ -494,8 +494,9 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     if f32:
         psi_h = psi_h.astype(np.float32)
         Vs_h = [v.astype(np.float32) for v in Vs_h]
+    chain = None if args.chain == "auto" else args.chain
     plan = W.Plan(cells, cell_of_orb, prec=pcode, graph=True,
-                  autotune=not args.no_autotune)
+                  autotune=not args.no_autotune, chain=chain)
     psi = torch.from_numpy(psi_h).to(dev)
     V = [torch.from_numpy(v).to(dev) for v in Vs_h]
     occ = torch.from_numpy(occ_h).to(dev)
@@ -579,7 +580,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
                 bp, bpsi, bhp, brho, bV, bocc = plan, psi, hp, rho, V, occ
             else:
                 bp = W.Plan(cells, cell_of_orb, prec=pcode,
-                            graph=True, autotune=not args.no_autotune)
+                            graph=True, autotune=not args.no_autotune, chain=chain)
                 bpsi, bhp = torch.empty_like(psi), torch.empty_like(hp)
                 brho = [torch.empty_like(r) for r in rho]
                 bV = [torch.empty_like(v) for v in V]
@@ -672,6 +673,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         "roofline": roofline,
         "clocks": clk,
         "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+        "chain": [ln for ln in plan.describe().splitlines() if ln.startswith("chain:")][0][7:],
     }
     if rank == 0 and world == 1 and not args.no_variants and args.prec == "f64":
         line["variants"] = measure_variants(args, W, torch, dev)
@@ -709,6 +711,9 @@ def main():
     ap.add_argument("--prec", choices=["f64", "f32", "f64emu"], default="f64",
                     help="f32 / f64emu run the FP32 / tensor-core FP64 form of the same "
                          "workload (profiling)")
+    ap.add_argument("--chain", choices=["auto", "fused", "passes"], default="auto",
+                    help="kernels of the local Hamiltonian: the autotuner's choice, the fused "
+                         "plane/column kernels, or the transposing 1D passes")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32 and autograd forms reported beside the FP64 line")
     args = ap.parse_args()

@@ -28,7 +28,7 @@ __all__ = [
 ]
 
 WVL_F64, WVL_F32, WVL_F64_EMU = 0, 1, 2
-WVL_PLAN_GRAPH, WVL_PLAN_AUTOTUNE = 1, 2
+WVL_PLAN_GRAPH, WVL_PLAN_AUTOTUNE, WVL_PLAN_FUSED, WVL_PLAN_PASSES = 1, 2, 4, 8
 WVL_NSTAGE = 6
 STAGES = ("synthesis", "magicfilter+potential", "magicfilter_T", "kinetic", "analysis",
           "reductions")
@@ -325,13 +325,18 @@ class Plan:
     (one enqueue of every pass over all cells; optional graph replay and
     autotuning)."""
 
-    def __init__(self, cells, cell_of_orb, prec=WVL_F64, graph=True, autotune=False):
+    def __init__(self, cells, cell_of_orb, prec=WVL_F64, graph=True, autotune=False, chain=None):
+        """chain: None (automatic; the autotuner may choose), "fused" (the
+        plane/column kernels) or "passes" (the transposing 1D passes)."""
         self.cells = [c if isinstance(c, Grid) else Grid(tuple(c)) for c in cells]
         self.cell_of_orb = [int(c) for c in cell_of_orb]
         self.prec = prec
         arr = (_Grid * len(self.cells))(*[c.c() for c in self.cells])
         co = (ctypes.c_int * max(1, len(self.cell_of_orb)))(*self.cell_of_orb)
         flags = (WVL_PLAN_GRAPH if graph else 0) | (WVL_PLAN_AUTOTUNE if autotune else 0)
+        if chain not in (None, "fused", "passes"):
+            raise ValueError("chain must be None, 'fused' or 'passes'")
+        flags |= {None: 0, "fused": WVL_PLAN_FUSED, "passes": WVL_PLAN_PASSES}[chain]
         h = _vp()
         _check(lib().wvl_plan_create(arr, len(self.cells), co, len(self.cell_of_orb), prec,
                                      flags, ctypes.byref(h)))

@@ -141,6 +141,7 @@ struct SegDesc {
     double* user_rho = nullptr;
     double* rho_part = nullptr;
     int groups = 1;          // M_POT: groups actually launched
+    bool rho_shared = false; // M_POT: write partials even with one group
 };
 
 template <typename T>
@@ -295,7 +296,7 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
                 if (d.user_rho == nullptr) {
                     s.rho = nullptr;
                     s.rho_gstride = 0;
-                } else if (G == 1) {
+                } else if (G == 1 && !d.rho_shared) {
                     s.rho = d.user_rho;
                     s.rho_gstride = 0;
                 } else {
@@ -355,7 +356,31 @@ struct CellRun {
     int bx[3] = {0, 0, 0};         // free/surface BC: box extents inside the padded cell
     int bo[3] = {0, 0, 0};         // free/surface BC: padding per side along each axis
     bool emu = false;              // FP64 convolutions on the tensor cores (emu.cuh)
+    int chain = 0;                 // OP_HPSI: CHAIN_AUTO, CHAIN_PASSES or CHAIN_FUSED
+    bool rho_shared = false;       // another run of the same call adds into the same rho:
+                                   //   the density goes through the run's partials
 };
+
+// Runs that add into one density array must not do so from one launch (their
+// read-modify-writes would race): such runs write partials, which the
+// reductions (one launch per run, in order) add into rho.
+template <typename T>
+static void mark_shared_rho(std::vector<CellRun<T>>& runs) {
+    for (auto& r : runs) {
+        r.rho_shared = false;
+        if (!r.rho) continue;
+        int uses = 0;
+        for (const auto& q : runs) uses += (q.rho == r.rho);
+        r.rho_shared = uses > 1;
+    }
+}
+
+// Which kernels run the local Hamiltonian: the fifteen transposing 1D passes,
+// or the six plane/column kernels of fused_kernel.cu (where every cell fits
+// them).  CHAIN_AUTO takes the fused chain for FP32 and the passes for FP64
+// (bound by the FP64 pipe, where the fused chain saves no arithmetic); a
+// plan's autotuner may replace that choice by a measured one.
+enum Chain { CHAIN_AUTO = 0, CHAIN_PASSES = 1, CHAIN_FUSED = 2 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -445,6 +470,7 @@ static std::vector<PassCall<T>> build_calls(int op, std::vector<CellRun<T>>& run
             d.s.part = r.epart;
             d.user_rho = r.rho;
             d.rho_part = r.rpart;
+            d.rho_shared = r.rho_shared;
             return d;
         });
     };
@@ -602,7 +628,7 @@ static wvl_status exec_reductions(int op, std::vector<CellRun<T>>& runs,
         cudaError_t e = cudaSuccess;
         if (pot) {
             const SegDesc<T>& d = pot->segs[i];
-            if (r.rho && d.groups > 1) {
+            if (r.rho && (d.groups > 1 || d.rho_shared)) {
                 e = launch_rho_reduce(r.rpart, r.P, d.groups, r.rho, st);
                 if (e != cudaSuccess) return cuda_fail(e, "density reduction");
             }
@@ -662,12 +688,198 @@ struct Prof {
     }
 };
 
+// ----------------------------------------------------------- fused chain
+// every fine extent a multiple of 8 in [FZ_MIN_FINE, FZ_MAX_FINE], periodic
+// full-grid cells, the planes within the shared memory of one CTA
+static constexpr size_t FZ_SMEM_MAX = 224 * 1024;
+template <typename T>
+static bool fused_cell_ok(const int Nf[3]) {
+    for (int d = 0; d < 3; ++d)
+        if (Nf[d] % 8 != 0 || Nf[d] < FZ_MIN_FINE || Nf[d] > FZ_MAX_FINE) return false;
+    for (int prog = 0; prog < FZ_NPROG; ++prog)
+        if (fz_smem<T>(prog, Nf[0], Nf[1], Nf[2]) > FZ_SMEM_MAX) return false;
+    return true;
+}
+template <typename T>
+static bool fused_ok(const std::vector<CellRun<T>>& runs) {
+    if (runs.empty()) return false;
+    for (const auto& r : runs)
+        if (r.emu || r.mapc != nullptr || r.bx[0] > 0 || !fused_cell_ok<T>(r.Nf)) return false;
+    return true;
+}
+
+struct StageClock {
+    Prof* prof;
+    cudaStream_t st;
+    int cur = -1;
+    cudaEvent_t ev0 = nullptr;
+    void begin(int stg) {
+        if (!prof || !prof->on || stg == cur) return;
+        end();
+        cur = stg;
+        ev0 = prof->get();
+        cudaEventRecord(ev0, st);
+    }
+    void end() {
+        if (!prof || !prof->on || cur < 0) return;
+        cudaEvent_t e1 = prof->get();
+        cudaEventRecord(e1, st);
+        prof->pending.emplace_back(cur, ev0, e1);
+        cur = -1;
+    }
+};
+
+// The local Hamiltonian by the six kernels of fused_kernel.cu.  Buffers of a
+// run: A = buf[0] .. D = buf[3]:  SYN3 c -> A;  SKM12 A -> s B, v C, t D;
+// POT3 D -> A;  MFTV12 A (+ C) -> D;  KA3 D (+ B) -> A;  ANA12 A -> H psi.
+// Ekin partials: [norb][N3 (SKM12) + N2 ncb (KA3)]; Epot: [norb][N2 ncb].
+// Profiling stages: synthesis = SYN3 + SKM12 (which also applies T_1, T_2 and
+// MF_1, MF_2), magic filter + potential = POT3 (MF_3, V, rho, MFT_3),
+// transposed magic filter = MFTV12, kinetic = KA3 (T_3 and A_3), analysis =
+// ANA12.
+template <typename T>
+static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStream_t st) {
+    static const int kStage[FZ_NPROG] = {ST_SYN, ST_SYN, ST_MF, ST_MFT, ST_KIN, ST_ANA};
+    StageClock clk{prof, st};
+    constexpr int LTC = fz_ltc<T>();
+    auto taps = [](int kind, double h, T (&dst)[2][32]) {
+        PassParams<T> tp;
+        std::memset(&tp, 0, sizeof tp);
+        fill_taps(tp, kind, h);
+        std::memcpy(dst, tp.f, sizeof dst);
+    };
+    std::vector<int> groups(runs.size(), 1);
+    for (int prog = 0; prog < FZ_NPROG; ++prog) {
+        clk.begin(kStage[prog]);
+        size_t i = 0;
+        while (i < runs.size()) {
+            FzParams<T> p;
+            std::memset(&p, 0, sizeof p);
+            const CellRun<T>& r0 = runs[i];
+            switch (prog) {
+            case FZ_SYN3: taps(K_SYN, 0.0, p.tap[0]); break;
+            case FZ_SKM12:
+                taps(K_SYN, 0.0, p.tap[0]);
+                taps(K_KIN, r0.hg[0], p.tap[1]);
+                taps(K_KIN, r0.hg[1], p.tap[2]);
+                taps(K_MF, 0.0, p.tap[3]);
+                break;
+            case FZ_POT3: taps(K_MF, 0.0, p.tap[0]); taps(K_MFT, 0.0, p.tap[1]); break;
+            case FZ_MFTV12: taps(K_MFT, 0.0, p.tap[0]); break;
+            case FZ_KA3: taps(K_KIN, r0.hg[2], p.tap[0]); taps(K_ANA, 0.0, p.tap[1]); break;
+            case FZ_ANA12: taps(K_ANA, 0.0, p.tap[0]); break;
+            }
+            long long jobs = 0;
+            size_t smem = 0;
+            int k = 0;
+            for (; i < runs.size() && k < MAXSEG; ++i, ++k) {
+                CellRun<T>& r = runs[i];
+                // the kinetic taps are per launch: one axis spacing per launch
+                if (k > 0 && (r.hg[0] != r0.hg[0] || r.hg[1] != r0.hg[1] || r.hg[2] != r0.hg[2]))
+                    break;
+                FzSeg<T>& s = p.seg[k];
+                s.P = r.P;
+                s.N1 = r.Nf[0];
+                s.N2 = r.Nf[1];
+                s.N3 = r.Nf[2];
+                s.n1 = r.n[0];
+                s.n2 = r.n[1];
+                s.norb = r.norb;
+                s.opg = 1;
+                s.ncb = (s.N1 + LTC - 1) / LTC;
+                const int ctiles = s.N2 * s.ncb;
+                const bool plane = prog == FZ_SKM12 || prog == FZ_MFTV12 || prog == FZ_ANA12;
+                s.RS = plane ? fz_plane_rs<T>(s.N1) : LTC;
+                long long units = r.norb;
+                T* const A = r.buf[0];
+                T* const B = r.buf[1];
+                T* const C = r.buf[2];
+                T* const D = r.buf[3];
+                switch (prog) {
+                case FZ_SYN3: s.in = r.in; s.out = A; break;
+                case FZ_SKM12:
+                    s.in = A; s.out = B; s.out2 = C; s.out3 = D;
+                    s.part = r.kpart; s.ptiles = s.N3 + ctiles; s.poff = 0;
+                    break;
+                case FZ_POT3: {
+                    s.in = D; s.out = A; s.V = r.V; s.occ = r.occ;
+                    s.part = r.epart; s.ptiles = ctiles; s.poff = 0;
+                    // orbital groups, each adding one density partial of P doubles
+                    const long long want = (sizeof(T) == 4 ? 16LL : 4LL) * num_sms();
+                    const int gmax = r.rho ? std::min(GMAX, r.norb) : r.norb;
+                    long long G = (want + ctiles - 1) / ctiles;
+                    G = std::max(1LL, std::min<long long>(G, std::max(gmax, 1)));
+                    s.opg = (int)((r.norb + G - 1) / G);
+                    G = (r.norb + s.opg - 1) / s.opg;
+                    groups[i] = (int)G;
+                    units = G;
+                    if (r.rho == nullptr) {
+                        s.rho = nullptr;
+                    } else if (G == 1 && !r.rho_shared) {
+                        s.rho = r.rho;
+                        s.rho_gstride = 0;
+                    } else {
+                        s.rho = r.rpart;
+                        s.rho_gstride = r.P;
+                    }
+                    break;
+                }
+                case FZ_MFTV12: s.in = A; s.in2 = C; s.out = D; break;
+                case FZ_KA3:
+                    s.in = D; s.in2 = B; s.out = A;
+                    s.part = r.kpart; s.ptiles = s.N3 + ctiles; s.poff = s.N3;
+                    break;
+                case FZ_ANA12: s.in = A; s.out = r.out; break;
+                }
+                s.blk0 = jobs;
+                jobs += units * (plane ? s.N3 : ctiles);
+                smem = std::max(smem, fz_smem<T>(prog, s.N1, s.N2, s.N3));
+            }
+            p.nseg = k;
+            p.njobs = jobs;
+            cudaError_t e = launch_fused<T>(prog, p, smem, st);
+            if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+        }
+    }
+    clk.begin(ST_RED);
+    for (size_t i = 0; i < runs.size(); ++i) {
+        CellRun<T>& r = runs[i];
+        const int ctiles = r.Nf[1] * ((r.Nf[0] + LTC - 1) / LTC);
+        cudaError_t e = cudaSuccess;
+        if (r.rho && (groups[i] > 1 || r.rho_shared)) {
+            e = launch_rho_reduce(r.rpart, r.P, groups[i], r.rho, st);
+            if (e != cudaSuccess) return cuda_fail(e, "density reduction");
+        }
+        if (r.epot) {
+            e = launch_reduce_parts(r.epart, nullptr, ctiles, r.norb, r.epot, st);
+            if (e != cudaSuccess) return cuda_fail(e, "epot reduction");
+        }
+        if (r.ekin) {
+            e = launch_reduce_parts(r.kpart, nullptr, r.Nf[2] + ctiles, r.norb, r.ekin, st);
+            if (e != cudaSuccess) return cuda_fail(e, "ekin reduction");
+        }
+    }
+    clk.end();
+    return WVL_OK;
+}
+
 using TuneTable = std::map<int, Tune>;
 static int tune_key(int kind, int mode, int pass) { return kind * 100 + mode * 10 + pass; }
 
 template <typename T>
 static wvl_status run_op(int op, std::vector<CellRun<T>>& runs, const TuneTable* tt,
                          Prof* prof, cudaStream_t st) {
+    mark_shared_rho(runs);
+    if (op == OP_HPSI && !runs.empty()) {
+        const int ch = runs.front().chain;
+        const bool ok = fused_ok(runs);
+        if (ch == CHAIN_FUSED && !ok)
+            return fail(WVL_EUNSUPPORTED, "fused chain: every fine extent must be a multiple of 8 "
+                        "in [%d, %d] on a periodic full-grid cell, in FP64 or FP32",
+                        FZ_MIN_FINE, FZ_MAX_FINE);
+        if (ok && (ch == CHAIN_FUSED || (ch == CHAIN_AUTO && sizeof(T) == 4)))
+            return run_fused<T>(runs, prof, st);
+    }
     std::vector<PassCall<T>> calls = build_calls<T>(op, runs);
     int cur_stage = -1;
     cudaEvent_t ev0 = nullptr;
@@ -989,6 +1201,7 @@ struct wvl_plan {
     size_t ws_bytes = 0;
     TuneTable tune;
     bool tuned = false;
+    int chain = CHAIN_AUTO;        // forced by the flags, or the autotuner's choice
     Prof prof;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -1360,15 +1573,34 @@ wvl_status wvl_plan_create(const wvl_grid* cells, int ncell, const int* cell_of_
     if (!cells || ncell < 1) return fail(WVL_EINVAL, "need at least one cell");
     if (norb < 0 || (norb > 0 && !cell_of_orb)) return fail(WVL_EINVAL, "bad orbital list");
     WVL_TRY(check_prec(prec));
-    if (flags & ~(WVL_PLAN_GRAPH | WVL_PLAN_AUTOTUNE)) return fail(WVL_EINVAL, "unknown plan flags");
+    if (flags & ~(WVL_PLAN_GRAPH | WVL_PLAN_AUTOTUNE | WVL_PLAN_FUSED | WVL_PLAN_PASSES))
+        return fail(WVL_EINVAL, "unknown plan flags");
+    if ((flags & WVL_PLAN_FUSED) && (flags & WVL_PLAN_PASSES))
+        return fail(WVL_EINVAL, "WVL_PLAN_FUSED and WVL_PLAN_PASSES exclude each other");
     for (int c = 0; c < ncell; ++c) WVL_TRY(check_grid(&cells[c]));
     for (int o = 0; o < norb; ++o)
         if (cell_of_orb[o] < 0 || cell_of_orb[o] >= ncell)
             return fail(WVL_EINVAL, "cell_of_orb[%d] = %d out of range", o, cell_of_orb[o]);
+    if (flags & WVL_PLAN_FUSED) {
+        if (prec == WVL_F64_EMU)
+            return fail(WVL_EUNSUPPORTED, "the fused chain has no tensor-core form");
+        for (int c = 0; c < ncell; ++c) {
+            int n[3], Nf[3];
+            double hg[3];
+            long long P;
+            grid_dims(&cells[c], n, Nf, hg, P);
+            const bool ok = prec == WVL_F32 ? fused_cell_ok<float>(Nf) : fused_cell_ok<double>(Nf);
+            if (!ok)
+                return fail(WVL_EUNSUPPORTED, "cell %d: the fused chain needs fine extents that are "
+                            "multiples of 8 in [%d, %d] (and planes that fit one CTA)", c,
+                            FZ_MIN_FINE, FZ_MAX_FINE);
+        }
+    }
     wvl_plan* p = new (std::nothrow) wvl_plan;
     if (!p) return fail(WVL_EINVAL, "host allocation failed");
     p->prec = prec;
     p->flags = flags;
+    p->chain = (flags & WVL_PLAN_FUSED) ? CHAIN_FUSED : (flags & WVL_PLAN_PASSES) ? CHAIN_PASSES : CHAIN_AUTO;
     p->cells.assign(cells, cells + ncell);
     p->cell_of_orb.assign(cell_of_orb, cell_of_orb + norb);
     p->norb = norb;
@@ -1434,6 +1666,7 @@ static wvl_status plan_runs(wvl_plan* plan, const void* psi, const void* const* 
         r.ekin = ekin + pr.o0;
         r.epot = epot + pr.o0;
         r.emu = plan->prec == WVL_F64_EMU;
+        r.chain = plan->chain;
         carve(r, static_cast<char*>(ws) + pr.ws_off);
         runs.push_back(r);
     }
@@ -1484,6 +1717,7 @@ static wvl_status plan_exec(wvl_plan* plan, const void* psi, const void* const* 
     // capture the enqueue sequence into a graph; the kernels' shared-memory
     // attributes are set before capture (host-only calls)
     cudaError_t e = (plan->prec == WVL_F64_EMU) ? prepare_emu_kernels() : prepare_pass_kernels<T>();
+    if (e == cudaSuccess && plan->prec != WVL_F64_EMU) e = prepare_fused_kernels<T>();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -1576,9 +1810,31 @@ static wvl_status plan_tune(wvl_plan* plan, const void* psi, const void* const* 
             }
         best[tune_key(c.kind, c.mode, c.pass)] = bv;
     }
+    plan->tune = best;
+    // the chain: time both where the flags leave the choice and the cells allow
+    if (!(plan->flags & (WVL_PLAN_FUSED | WVL_PLAN_PASSES)) && fused_ok(runs)) {
+        float tc[2] = {0.f, 0.f};
+        for (int ch = 0; ch < 2; ++ch) {
+            for (auto& r : runs) r.chain = ch == 0 ? CHAIN_PASSES : CHAIN_FUSED;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                wvl_status s = run_op<T>(OP_HPSI, runs, &plan->tune, nullptr, st);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                if (s != WVL_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return s;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tc[ch] += ms;
+            }
+        }
+        plan->chain = tc[1] < tc[0] ? CHAIN_FUSED : CHAIN_PASSES;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    plan->tune = best;
     plan->tuned = true;
     if (plan->gexec) {
         cudaGraphExecDestroy(plan->gexec);
@@ -1612,6 +1868,9 @@ wvl_status wvl_plan_describe(const wvl_plan* plan, char* buf, size_t len) {
     if (!plan || !buf || len == 0) return fail(WVL_EINVAL, "NULL argument");
     static const char* kn[] = {"synthesis", "analysis", "magicfilter", "magicfilter_T", "kinetic"};
     std::string s = plan->tuned ? "autotuned\n" : "defaults\n";
+    s += plan->chain == CHAIN_FUSED ? "chain: fused plane/column kernels\n"
+         : plan->chain == CHAIN_PASSES ? "chain: transposing 1D passes\n"
+         : "chain: automatic (fused plane/column kernels for FP32 where the cells allow)\n";
     for (const auto& kv : plan->tune) {
         char line[128];
         snprintf(line, sizeof line, "%s mode %d pass %d: R=%d LT=%d %s\n", kn[kv.first / 100],

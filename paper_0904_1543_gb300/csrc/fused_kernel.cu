@@ -1,0 +1,616 @@
+// The local Hamiltonian chain (Sec. "Local hamiltonian", Sec. "Three
+// dimensional operators", Eqs. 3dconv and kinetic1d) as six kernels that keep
+// fine-grid planes and column tiles on chip across several 1D filters.
+//
+// Every 3D operator of the chain (synthesis S, magic filter MF, its transpose
+// MFT, the kinetic filter T = T_1 + T_2 + T_3, analysis A) is a product, or
+// for T a sum, of 1D operators along the three axes, and 1D operators along
+// different axes commute.  The chain therefore applies axis 3 in column
+// kernels (a tile of all N3 rows x 32 FP32 / 16 FP64 columns at one I2) and
+// axes 1 and 2 in plane kernels (one I3 plane), and groups the filters so
+// that what one kernel loads passes through several of them before it is
+// written back:
+//
+//   FZ_SYN3   (column)  a  = S_3 c                 c gathered from the compressed form
+//   FZ_SKM12  (plane)   s  = S_1 S_2 a;  v = (T_1 + T_2) s;  t = MF_1 MF_2 s
+//   FZ_POT3   (column)  psi_r = MF_3 t;  y_r = V psi_r;  rho += occ psi_r^2;  x = MFT_3 y_r
+//   FZ_MFTV12 (plane)   w  = MFT_1 MFT_2 x + v
+//   FZ_KA3    (column)  z  = w + T_3 s;  b = A_3 z
+//   FZ_ANA12  (plane)   H psi = A_1 A_2 b, scattered into the compressed form
+//
+// which gives z = MFT V MF s + T s and H psi = A z (steps 1 to 7 of the
+// chain), Ekin = <s, T s> (partials from FZ_SKM12 and FZ_KA3) and
+// Epot = <psi_r, V psi_r> (FZ_POT3).  Six round trips through HBM instead of
+// the fifteen of the transposing passes: about 64 instead of 140 bytes per
+// orbital point in FP32.
+//
+// Row pass: a lane owns one row (a warp, 32 rows at the same columns, so the
+// periodic wrap is decided per warp) and FZ_RR consecutive outputs computed
+// from a register window read as 16-byte vectors.  Column pass: a thread owns
+// one 16-byte column vector and FZ_RC consecutive rows; consecutive threads
+// take consecutive vectors of a row.  Both wrap periodically; taps are kernel
+// parameters indexed at compile time, so the inner loops are loads and FMAs.
+// The plane row stride keeps an odd number of 16-byte words per row, so the
+// 8 lanes of each phase of a lane-per-row vector load hit distinct banks.
+#include <atomic>
+
+#include <cuda_runtime.h>
+
+#include "pass_kernel.cuh"
+
+namespace wvl {
+namespace {
+
+template <typename T>
+struct Vec {
+    T v[16 / sizeof(T)];
+};
+
+template <typename T>
+__device__ __forceinline__ Vec<T> ldv(const T* p) {
+    Vec<T> r;
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+    } else {
+        const double2 q = *reinterpret_cast<const double2*>(p);
+        r.v[0] = q.x; r.v[1] = q.y;
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void stv(T* p, const T (&v)[16 / sizeof(T)]) {
+    if constexpr (sizeof(T) == 4)
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+
+__device__ __forceinline__ double fz_block_sum(double v, double* red) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// acc[k] += f[k & 1][t] win[j + D] for output k of a chunk whose window
+// element j is input position (first output - HL + j)
+template <typename T, int KIND, int NOUT, int D, int NW>
+__device__ __forceinline__ void fir(const T (&win)[NW], const T (&f)[2][32], T (&acc)[NOUT]) {
+    constexpr int NT = KT<KIND>::NT;
+    constexpr int W = NOUT + NT - 1 + KT<KIND>::EXTRA;
+    #pragma unroll
+    for (int j = 0; j < W; ++j)
+        #pragma unroll
+        for (int k = 0; k < NOUT; ++k) {
+            const int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
+            if (t >= 0 && t < NT) acc[k] = fma(f[k & 1][t], win[j + D], acc[k]);
+        }
+}
+
+// Row pass over a plane in shared memory:
+//   dst(r, c) = sum_t f[c & 1][t] src(r, (c - HL + off(c & 1) + t) mod ncols)
+// (the 1D filter of Eq. 1dconvtrans along the row, periodic)
+template <typename T, int KIND>
+__device__ __forceinline__ void row_pass(const T* __restrict__ src, T* __restrict__ dst,
+                                         int nrows, int ncols, int RS, const T (&f)[2][32]) {
+    constexpr int VEC = 16 / (int)sizeof(T);
+    constexpr int RR = FZ_RR;
+    constexpr int HL = KT<KIND>::HL;
+    constexpr int HLR = (HL + VEC - 1) / VEC * VEC;   // window start, vector aligned
+    constexpr int D = HLR - HL;
+    constexpr int W = RR + KT<KIND>::NT - 1 + KT<KIND>::EXTRA;
+    constexpr int WV = (W + D + VEC - 1) / VEC;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);
+    const int nrb = (nrows + 31) >> 5, nch = ncols / RR;
+    #pragma unroll 1
+    for (int it = warp; it < nrb * nch; it += nwarps) {
+        const int ch = it / nrb, rb = it - ch * nrb;
+        const int r = rb * 32 + lane;
+        if (r >= nrows) continue;
+        const int c0 = ch * RR;
+        const T* row = src + r * RS;
+        T win[WV * VEC];
+        const int p0 = c0 - HLR;
+        if (p0 >= 0 && p0 + WV * VEC <= ncols) {
+            #pragma unroll
+            for (int q = 0; q < WV; ++q) {
+                const Vec<T> v = ldv(row + p0 + q * VEC);
+                #pragma unroll
+                for (int e = 0; e < VEC; ++e) win[q * VEC + e] = v.v[e];
+            }
+        } else {
+            int pq = p0;
+            while (pq < 0) pq += ncols;
+            #pragma unroll
+            for (int q = 0; q < WV; ++q) {
+                const Vec<T> v = ldv(row + pq);
+                #pragma unroll
+                for (int e = 0; e < VEC; ++e) win[q * VEC + e] = v.v[e];
+                pq += VEC;
+                if (pq >= ncols) pq -= ncols;
+            }
+        }
+        T acc[RR];
+        #pragma unroll
+        for (int k = 0; k < RR; ++k) acc[k] = T(0);
+        fir<T, KIND, RR, D>(win, f, acc);
+        T* o = dst + r * RS + c0;
+        #pragma unroll
+        for (int q = 0; q < RR / VEC; ++q) {
+            T u[VEC];
+            #pragma unroll
+            for (int e = 0; e < VEC; ++e) u[e] = acc[q * VEC + e];
+            stv(o + q * VEC, u);
+        }
+    }
+}
+
+// Row offsets of a periodic column: rowoff[FZ_PADR + q] = (q mod nrows) * RS
+// for q in [-FZ_PADR, nrows + FZ_PADR), which covers every filter's window.
+constexpr int FZ_PADR = 16;
+__device__ __forceinline__ void fill_rowoff(int* rowoff, int nrows, int RS) {
+    for (int q = (int)threadIdx.x - FZ_PADR; q < nrows + FZ_PADR; q += blockDim.x) {
+        int w = q < 0 ? q + nrows : (q >= nrows ? q - nrows : q);
+        rowoff[q + FZ_PADR] = w * RS;
+    }
+}
+
+// One column-pass item: rows r0 .. r0 + FZ_RC - 1 of the 16-byte column
+// vector cv,
+//   acc[k][e] = sum_t f[k & 1][t] src((r0 + k - HL + off(k & 1) + t) mod nrows, cv VEC + e)
+// the wrapped rows taken from the offset table (one path for every item)
+template <typename T, int KIND>
+__device__ __forceinline__ void col_item(const T* __restrict__ src, const int* __restrict__ rowoff,
+                                         int r0, int cv, const T (&f)[2][32],
+                                         T (&acc)[FZ_RC][16 / sizeof(T)]) {
+    constexpr int VEC = 16 / (int)sizeof(T);
+    constexpr int RC = FZ_RC;
+    constexpr int NT = KT<KIND>::NT, HL = KT<KIND>::HL;
+    constexpr int W = RC + NT - 1 + KT<KIND>::EXTRA;
+    static_assert(HL <= FZ_PADR && W - HL - RC <= FZ_PADR, "window beyond the offset table");
+    #pragma unroll
+    for (int k = 0; k < RC; ++k)
+        #pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[k][e] = T(0);
+    const T* base = src + cv * VEC;
+    const int* ro = rowoff + FZ_PADR + r0 - HL;
+    #pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const Vec<T> v = ldv(base + ro[j]);
+        #pragma unroll
+        for (int k = 0; k < RC; ++k) {
+            const int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
+            if (t >= 0 && t < NT)
+                #pragma unroll
+                for (int e = 0; e < VEC; ++e) acc[k][e] = fma(f[k & 1][t], v.v[e], acc[k][e]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ plane kernels
+template <typename T, int PROG>
+__global__ void __launch_bounds__(FZ_PTHREADS)
+fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
+    constexpr int VEC = 16 / (int)sizeof(T);
+    constexpr int RC = FZ_RC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[FZ_PTHREADS / 32];
+    __shared__ int rowoff[FZ_MAX_FINE + 2 * FZ_PADR];
+    const long long job = blockIdx.x;
+    int si = 0;
+    #pragma unroll 1
+    while (si + 1 < p.nseg && job >= p.seg[si + 1].blk0) ++si;
+    const FzSeg<T>& S = p.seg[si];
+    const long long loc = job - S.blk0;
+    const int I3 = (int)(loc % S.N3);
+    const int o = (int)(loc / S.N3);
+    const int N1 = S.N1, N2 = S.N2, RS = S.RS;
+    const long long pbase = (long long)o * S.P + (long long)I3 * N1 * N2;
+    T* const X = reinterpret_cast<T*>(smem_raw);
+    T* const Y = X + N2 * RS;
+    const int ncv = N1 / VEC;
+    const int nitems = (N2 / RC) * ncv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NWARP = FZ_PTHREADS / 32;
+
+    // the plane, row I2 -> X + I2 RS (a warp per row, lanes over its vectors)
+    {
+        const T* src = S.in + pbase;
+        #pragma unroll 1
+        for (int r = warp; r < N2; r += NWARP)
+            for (int c = lane; c < ncv; c += 32)
+                cp_async16(X + r * RS + c * VEC, src + (long long)r * N1 + c * VEC);
+        cp_commit();
+        fill_rowoff(rowoff, N2, RS);
+        cp_wait<0>();
+        __syncthreads();
+    }
+
+    if constexpr (PROG == FZ_SKM12) {
+        Acc<T> e;
+        // s = S_1 S_2 a -> global and X
+        row_pass<T, K_SYN>(X, Y, N2, N1, RS, p.tap[0]);
+        __syncthreads();
+        #pragma unroll 1
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
+            T acc[RC][VEC];
+            col_item<T, K_SYN>(Y, rowoff, r0, cv, p.tap[0], acc);
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk) {
+                stv(S.out + pbase + (long long)(r0 + kk) * N1 + cv * VEC, acc[kk]);
+                stv(X + (r0 + kk) * RS + cv * VEC, acc[kk]);
+            }
+        }
+        __syncthreads();
+        // v = T_1 s + T_2 s, Ekin part <s, v>
+        row_pass<T, K_KIN>(X, Y, N2, N1, RS, p.tap[1]);
+        __syncthreads();
+        #pragma unroll 1
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
+            T acc[RC][VEC];
+            col_item<T, K_KIN>(X, rowoff, r0, cv, p.tap[2], acc);
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk) {
+                const int off = (r0 + kk) * RS + cv * VEC;
+                const Vec<T> t1 = ldv(Y + off);
+                const Vec<T> sv = ldv(X + off);
+                T v[VEC];
+                #pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    v[q] = acc[kk][q] + t1.v[q];
+                    e.fma_add(sv.v[q], v[q]);
+                }
+                stv(S.out2 + pbase + (long long)(r0 + kk) * N1 + cv * VEC, v);
+            }
+        }
+        __syncthreads();
+        // t = MF_1 MF_2 s
+        row_pass<T, K_MF>(X, Y, N2, N1, RS, p.tap[3]);
+        __syncthreads();
+        #pragma unroll 1
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
+            T acc[RC][VEC];
+            col_item<T, K_MF>(Y, rowoff, r0, cv, p.tap[3], acc);
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk)
+                stv(S.out3 + pbase + (long long)(r0 + kk) * N1 + cv * VEC, acc[kk]);
+        }
+        const double tot = fz_block_sum(e.get(), red);
+        if (threadIdx.x == 0) S.part[(long long)o * S.ptiles + S.poff + I3] = tot;
+    } else if constexpr (PROG == FZ_MFTV12) {
+        // w = MFT_1 MFT_2 x + v
+        row_pass<T, K_MFT>(X, Y, N2, N1, RS, p.tap[0]);
+        __syncthreads();
+        // X is free: each thread fetches the v of its own outputs there,
+        // overlapped with its column passes
+        #pragma unroll 1
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk)
+                cp_async16(X + (r0 + kk) * RS + cv * VEC,
+                           S.in2 + pbase + (long long)(r0 + kk) * N1 + cv * VEC);
+        }
+        cp_commit();
+        #pragma unroll 1
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
+            T acc[RC][VEC];
+            col_item<T, K_MFT>(Y, rowoff, r0, cv, p.tap[0], acc);
+            cp_wait<0>();
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk) {
+                const Vec<T> v = ldv(X + (r0 + kk) * RS + cv * VEC);
+                T w[VEC];
+                #pragma unroll
+                for (int q = 0; q < VEC; ++q) w[q] = acc[kk][q] + v.v[q];
+                stv(S.out + pbase + (long long)(r0 + kk) * N1 + cv * VEC, w);
+            }
+        }
+    } else {
+        // H psi = A_1 A_2 b into the compressed form: (I1, I2, I3) holds
+        // c^mu at coarse point (I1/2, I2/2, I3/2), mu = a1 + 2 a2 + 4 a3
+        row_pass<T, K_ANA>(X, Y, N2, N1, RS, p.tap[0]);
+        __syncthreads();
+        T* const cc = S.out + (long long)o * S.P;
+        T* const cf = cc + S.P / 8;
+        const long long cz = (long long)(I3 >> 1) * S.n2;
+        const int a3 = 4 * (I3 & 1);
+        #pragma unroll 1
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
+            T acc[RC][VEC];
+            col_item<T, K_ANA>(Y, rowoff, r0, cv, p.tap[0], acc);
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk) {
+                const int I2 = r0 + kk;
+                const long long crow = (cz + (I2 >> 1)) * S.n1;
+                const int a23 = a3 + 2 * (I2 & 1);
+                #pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    const int I1 = cv * VEC + q;
+                    const int mu = a23 + (I1 & 1);
+                    const long long ci = crow + (I1 >> 1);
+                    if (mu == 0) cc[ci] = acc[kk][q];
+                    else cf[ci * 7 + mu - 1] = acc[kk][q];
+                }
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------- column kernels
+// A tile is N3 rows (I3) of LTC = 128 bytes of columns (I1 from c0) at one I2;
+// column-pass item it covers rows 8 (it / 8) .. + 7 of column vector it % 8
+// (vectors past a partial last tile are idle).
+template <typename T, int PROG>
+__global__ void __launch_bounds__(FZ_CTHREADS)
+fz_col_kernel(const __grid_constant__ FzParams<T> p) {
+    constexpr int VEC = 16 / (int)sizeof(T);
+    constexpr int RC = FZ_RC;
+    constexpr int LTC = fz_ltc<T>();
+    constexpr int CV = LTC / VEC;        // 8 column vectors per tile row
+    static_assert(CV == 8, "tile rows are 128 bytes");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[FZ_CTHREADS / 32];
+    __shared__ int rowoff[FZ_MAX_FINE + 2 * FZ_PADR];
+    const long long job = blockIdx.x;
+    int si = 0;
+    #pragma unroll 1
+    while (si + 1 < p.nseg && job >= p.seg[si + 1].blk0) ++si;
+    const FzSeg<T>& S = p.seg[si];
+    const long long loc = job - S.blk0;
+    const int cb = (int)(loc % S.ncb);
+    const long long rest = loc / S.ncb;
+    const int I2 = (int)(rest % S.N2);
+    const int u = (int)(rest / S.N2);   // orbital, or orbital group for FZ_POT3
+    const int N1 = S.N1, N2 = S.N2, N3 = S.N3, RS = S.RS;
+    const long long plane = (long long)N1 * N2;
+    const int c0 = cb * LTC;
+    const int ncv = min(LTC, N1 - c0) / VEC;
+    const long long col0 = (long long)I2 * N1 + c0;   // (I3 = 0, I2, c0) in an orbital
+    T* const X = reinterpret_cast<T*>(smem_raw);
+    T* const Y = X + N3 * RS;
+    const int nitems = (N3 / RC) * CV;
+    const int ptile = I2 * S.ncb + cb;
+    fill_rowoff(rowoff, N3, RS);
+
+    // tile rows (ncv vectors each) -> dst + I3 RS; thread t copies vector
+    // t % 8 of rows t / 8, t / 8 + 16, ...
+    auto load_tile = [&](T* dst, const T* src) {
+        const int c = threadIdx.x & (CV - 1);
+        if (c < ncv)
+            #pragma unroll 1
+            for (int r = threadIdx.x / CV; r < N3; r += FZ_CTHREADS / CV)
+                cp_async16(dst + r * RS + c * VEC, src + (long long)r * plane + c * VEC);
+        cp_commit();
+    };
+
+    if constexpr (PROG == FZ_SYN3) {
+        // gather: tile element (I3, I1) is c^mu at coarse point
+        // (I1/2, I2/2, I3/2), mu = a1 + 2 a2 + 4 a3 (the interleaved layout)
+        const T* cc = S.in + (long long)u * S.P;
+        const T* cf = cc + S.P / 8;
+        const int ncols = ncv * VEC;
+        const int a2 = 2 * (I2 & 1);
+        const int x = threadIdx.x & (LTC - 1);
+        const int I1 = c0 + x;
+        const long long cxy = (long long)(I2 >> 1) * S.n1 + (I1 >> 1);
+        const long long nxy = (long long)S.n2 * S.n1;
+        if (x < ncols)
+            #pragma unroll 1
+            for (int r = threadIdx.x / LTC; r < N3; r += FZ_CTHREADS / LTC) {
+                const int mu = (I1 & 1) + a2 + 4 * (r & 1);
+                const long long ci = (long long)(r >> 1) * nxy + cxy;
+                cp_async(X + r * RS + x, (mu == 0) ? cc + ci : cf + ci * 7 + mu - 1);
+            }
+        cp_commit();
+        cp_wait<0>();
+        __syncthreads();
+        T* const ob = S.out + (long long)u * S.P + col0;
+        #pragma unroll 1
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int k = it >> 3, cv = it & 7, r0 = k * RC;
+            if (cv >= ncv) continue;
+            T acc[RC][VEC];
+            col_item<T, K_SYN>(X, rowoff, r0, cv, p.tap[0], acc);
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
+        }
+    } else if constexpr (PROG == FZ_KA3) {
+        const long long ob = (long long)u * S.P + col0;
+        load_tile(X, S.in + ob);    // w
+        load_tile(Y, S.in2 + ob);   // s
+        cp_wait<0>();
+        __syncthreads();
+        Acc<T> e;
+        // z = w + T_3 s in place of w; Ekin part <s, T_3 s>
+        #pragma unroll 1
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int k = it >> 3, cv = it & 7, r0 = k * RC;
+            if (cv >= ncv) continue;
+            T acc[RC][VEC];
+            col_item<T, K_KIN>(Y, rowoff, r0, cv, p.tap[0], acc);
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk) {
+                const int off = (r0 + kk) * RS + cv * VEC;
+                const Vec<T> sv = ldv(Y + off);
+                const Vec<T> wv = ldv(X + off);
+                T z[VEC];
+                #pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    e.fma_add(sv.v[q], acc[kk][q]);
+                    z[q] = wv.v[q] + acc[kk][q];
+                }
+                stv(X + off, z);
+            }
+        }
+        __syncthreads();
+        #pragma unroll 1
+        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            const int k = it >> 3, cv = it & 7, r0 = k * RC;
+            if (cv >= ncv) continue;
+            T acc[RC][VEC];
+            col_item<T, K_ANA>(X, rowoff, r0, cv, p.tap[1], acc);
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk)
+                stv(S.out + ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
+        }
+        const double tot = fz_block_sum(e.get(), red);
+        if (threadIdx.x == 0) S.part[(long long)u * S.ptiles + S.poff + ptile] = tot;
+    } else {
+        // FZ_POT3: the orbitals of group u in order; each thread owns one
+        // item (the launcher keeps nitems <= FZ_CTHREADS), so its density
+        // sums stay in registers across the orbitals; the potential tile is
+        // staged once per job
+        T* const Z = Y + N3 * RS;
+        const int o0 = u * S.opg, o1 = min(S.norb, o0 + S.opg);
+        const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RC;
+        const bool mine = (int)threadIdx.x < nitems && cv < ncv;
+        Acc<T> racc[RC][VEC];
+        load_tile(Z, S.V + col0);
+        load_tile(X, S.in + (long long)o0 * S.P + col0);
+        #pragma unroll 1
+        for (int o = o0; o < o1; ++o) {
+            cp_wait<0>();
+            __syncthreads();
+            Acc<T> e;
+            const T occ = (T)(S.occ ? S.occ[o] : 1.0);
+            T acc[RC][VEC];
+            if (mine) {
+                col_item<T, K_MF>(X, rowoff, r0, cv, p.tap[0], acc);
+                #pragma unroll
+                for (int kk = 0; kk < RC; ++kk) {
+                    const int off = (r0 + kk) * RS + cv * VEC;
+                    const Vec<T> vv = ldv(Z + off);
+                    T y[VEC];
+                    #pragma unroll
+                    for (int q = 0; q < VEC; ++q) {
+                        const T psi = acc[kk][q];
+                        y[q] = vv.v[q] * psi;
+                        e.fma_add(y[q], psi);
+                        racc[kk][q].add(occ * psi * psi);
+                    }
+                    stv(Y + off, y);
+                }
+            }
+            __syncthreads();
+            // X is free: fetch the next orbital's tile during the MFT pass
+            if (o + 1 < o1) load_tile(X, S.in + (long long)(o + 1) * S.P + col0);
+            if (mine) {
+                col_item<T, K_MFT>(Y, rowoff, r0, cv, p.tap[1], acc);
+                T* const ob = S.out + (long long)o * S.P + col0;
+                #pragma unroll
+                for (int kk = 0; kk < RC; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
+            }
+            const double tot = fz_block_sum(e.get(), red);
+            if (threadIdx.x == 0) S.part[(long long)o * S.ptiles + S.poff + ptile] = tot;
+        }
+        if (mine && S.rho != nullptr) {
+            double* const rb = S.rho + (long long)u * S.rho_gstride;
+            #pragma unroll
+            for (int kk = 0; kk < RC; ++kk)
+                #pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    const long long g = (long long)(r0 + kk) * plane + col0 + cv * VEC + q;
+                    if (S.rho_gstride == 0) rb[g] += racc[kk][q].get();
+                    else rb[g] = racc[kk][q].get();
+                }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host
+template <int PROG>
+constexpr bool fz_is_plane() { return PROG == FZ_SKM12 || PROG == FZ_MFTV12 || PROG == FZ_ANA12; }
+
+constexpr int FZ_SMEM_OPTIN = 224 * 1024;   // under the opt-in limit with the static reduction buffer
+
+template <typename T, int PROG>
+cudaError_t fz_ensure_attr() {
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done.load() & bit)) {
+        if constexpr (fz_is_plane<PROG>())
+            err = cudaFuncSetAttribute(fz_plane_kernel<T, PROG>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, FZ_SMEM_OPTIN);
+        else
+            err = cudaFuncSetAttribute(fz_col_kernel<T, PROG>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, FZ_SMEM_OPTIN);
+        if (err != cudaSuccess) return err;
+        done.fetch_or(bit);
+    }
+    return cudaSuccess;
+}
+
+template <typename T, int PROG>
+cudaError_t fz_launch(const FzParams<T>& p, size_t smem, cudaStream_t st) {
+    cudaError_t err = fz_ensure_attr<T, PROG>();
+    if (err != cudaSuccess) return err;
+    if (p.njobs <= 0) return cudaSuccess;
+    if (p.njobs > 0x7fffffffLL || smem > (size_t)FZ_SMEM_OPTIN) return cudaErrorInvalidConfiguration;
+    if constexpr (fz_is_plane<PROG>())
+        fz_plane_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(FZ_PTHREADS), smem, st>>>(p);
+    else
+        fz_col_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(FZ_CTHREADS), smem, st>>>(p);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+size_t fz_smem(int prog, int N1, int N2, int N3) {
+    if (prog == FZ_SKM12 || prog == FZ_MFTV12 || prog == FZ_ANA12)
+        return 2 * (size_t)N2 * fz_plane_rs<T>(N1) * sizeof(T);
+    // FZ_POT3 also stages the potential tile
+    return (prog == FZ_POT3 ? 3 : 2) * (size_t)N3 * fz_ltc<T>() * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_fused(int prog, const FzParams<T>& p, size_t smem, cudaStream_t st) {
+    switch (prog) {
+    case FZ_SYN3: return fz_launch<T, FZ_SYN3>(p, smem, st);
+    case FZ_SKM12: return fz_launch<T, FZ_SKM12>(p, smem, st);
+    case FZ_POT3: return fz_launch<T, FZ_POT3>(p, smem, st);
+    case FZ_MFTV12: return fz_launch<T, FZ_MFTV12>(p, smem, st);
+    case FZ_KA3: return fz_launch<T, FZ_KA3>(p, smem, st);
+    case FZ_ANA12: return fz_launch<T, FZ_ANA12>(p, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t prepare_fused_kernels() {
+    cudaError_t e;
+    if ((e = fz_ensure_attr<T, FZ_SYN3>()) != cudaSuccess) return e;
+    if ((e = fz_ensure_attr<T, FZ_SKM12>()) != cudaSuccess) return e;
+    if ((e = fz_ensure_attr<T, FZ_POT3>()) != cudaSuccess) return e;
+    if ((e = fz_ensure_attr<T, FZ_MFTV12>()) != cudaSuccess) return e;
+    if ((e = fz_ensure_attr<T, FZ_KA3>()) != cudaSuccess) return e;
+    return fz_ensure_attr<T, FZ_ANA12>();
+}
+
+template size_t fz_smem<float>(int, int, int, int);
+template size_t fz_smem<double>(int, int, int, int);
+template cudaError_t launch_fused<float>(int, const FzParams<float>&, size_t, cudaStream_t);
+template cudaError_t launch_fused<double>(int, const FzParams<double>&, size_t, cudaStream_t);
+template cudaError_t prepare_fused_kernels<float>();
+template cudaError_t prepare_fused_kernels<double>();
+
+}  // namespace wvl

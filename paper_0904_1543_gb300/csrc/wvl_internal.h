@@ -90,6 +90,75 @@ struct PassParams {
     Seg<T> seg[MAXSEG];
 };
 
+// ------------------------------------------------ fused plane/column chain
+// The local Hamiltonian chain as six kernels (fused_kernel.cu): each xy plane
+// kernel keeps one fine-grid plane of an orbital in shared memory and applies
+// the axis-1 and axis-2 filters of one or more operators to it; each column
+// kernel keeps an N3 x 32-column (FP64: 16) tile and applies the axis-3
+// filters.  Programs, in chain order:
+enum FzProg {
+    FZ_SYN3 = 0,    // column: gather c from the compressed form, S along axis 3
+    FZ_SKM12 = 1,   // plane:  S (axes 1, 2) -> s;  v = (T1 + T2) s;  t = MF1 MF2 s
+    FZ_POT3 = 2,    // column: psi_r = MF3 t;  V psi_r, rho, Epot;  MFT3 (V psi_r)
+    FZ_MFTV12 = 3,  // plane:  w = MFT1 MFT2 (.) + v
+    FZ_KA3 = 4,     // column: z = w + T3 s (Ekin part);  A along axis 3
+    FZ_ANA12 = 5,   // plane:  A (axes 1, 2), scatter into the compressed form
+    FZ_NPROG = 6
+};
+constexpr int FZ_PTHREADS = 256;   // plane kernels
+constexpr int FZ_CTHREADS = 128;   // column kernels
+constexpr int FZ_RR = 8;           // row-pass outputs per thread (along the row)
+constexpr int FZ_RC = 8;           // column-pass outputs per thread (along the column)
+constexpr int FZ_MIN_FINE = 32;    // fine extents the fused chain takes: multiples
+constexpr int FZ_MAX_FINE = 128;   //   of 8 in [32, 128]
+template <typename T>
+__host__ __device__ constexpr int fz_ltc() { return 128 / (int)sizeof(T); }   // tile columns
+
+template <typename T>
+struct FzSeg {
+    const T* in;          // program input (FZ_SYN3: compressed psi)
+    const T* in2;         // FZ_MFTV12: v;  FZ_KA3: s
+    T* out;               // program output (FZ_ANA12: compressed H psi; FZ_SKM12: s)
+    T* out2;              // FZ_SKM12: v
+    T* out3;              // FZ_SKM12: t
+    const T* V;           // FZ_POT3: potential
+    double* rho;          // FZ_POT3: density target (null = none)
+    long long rho_gstride;// 0 -> rho += ; else group g writes rho[g * stride]
+    const double* occ;    // FZ_POT3: occupations
+    double* part;         // energy partials [norb][ptiles]; this program writes from poff
+    long long P;          // fine points per orbital
+    long long blk0;       // first job of the segment in the launch
+    int N1, N2, N3, n1, n2;
+    int norb, opg;        // FZ_POT3: orbitals per group
+    int ncb;              // column blocks per row, ceil(N1 / fz_ltc)
+    int ptiles, poff;
+    int RS;               // shared-memory row stride in elements
+};
+
+template <typename T>
+struct FzParams {
+    T tap[4][2][32];      // the program's filters, per output parity (see fused_kernel.cu)
+    long long njobs;
+    int nseg;
+    FzSeg<T> seg[MAXSEG];
+};
+
+// shared-memory row stride of an xy plane with N1 columns: a 16-byte multiple
+// whose count of 16-byte words is odd (lane-per-row vector loads hit distinct banks)
+template <typename T>
+inline int fz_plane_rs(int N1) {
+    const int v = 16 / (int)sizeof(T);
+    int w = (N1 + v - 1) / v;
+    if ((w & 1) == 0) ++w;
+    return w * v;
+}
+template <typename T>
+size_t fz_smem(int prog, int N1, int N2, int N3);
+template <typename T>
+cudaError_t launch_fused(int prog, const FzParams<T>& p, size_t smem, cudaStream_t st);
+template <typename T>
+cudaError_t prepare_fused_kernels();
+
 // Per-kind geometry: taps, parity offsets, left/right halo.
 struct KindGeom {
     int nt, off0, off1, extra, hl, hr;

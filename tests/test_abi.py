@@ -138,3 +138,32 @@ def test_timeout_selftest_arguments():
     assert L.wvl_selftest_timeout(0.0, None) == 1
     assert L.wvl_selftest_timeout(1e9, None) == 1
     assert L.wvl_wait_timeouts(None) == 1
+
+
+def test_chain_flags_validation():
+    """The fused chain takes periodic cells whose fine extents are multiples
+    of 8 in [32, 128], in FP64 or FP32; the two chain flags exclude each
+    other.  All checked on the host by wvl_plan_create."""
+    ok = [W.Grid((16, 20, 24)), W.Grid((56, 56, 56))]
+    for prec in (W.WVL_F64, W.WVL_F32):
+        W.Plan(ok, [0, 1], prec=prec, chain="fused")
+        W.Plan(ok, [0, 1], prec=prec, chain="passes")
+        W.Plan(ok, [0, 1], prec=prec)
+    W.Plan([W.Grid((64, 64, 64))], [0], prec=W.WVL_F32, chain="fused")
+    for bad in ((12, 16, 16), (16, 18, 16), (16, 16, 68), (17, 16, 16)):
+        with pytest.raises(W.WvlError):
+            W.Plan([W.Grid(bad)], [0], prec=W.WVL_F32, chain="fused")
+        W.Plan([W.Grid(bad)], [0], prec=W.WVL_F32, chain="passes")
+    with pytest.raises(W.WvlError):
+        W.Plan(ok, [0], prec=W.WVL_F64_EMU, chain="fused")
+    # FP64 planes of 128 x 128 exceed one CTA's shared memory
+    with pytest.raises(W.WvlError):
+        W.Plan([W.Grid((64, 64, 64))], [0], prec=W.WVL_F64, chain="fused")
+    with pytest.raises(ValueError):
+        W.Plan(ok, [0], chain="other")
+    L = W.lib()
+    h = ctypes.c_void_p()
+    g = ok[0].c()
+    co = (ctypes.c_int * 1)(0)
+    assert L.wvl_plan_create(ctypes.byref(g), 1, co, 1, 0, 4 | 8, ctypes.byref(h)) == 1   # EINVAL
+    assert L.wvl_plan_create(ctypes.byref(g), 1, co, 1, 0, 16, ctypes.byref(h)) == 1      # EINVAL

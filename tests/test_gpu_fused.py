@@ -1,0 +1,259 @@
+"""GPU parity of the fused local Hamiltonian chain (the six plane/column
+kernels, WVL_PLAN_FUSED) against the FP64 oracle.
+
+The chain applies the same 1D filters as the transposing passes, grouped by
+axis: axis 3 on N3 x 128-byte column tiles, axes 1 and 2 on whole planes in
+shared memory.  FP64 results therefore agree with the oracle to a few 1e-16
+and are held to the 1e-12 bound; FP32 to the FP32 bounds (2e-5 H psi, 1e-5
+density and energies) with the oracle run in FP64 on the FP32-rounded inputs.
+
+Sizes: fine extents 32 to 128 in steps of 8 with uneven axes (N1 = 40, 48,
+80, 112 leave a partial last column tile), cells of different spacings (one
+launch per spacing), more orbitals than density groups (the potential kernel
+walks the orbitals of a group), no density target, the largest planes
+(FP32 128 x 128, FP64 112 x 112) and the bench's cells on sampled orbitals.
+"""
+import numpy as np
+import pytest
+
+import oracle.wavelet as O
+from paper_0904_1543_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+RTOL64 = 1e-12
+
+
+def close(got, ref, rtol, what=""):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert got.shape == ref.shape, (what, got.shape, ref.shape)
+    scale = np.abs(ref).max()
+    if scale == 0:
+        assert np.abs(got).max() == 0, what
+        return
+    d = np.abs(got - ref)
+    big = np.abs(ref) >= 1e-3 * scale
+    norm = d.max() / scale
+    elem = (d[big] / np.abs(ref[big])).max()
+    assert norm <= rtol, f"{what}: normwise {norm:.3e} > {rtol:.1e}"
+    assert elem <= max(rtol, 10 * rtol if rtol > 1e-9 else rtol), f"{what}: elementwise {elem:.3e}"
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_0904_1543_gb300 as W
+    return W
+
+
+def cuda(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def run_plan(W, cells, cell_of_orb, psi, Vs, occ, prec, chain, rho=True, graph=True,
+             autotune=False):
+    """One plan call on a side stream (graphs are captured off the default
+    stream); returns host copies of H psi, ekin, epot, rho per cell."""
+    import torch
+    plan = W.Plan(cells, cell_of_orb, prec=prec, graph=graph, autotune=autotune, chain=chain)
+    p = cuda(psi)
+    V = [cuda(v) for v in Vs]
+    o = cuda(occ)
+    rh = [torch.zeros(c.fine, dtype=torch.float64, device="cuda") for c in cells] if rho else None
+    hp = torch.empty_like(p)
+    ek = torch.empty(len(occ), dtype=torch.float64, device="cuda")
+    ep = torch.empty_like(ek)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        if autotune:
+            plan.autotune(p, V, o, rho=rh)
+        for _ in range(2):          # capture, then replay
+            if rho:
+                for r in rh:
+                    r.zero_()
+            plan.hpsi(p, V, o, hpsi=hp, rho=rh, ekin=ek, epot=ep)
+    torch.cuda.synchronize()
+    return (host(hp), host(ek), host(ep), [host(r) for r in rh] if rho else None, plan)
+
+
+def check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, rtol, rtol_e, orbitals=None):
+    hp, ek, ep, rho, plan = out
+    rho_ref = [np.zeros(c.fine) for c in cells]
+    for o, c in enumerate(cell_of_orb):
+        if orbitals is not None and o not in orbitals:
+            continue
+        r = O.hpsi_local(psis[o].astype(np.float64), Vs[c].astype(np.float64), occ[o],
+                         cells[c].n, cells[c].h)
+        a, b = plan.offsets[o], plan.offsets[o + 1]
+        close(hp[a:b], r["hpsi_c"], rtol, f"orbital {o}")
+        assert rel(ek[o], r["ekin"]) < rtol_e, ("ekin", o, ek[o], r["ekin"])
+        assert rel(ep[o], r["epot"]) < rtol_e, ("epot", o, ep[o], r["epot"])
+        rho_ref[c] += r["rho"]
+    if rho is not None and orbitals is None:
+        for c in range(len(cells)):
+            close(rho[c], rho_ref[c], rtol_e, f"rho cell {c}")
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_fused_f64_uneven_cells(W, graph):
+    """Three cells (one with other spacings) in one plan: 32^3, 40 x 32 x 48
+    and 48 x 40 x 32 fine, orbitals of the cells interleaved."""
+    cells = [W.Grid((16, 16, 16)), W.Grid((20, 16, 24)), W.Grid((24, 20, 16), (0.2, 0.25, 0.3))]
+    cell_of_orb = [0, 0, 1, 1, 1, 2, 0]
+    psis = [inputs.orbital(51, o, cells[c].n) for o, c in enumerate(cell_of_orb)]
+    Vs = [inputs.gaussian_potential(51, c, cells[c].n) for c in range(3)]
+    occ = np.array([2.0, 1.0, 2.0, 0.5, 2.0, 2.0, 1.5])
+    out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, W.WVL_F64, "fused",
+                   graph=graph)
+    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, RTOL64, RTOL64)
+
+
+def test_fused_f64_orbital_groups_and_no_density(W):
+    """40 orbitals on a 32^3 cell: fewer density groups than orbitals, so the
+    potential kernel walks several orbitals per group; then the same without
+    a density target."""
+    n = (16, 16, 16)
+    cells = [W.Grid(n)]
+    norb = 40
+    psis = [inputs.orbital(52, o, n) for o in range(norb)]
+    Vs = [inputs.gaussian_potential(52, 0, n)]
+    occ = np.linspace(0.5, 2.0, norb)
+    psi = np.concatenate(psis)
+    out = run_plan(W, cells, [0] * norb, psi, Vs, occ, W.WVL_F64, "fused")
+    check_against_oracle(cells, [0] * norb, psis, Vs, occ, out, RTOL64, RTOL64)
+    hp2, ek2, ep2, _, _ = run_plan(W, cells, [0] * norb, psi, Vs, occ, W.WVL_F64, "fused", rho=False)
+    assert np.array_equal(hp2, out[0])
+    assert np.array_equal(ek2, out[1]) and np.array_equal(ep2, out[2])
+
+
+def test_fused_matches_passes_f64(W):
+    """The two chains on the same orbitals (56 x 64 x 72 fine) agree within
+    the FP64 bound (normwise they differ by a few 1e-16; elementwise, on
+    entries near 1e-3 of the maximum, by up to a few 1e-13)."""
+    n = (28, 32, 36)
+    cells = [W.Grid(n)]
+    psis = [inputs.orbital(53, o, n) for o in range(3)]
+    Vs = [inputs.gaussian_potential(53, 0, n)]
+    occ = np.array([2.0, 2.0, 1.0])
+    psi = np.concatenate(psis)
+    a = run_plan(W, cells, [0] * 3, psi, Vs, occ, W.WVL_F64, "fused")
+    b = run_plan(W, cells, [0] * 3, psi, Vs, occ, W.WVL_F64, "passes")
+    close(a[0], b[0], RTOL64, "fused vs passes H psi")
+    close(a[3][0], b[3][0], RTOL64, "fused vs passes rho")
+    assert np.max(np.abs(a[1] - b[1]) / np.abs(b[1])) < 1e-13
+    assert np.max(np.abs(a[2] - b[2]) / np.abs(b[2])) < 1e-13
+    check_against_oracle(cells, [0] * 3, psis, Vs, occ, a, RTOL64, RTOL64, orbitals={1})
+
+
+def test_fused_f32_uneven_cells(W):
+    cells = [W.Grid((16, 16, 16)), W.Grid((20, 24, 16)), W.Grid((40, 16, 20))]
+    cell_of_orb = [0, 1, 2, 1, 0, 2]
+    psis = [inputs.orbital(54, o, cells[c].n).astype(np.float32) for o, c in enumerate(cell_of_orb)]
+    Vs = [inputs.gaussian_potential(54, c, cells[c].n).astype(np.float32) for c in range(3)]
+    occ = np.array([2.0, 1.0, 2.0, 0.5, 2.0, 1.5])
+    out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, W.WVL_F32, "fused")
+    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, 2e-5, 1e-5)
+
+
+def test_fused_f32_single_cell_default(W):
+    """wvl_hpsi_local in FP32 on a cell the fused kernels take (the default
+    there) against the oracle."""
+    import torch
+    n = (16, 20, 24)
+    g = W.Grid(n)
+    psi = inputs.orbitals(55, 3, n).astype(np.float32)
+    V = inputs.gaussian_potential(55, 0, n).astype(np.float32)
+    occ = np.array([2.0, 1.0, 0.5])
+    rho = torch.zeros(g.fine, dtype=torch.float64, device="cuda")
+    hp, ek, ep = W.hpsi_local(cuda(psi), cuda(V), cuda(occ), g, rho=rho)
+    hp_r, rho_r, ek_r, ep_r = O.hpsi_batch(psi.astype(np.float64), V.astype(np.float64), occ, n)
+    close(host(hp), hp_r, 2e-5, "hpsi f32")
+    close(host(rho), rho_r, 1e-5, "rho f32")
+    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < 1e-5
+    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < 1e-5
+
+
+def test_fused_largest_planes(W):
+    """FP32 planes of 128 x 128 and FP64 planes of 112 x 112 (the largest each
+    form takes), two orbitals each, one checked against the oracle."""
+    for prec, n, dt, tol, tol_e in ((W.WVL_F32, (64, 64, 64), np.float32, 2e-5, 1e-5),
+                                    (W.WVL_F64, (56, 56, 40), np.float64, RTOL64, RTOL64)):
+        cells = [W.Grid(n)]
+        psis = [inputs.orbital(56, o, n).astype(dt) for o in range(2)]
+        Vs = [inputs.gaussian_potential(56, 0, n).astype(dt)]
+        occ = np.array([2.0, 2.0])
+        out = run_plan(W, cells, [0, 0], np.concatenate(psis), Vs, occ, prec, "fused")
+        check_against_oracle(cells, [0, 0], psis, Vs, occ, out, tol, tol_e, orbitals={1})
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_fused_bench_cells_sampled(W, prec):
+    """The bench's 192 orbitals (64 on each coarse 56^3, 48^3, 40^3 cell)
+    through a graph-captured fused plan: one orbital of each cell against
+    the oracle, and sum_I V rho = sum_o occ_o Epot_o on every cell."""
+    sizes = [(56, 56, 56), (48, 48, 48), (40, 40, 40)]
+    cells = [W.Grid(s) for s in sizes]
+    cell_of_orb = [c for c in range(3) for _ in range(64)]
+    dt = np.float64 if prec == "f64" else np.float32
+    p = W.WVL_F64 if prec == "f64" else W.WVL_F32
+    psis = [inputs.orbital(2, o, sizes[c]).astype(dt) for o, c in enumerate(cell_of_orb)]
+    Vs = [inputs.gaussian_potential(2, c, sizes[c]).astype(dt) for c in range(3)]
+    occ = np.full(192, 2.0)
+    out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, p, "fused")
+    tol, tol_e = (RTOL64, RTOL64) if prec == "f64" else (2e-5, 1e-5)
+    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, tol, tol_e,
+                         orbitals={5, 64 + 17, 128 + 63})
+    hp, ek, ep, rho, _ = out
+    for c in range(3):
+        assert rho[c].min() >= 0
+        lhs = float(np.sum(Vs[c].astype(np.float64) * rho[c]))
+        rhs = float(np.sum((occ * ep)[64 * c:64 * (c + 1)]))
+        assert rel(lhs, rhs) < (1e-11 if prec == "f64" else 1e-5), (c, lhs, rhs)
+
+
+def test_autotuned_chain_choice(W):
+    """With no chain flag the autotuner times both chains; whichever it
+    keeps, the result stays within the FP64 bound."""
+    n = (24, 24, 24)
+    cells = [W.Grid(n)]
+    psis = [inputs.orbital(57, o, n) for o in range(8)]
+    Vs = [inputs.gaussian_potential(57, 0, n)]
+    occ = np.full(8, 2.0)
+    out = run_plan(W, cells, [0] * 8, np.concatenate(psis), Vs, occ, W.WVL_F64, None,
+                   autotune=True)
+    d = out[4].describe()
+    assert "autotuned" in d and "chain:" in d
+    check_against_oracle(cells, [0] * 8, psis, Vs, occ, out, RTOL64, RTOL64, orbitals={0, 7})
+
+
+@pytest.mark.parametrize("chain", ["fused", "passes"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_density_of_interleaved_runs(W, chain, prec):
+    """Orbitals of two cells interleaved one by one: every run holds one
+    orbital, and two runs add into each cell's density.  Their sums must not
+    race (they go through per-run partials and ordered reductions)."""
+    cells = [W.Grid((16, 16, 16)), W.Grid((20, 24, 16))]
+    cell_of_orb = [0, 1, 0, 1, 1, 0]
+    dt = np.float64 if prec == "f64" else np.float32
+    p = W.WVL_F64 if prec == "f64" else W.WVL_F32
+    psis = [inputs.orbital(58, o, cells[c].n).astype(dt) for o, c in enumerate(cell_of_orb)]
+    Vs = [inputs.gaussian_potential(58, c, cells[c].n).astype(dt) for c in range(2)]
+    occ = np.array([2.0, 1.0, 0.5, 2.0, 1.5, 1.0])
+    tol = RTOL64 if prec == "f64" else 1e-5
+    for rep in range(2):
+        out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, p, chain,
+                       graph=rep == 1)
+        check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out,
+                             tol if prec == "f64" else 2e-5, tol)
