@@ -33,6 +33,8 @@
 // The plane row stride keeps an odd number of 16-byte words per row, so the
 // 8 lanes of each phase of a lane-per-row vector load hit distinct banks.
 #include <atomic>
+#include <type_traits>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -67,6 +69,17 @@ __device__ __forceinline__ void stv(T* p, const T (&v)[16 / sizeof(T)]) {
         *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
 }
 
+// compile-time loop: f(integral_constant<int, 0>) ... f(integral_constant<int, N - 1>),
+// so tap indices are constants by construction (no run-time index or test)
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
 __device__ __forceinline__ double fz_block_sum(double v, double* red) {
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -86,23 +99,23 @@ template <typename T, int KIND, int NOUT, int D, int NW>
 __device__ __forceinline__ void fir(const T (&win)[NW], const T (&f)[2][32], T (&acc)[NOUT]) {
     constexpr int NT = KT<KIND>::NT;
     constexpr int W = NOUT + NT - 1 + KT<KIND>::EXTRA;
-    #pragma unroll
-    for (int j = 0; j < W; ++j)
-        #pragma unroll
-        for (int k = 0; k < NOUT; ++k) {
-            const int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
-            if (t >= 0 && t < NT) acc[k] = fma(f[k & 1][t], win[j + D], acc[k]);
-        }
+    static_for<W>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        static_for<NOUT>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
+            if constexpr (t >= 0 && t < NT) acc[k] = fma(f[k & 1][t], win[j + D], acc[k]);
+        });
+    });
 }
 
 // Row pass over a plane in shared memory:
 //   dst(r, c) = sum_t f[c & 1][t] src(r, (c - HL + off(c & 1) + t) mod ncols)
 // (the 1D filter of Eq. 1dconvtrans along the row, periodic)
-template <typename T, int KIND>
-__device__ __forceinline__ void row_pass(const T* __restrict__ src, T* __restrict__ dst,
-                                         int nrows, int ncols, int RS, const T (&f)[2][32]) {
+template <typename T, int KIND, int RR>
+__device__ __forceinline__ void row_pass_r(const T* __restrict__ src, T* __restrict__ dst,
+                                           int nrows, int ncols, int RS, const T (&f)[2][32]) {
     constexpr int VEC = 16 / (int)sizeof(T);
-    constexpr int RR = FZ_RR;
     constexpr int HL = KT<KIND>::HL;
     constexpr int HLR = (HL + VEC - 1) / VEC * VEC;   // window start, vector aligned
     constexpr int D = HLR - HL;
@@ -164,6 +177,15 @@ __device__ __forceinline__ void fill_rowoff(int* rowoff, int nrows, int RS) {
     }
 }
 
+// 16 outputs per lane where the rows allow it (half the window loads and
+// loop overhead per FMA of 8), else 8
+template <typename T, int KIND>
+__device__ __forceinline__ void row_pass(const T* __restrict__ src, T* __restrict__ dst,
+                                         int nrows, int ncols, int RS, const T (&f)[2][32]) {
+    if (ncols % 16 == 0) row_pass_r<T, KIND, 16>(src, dst, nrows, ncols, RS, f);
+    else row_pass_r<T, KIND, FZ_RR>(src, dst, nrows, ncols, RS, f);
+}
+
 // One column-pass item: rows r0 .. r0 + FZ_RC - 1 of the 16-byte column
 // vector cv,
 //   acc[k][e] = sum_t f[k & 1][t] src((r0 + k - HL + off(k & 1) + t) mod nrows, cv VEC + e)
@@ -183,17 +205,18 @@ __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* _
         for (int e = 0; e < VEC; ++e) acc[k][e] = T(0);
     const T* base = src + cv * VEC;
     const int* ro = rowoff + FZ_PADR + r0 - HL;
-    #pragma unroll
-    for (int j = 0; j < W; ++j) {
+    static_for<W>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
         const Vec<T> v = ldv(base + ro[j]);
-        #pragma unroll
-        for (int k = 0; k < RC; ++k) {
-            const int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
-            if (t >= 0 && t < NT)
+        static_for<RC>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
+            if constexpr (t >= 0 && t < NT) {
                 #pragma unroll
                 for (int e = 0; e < VEC; ++e) acc[k][e] = fma(f[k & 1][t], v.v[e], acc[k][e]);
-        }
-    }
+            }
+        });
+    });
 }
 
 // ------------------------------------------------------------ plane kernels
@@ -260,6 +283,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
             const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
             T acc[RC][VEC];
             col_item<T, K_KIN>(X, rowoff, r0, cv, p.tap[2], acc);
+            T ei = T(0);   // the item's <s, v> (at most 32 products), then compensated
             #pragma unroll
             for (int kk = 0; kk < RC; ++kk) {
                 const int off = (r0 + kk) * RS + cv * VEC;
@@ -269,10 +293,11 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
                 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
                     v[q] = acc[kk][q] + t1.v[q];
-                    e.fma_add(sv.v[q], v[q]);
+                    ei = fma(sv.v[q], v[q], ei);
                 }
                 stv(S.out2 + pbase + (long long)(r0 + kk) * N1 + cv * VEC, v);
             }
+            e.add(ei);
         }
         __syncthreads();
         // t = MF_1 MF_2 s
@@ -443,6 +468,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             if (cv >= ncv) continue;
             T acc[RC][VEC];
             col_item<T, K_KIN>(Y, rowoff, r0, cv, p.tap[0], acc);
+            T ei = T(0);
             #pragma unroll
             for (int kk = 0; kk < RC; ++kk) {
                 const int off = (r0 + kk) * RS + cv * VEC;
@@ -451,11 +477,12 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                 T z[VEC];
                 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
-                    e.fma_add(sv.v[q], acc[kk][q]);
+                    ei = fma(sv.v[q], acc[kk][q], ei);
                     z[q] = wv.v[q] + acc[kk][q];
                 }
                 stv(X + off, z);
             }
+            e.add(ei);
         }
         __syncthreads();
         #pragma unroll 1
@@ -477,6 +504,10 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         // staged once per job
         T* const Z = Y + N3 * RS;
         const int o0 = u * S.opg, o1 = min(S.norb, o0 + S.opg);
+        // Epot partial of orbital o0 + j from warp w: epw[(j % FZ_EPW) * 4 + w],
+        // written out every FZ_EPW orbitals
+        constexpr int NW = FZ_CTHREADS / 32;
+        double* const epw = reinterpret_cast<double*>(Z + N3 * RS);
         const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RC;
         const bool mine = (int)threadIdx.x < nitems && cv < ncv;
         Acc<T> racc[RC][VEC];
@@ -491,6 +522,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             T acc[RC][VEC];
             if (mine) {
                 col_item<T, K_MF>(X, rowoff, r0, cv, p.tap[0], acc);
+                T ei = T(0);
                 #pragma unroll
                 for (int kk = 0; kk < RC; ++kk) {
                     const int off = (r0 + kk) * RS + cv * VEC;
@@ -500,11 +532,12 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                     for (int q = 0; q < VEC; ++q) {
                         const T psi = acc[kk][q];
                         y[q] = vv.v[q] * psi;
-                        e.fma_add(y[q], psi);
+                        ei = fma(y[q], psi, ei);
                         racc[kk][q].add(occ * psi * psi);
                     }
                     stv(Y + off, y);
                 }
+                e.add(ei);
             }
             __syncthreads();
             // X is free: fetch the next orbital's tile during the MFT pass
@@ -515,8 +548,21 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                 #pragma unroll
                 for (int kk = 0; kk < RC; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
             }
-            const double tot = fz_block_sum(e.get(), red);
-            if (threadIdx.x == 0) S.part[(long long)o * S.ptiles + S.poff + ptile] = tot;
+            double ew = e.get();
+            #pragma unroll
+            for (int sh = 16; sh > 0; sh >>= 1) ew += __shfl_down_sync(0xffffffffu, ew, sh);
+            const int j = (o - o0) % FZ_EPW;
+            if ((threadIdx.x & 31) == 0) epw[j * NW + (threadIdx.x >> 5)] = ew;
+            if (j == FZ_EPW - 1 || o + 1 == o1) {
+                // orbitals o - j .. o: warp partials in a fixed order
+                __syncthreads();
+                if ((int)threadIdx.x <= j) {
+                    double t = 0.0;
+                    #pragma unroll
+                    for (int w = 0; w < NW; ++w) t += epw[threadIdx.x * NW + w];
+                    S.part[(long long)(o - j + (int)threadIdx.x) * S.ptiles + S.poff + ptile] = t;
+                }
+            }
         }
         if (mine && S.rho != nullptr) {
             double* const rb = S.rho + (long long)u * S.rho_gstride;
@@ -578,8 +624,10 @@ template <typename T>
 size_t fz_smem(int prog, int N1, int N2, int N3) {
     if (prog == FZ_SKM12 || prog == FZ_MFTV12 || prog == FZ_ANA12)
         return 2 * (size_t)N2 * fz_plane_rs<T>(N1) * sizeof(T);
-    // FZ_POT3 also stages the potential tile
-    return (prog == FZ_POT3 ? 3 : 2) * (size_t)N3 * fz_ltc<T>() * sizeof(T);
+    // FZ_POT3 also stages the potential tile and keeps per-warp Epot partials
+    if (prog == FZ_POT3)
+        return 3 * (size_t)N3 * fz_ltc<T>() * sizeof(T) + (size_t)FZ_EPW * (FZ_CTHREADS / 32) * 8;
+    return 2 * (size_t)N3 * fz_ltc<T>() * sizeof(T);
 }
 
 template <typename T>

@@ -111,6 +111,7 @@ constexpr int FZ_RR = 8;           // row-pass outputs per thread (along the row
 constexpr int FZ_RC = 8;           // column-pass outputs per thread (along the column)
 constexpr int FZ_MIN_FINE = 32;    // fine extents the fused chain takes: multiples
 constexpr int FZ_MAX_FINE = 128;   //   of 8 in [32, 128]
+constexpr int FZ_EPW = 64;         // FZ_POT3: orbitals whose Epot partials are held at once
 template <typename T>
 __host__ __device__ constexpr int fz_ltc() { return 128 / (int)sizeof(T); }   // tile columns
 
