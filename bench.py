@@ -297,9 +297,12 @@ def measure_variants(args, W, torch, dev):
     occ = torch.full((norb,), 2.0, dtype=torch.float64, device=dev)
     psi32, V32 = psi64.float(), V64.float()
     res = {}
-    for name, p, v, prec in (("f32", psi32, V32, W.WVL_F32), ("f64", psi64, V64, W.WVL_F64),
-                             ("emu", psi64, V64, W.WVL_F64_EMU)):
-        plan = W.Plan([g], [0] * norb, prec=prec, graph=True, autotune=True)
+    chains = {}
+    for name, p, v, prec, chain in (("f32", psi32, V32, W.WVL_F32, None),
+                                    ("f32_passes", psi32, V32, W.WVL_F32, "passes"),
+                                    ("f64", psi64, V64, W.WVL_F64, None),
+                                    ("emu", psi64, V64, W.WVL_F64_EMU, None)):
+        plan = W.Plan([g], [0] * norb, prec=prec, graph=True, autotune=True, chain=chain)
         hp = torch.empty_like(p)
         ek = torch.empty(norb, dtype=torch.float64, device=dev)
         ep = torch.empty_like(ek)
@@ -311,9 +314,18 @@ def measure_variants(args, W, torch, dev):
         plan.hpsi(p, [v], occ, hpsi=hp, rho=rho, ekin=ek, epot=ep)
         torch.cuda.synchronize()
         res[name] = (ms, hp, ek, ep, rho[0])
+        chains[name] = [ln for ln in plan.describe().splitlines() if ln.startswith("chain:")][0][7:]
         del plan
     ms32, hp32, ek32, ep32, rho32 = res["f32"]
+    ms32p = res["f32_passes"][0]
     pts32 = norb * 8 * n[0] * n[1] * n[2]
+    # HBM bytes per orbital-point the chain moves: fused plane/column kernels
+    # 64 B (4 B per element: c in 8 / 16 / 8 / 12 / 12 / 8 per kernel), the 15
+    # transposing passes 140 B (4 B in and out per pass; the kinetic passes
+    # also carry K and G, 44 B); the potential, density partials and their
+    # reduction add under 1 B per orbital-point at 256 orbitals per cell
+    fused = chains["f32"].startswith("fused")
+    bpp = 64.0 if fused else 140.0
     ms64, hp64, ek64, ep64, rho64 = res["f64"]
     mse, hpe, eke, epe, rhoe = res["emu"]
     # oracle on two sampled orbitals (FP64 arithmetic on the FP32-rounded inputs)
@@ -333,13 +345,14 @@ def measure_variants(args, W, torch, dev):
         "workload": "256 orbitals, periodic coarse 48^3 (fine 96^3), FP32 convolutions, "
                     "compensated/FP64 reductions, one autotuned graph-captured plan",
         "value": norb / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
+        "chain": chains["f32"],
+        "fp32_passes_same_workload": {"value": norb / (ms32p * 1e-3), "ms_per_step": ms32p},
         "fp64_same_workload": {"value": norb / (ms64 * 1e-3), "ms_per_step": ms64},
         "speedup_over_fp64": ms64 / ms32,
-        # HBM-bound: 140 B per orbital-point moved by the 15 FP32 passes (4 B
-        # in and out per pass; the kinetic passes also carry K and G, 44 B)
-        "roofline": {"bound": "hbm", "achieved": 140.0 * pts32 / (ms32 * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": bpp * pts32 / (ms32 * 1e-3) / 1e9,
                      "peak": HBM_GBS, "unit": "GB/s",
-                     "frac": 140.0 * pts32 / (ms32 * 1e-3) / 1e9 / HBM_GBS,
+                     "frac": bpp * pts32 / (ms32 * 1e-3) / 1e9 / HBM_GBS,
+                     "bytes_per_orbital_point": bpp,
                      "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"},
         "rel_err_hpsi_vs_oracle": err_h, "rel_err_energies_vs_oracle": err_e,
         "rel_err_rho_vs_fp64_gpu": err_rho,
@@ -448,6 +461,55 @@ def measure_variants(args, W, torch, dev):
         "timeouts": W.wait_timeouts(),
     }
     del plan, psi, hp, rho, Vd
+    torch.cuda.empty_cache()
+    # ---- the FP32 form on the headline workload: the autotuner's chain and
+    # the transposing passes, the oracle (FP64 on the FP32-rounded inputs) on
+    # the first orbital of each cell
+    psi32_h = psi_h.astype(np.float32)
+    Vs32_h = [v.astype(np.float32) for v in Vs_h]
+    psi = torch.from_numpy(psi32_h).to(dev)
+    Vd = [torch.from_numpy(v).to(dev) for v in Vs32_h]
+    hp = torch.empty_like(psi)
+    rho = [torch.zeros(c.fine, dtype=torch.float64, device=dev) for c in cells]
+    f32 = {}
+    for chain in (None, "passes"):
+        plan = W.Plan(cells, cell_of_orb, prec=W.WVL_F32, graph=True, autotune=True, chain=chain)
+        plan.autotune(psi, Vd, occd, hpsi=hp, rho=rho)
+        ms_c = _time_steps(torch, lambda: plan.hpsi(psi, Vd, occd, hpsi=hp, rho=rho, ekin=ek,
+                                                    epot=ep), args.steps, 3)
+        torch.cuda.synchronize()
+        f32[chain] = (ms_c, [ln for ln in plan.describe().splitlines()
+                             if ln.startswith("chain:")][0][7:])
+        if chain is None:
+            eh, ee = 0.0, 0.0
+            for c in range(3):
+                o = c * args.per_cell
+                r = O.hpsi_local(psi32_h[offs[o]:offs[o + 1]].astype(np.float64),
+                                 Vs32_h[c].astype(np.float64), 2.0, SIZES[c])
+                got = hp[offs[o]:offs[o + 1]].double().cpu().numpy()
+                eh = max(eh, float(np.abs(got - r["hpsi_c"]).max() / np.abs(r["hpsi_c"]).max()))
+                ee = max(ee, abs(float(ek[o]) - r["ekin"]) / abs(r["ekin"]),
+                         abs(float(ep[o]) - r["epot"]) / abs(r["epot"]))
+        del plan
+    ms_a, chain_a = f32[None]
+    pts_h = WORKLOAD["fine_points_per_step"]
+    bpp = 64.0 if chain_a.startswith("fused") else 140.0
+    out["fp32_headline_workload"] = {
+        "workload": WORKLOAD["workload"].replace("batched FP64", "batched FP32 convolutions "
+                                                 "(compensated/FP64 reductions)"),
+        "value": len(cell_of_orb) / (ms_a * 1e-3), "unit": UNIT, "ms_per_step": ms_a,
+        "chain": chain_a,
+        "passes_same_workload": {"value": len(cell_of_orb) / (f32["passes"][0] * 1e-3),
+                                 "ms_per_step": f32["passes"][0]},
+        "roofline": {"bound": "hbm", "achieved": bpp * pts_h / (ms_a * 1e-3) / 1e9,
+                     "peak": HBM_GBS, "unit": "GB/s",
+                     "frac": bpp * pts_h / (ms_a * 1e-3) / 1e9 / HBM_GBS,
+                     "bytes_per_orbital_point": bpp,
+                     "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"},
+        "rel_err_hpsi_vs_oracle": eh, "rel_err_energies_vs_oracle": ee,
+        "error_sample": "the first orbital of each cell against the FP64 oracle",
+    }
+    del psi, hp, rho, Vd
     torch.cuda.empty_cache()
 
     # ---- autograd, coarse 64^3 x 512 orbitals, FP32 forward + backward

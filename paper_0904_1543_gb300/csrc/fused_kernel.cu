@@ -220,13 +220,17 @@ __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* _
 }
 
 // ------------------------------------------------------------ plane kernels
+// threads of a plane kernel: 512 for the analysis (few registers: two CTAs per SM)
+template <int PROG>
+__host__ __device__ constexpr int fz_pthreads() { return PROG == FZ_ANA12 ? 2 * FZ_PTHREADS : FZ_PTHREADS; }
+
 template <typename T, int PROG>
-__global__ void __launch_bounds__(FZ_PTHREADS)
+__global__ void __launch_bounds__(fz_pthreads<PROG>())
 fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
     constexpr int VEC = 16 / (int)sizeof(T);
     constexpr int RC = FZ_RC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[FZ_PTHREADS / 32];
+    __shared__ double red[fz_pthreads<PROG>() / 32];
     __shared__ int rowoff[FZ_MAX_FINE + 2 * FZ_PADR];
     const long long job = blockIdx.x;
     int si = 0;
@@ -243,7 +247,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
     const int ncv = N1 / VEC;
     const int nitems = (N2 / RC) * ncv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NWARP = FZ_PTHREADS / 32;
+    constexpr int NWARP = fz_pthreads<PROG>() / 32;
 
     // the plane, row I2 -> X + I2 RS (a warp per row, lanes over its vectors)
     {
@@ -611,7 +615,7 @@ cudaError_t fz_launch(const FzParams<T>& p, size_t smem, cudaStream_t st) {
     if (p.njobs <= 0) return cudaSuccess;
     if (p.njobs > 0x7fffffffLL || smem > (size_t)FZ_SMEM_OPTIN) return cudaErrorInvalidConfiguration;
     if constexpr (fz_is_plane<PROG>())
-        fz_plane_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(FZ_PTHREADS), smem, st>>>(p);
+        fz_plane_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(fz_pthreads<PROG>()), smem, st>>>(p);
     else
         fz_col_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(FZ_CTHREADS), smem, st>>>(p);
     count_launches(1);
