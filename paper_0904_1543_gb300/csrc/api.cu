@@ -729,17 +729,17 @@ struct StageClock {
     }
 };
 
-// The local Hamiltonian by the six kernels of fused_kernel.cu.  Buffers of a
-// run: A = buf[0] .. D = buf[3]:  SYN3 c -> A;  SKM12 A -> s B, v C, t D;
-// POT3 D -> A;  MFTV12 A (+ C) -> D;  KA3 D (+ B) -> A;  ANA12 A -> H psi.
-// Ekin partials: [norb][N3 (SKM12) + N2 ncb (KA3)]; Epot: [norb][N2 ncb].
+// The local Hamiltonian by the five kernels of fused_kernel.cu.  Buffers of a
+// run: A = buf[0] .. D = buf[3]:  SYN3 c -> a A;  SKM12 A -> v C, t D;
+// POT3 D -> x B;  MFTA12 B (+ C) -> w' D;  TA3 D (+ A) -> H psi.
+// Ekin partials: [norb][N3 (SKM12) + N2/2 ncb (TA3)]; Epot: [norb][N2 ncb].
 // Profiling stages: synthesis = SYN3 + SKM12 (which also applies T_1, T_2 and
 // MF_1, MF_2), magic filter + potential = POT3 (MF_3, V, rho, MFT_3),
-// transposed magic filter = MFTV12, kinetic = KA3 (T_3 and A_3), analysis =
-// ANA12.
+// transposed magic filter = MFTA12 (MFT_1, MFT_2 and the analysis A_1, A_2),
+// kinetic = TA3 (T_3, A_3, compression); the analysis stage stays empty.
 template <typename T>
 static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStream_t st) {
-    static const int kStage[FZ_NPROG] = {ST_SYN, ST_SYN, ST_MF, ST_MFT, ST_KIN, ST_ANA};
+    static const int kStage[FZ_NPROG] = {ST_SYN, ST_SYN, ST_MF, ST_MFT, ST_KIN};
     StageClock clk{prof, st};
     constexpr int LTC = fz_ltc<T>();
     auto taps = [](int kind, double h, T (&dst)[2][32]) {
@@ -765,9 +765,8 @@ static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStrea
                 taps(K_MF, 0.0, p.tap[3]);
                 break;
             case FZ_POT3: taps(K_MF, 0.0, p.tap[0]); taps(K_MFT, 0.0, p.tap[1]); break;
-            case FZ_MFTV12: taps(K_MFT, 0.0, p.tap[0]); break;
-            case FZ_KA3: taps(K_KIN, r0.hg[2], p.tap[0]); taps(K_ANA, 0.0, p.tap[1]); break;
-            case FZ_ANA12: taps(K_ANA, 0.0, p.tap[0]); break;
+            case FZ_MFTA12: taps(K_MFT, 0.0, p.tap[0]); taps(K_ANA, 0.0, p.tap[1]); break;
+            case FZ_TA3: taps(K_KIN, r0.hg[2], p.tap[0]); taps(K_ANA, 0.0, p.tap[1]); break;
             }
             long long jobs = 0;
             size_t smem = 0;
@@ -788,7 +787,8 @@ static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStrea
                 s.opg = 1;
                 s.ncb = (s.N1 + LTC - 1) / LTC;
                 const int ctiles = s.N2 * s.ncb;
-                const bool plane = prog == FZ_SKM12 || prog == FZ_MFTV12 || prog == FZ_ANA12;
+                const int ktiles = s.N3 + (s.N2 / 2) * s.ncb;   // Ekin partials per orbital
+                const bool plane = prog == FZ_SKM12 || prog == FZ_MFTA12;
                 s.RS = plane ? fz_plane_rs<T>(s.N1) : LTC;
                 long long units = r.norb;
                 T* const A = r.buf[0];
@@ -798,11 +798,11 @@ static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStrea
                 switch (prog) {
                 case FZ_SYN3: s.in = r.in; s.out = A; break;
                 case FZ_SKM12:
-                    s.in = A; s.out = B; s.out2 = C; s.out3 = D;
-                    s.part = r.kpart; s.ptiles = s.N3 + ctiles; s.poff = 0;
+                    s.in = A; s.out2 = C; s.out3 = D;
+                    s.part = r.kpart; s.ptiles = ktiles; s.poff = 0;
                     break;
                 case FZ_POT3: {
-                    s.in = D; s.out = A; s.V = r.V; s.occ = r.occ;
+                    s.in = D; s.out = B; s.V = r.V; s.occ = r.occ;
                     s.part = r.epart; s.ptiles = ctiles; s.poff = 0;
                     // orbital groups, each adding one density partial of P doubles
                     const long long want = (sizeof(T) == 4 ? 16LL : 4LL) * num_sms();
@@ -824,15 +824,14 @@ static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStrea
                     }
                     break;
                 }
-                case FZ_MFTV12: s.in = A; s.in2 = C; s.out = D; break;
-                case FZ_KA3:
-                    s.in = D; s.in2 = B; s.out = A;
-                    s.part = r.kpart; s.ptiles = s.N3 + ctiles; s.poff = s.N3;
+                case FZ_MFTA12: s.in = B; s.in2 = C; s.out = D; break;
+                case FZ_TA3:
+                    s.in = D; s.in2 = A; s.out = r.out;
+                    s.part = r.kpart; s.ptiles = ktiles; s.poff = s.N3;
                     break;
-                case FZ_ANA12: s.in = A; s.out = r.out; break;
                 }
                 s.blk0 = jobs;
-                jobs += units * (plane ? s.N3 : ctiles);
+                jobs += units * (plane ? s.N3 : prog == FZ_TA3 ? ctiles / 2 : ctiles);
                 smem = std::max(smem, fz_smem<T>(prog, s.N1, s.N2, s.N3));
             }
             p.nseg = k;
@@ -855,7 +854,7 @@ static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStrea
             if (e != cudaSuccess) return cuda_fail(e, "epot reduction");
         }
         if (r.ekin) {
-            e = launch_reduce_parts(r.kpart, nullptr, r.Nf[2] + ctiles, r.norb, r.ekin, st);
+            e = launch_reduce_parts(r.kpart, nullptr, r.Nf[2] + ctiles / 2, r.norb, r.ekin, st);
             if (e != cudaSuccess) return cuda_fail(e, "ekin reduction");
         }
     }

@@ -1,37 +1,44 @@
 // The local Hamiltonian chain (Sec. "Local hamiltonian", Sec. "Three
-// dimensional operators", Eqs. 3dconv and kinetic1d) as six kernels that keep
+// dimensional operators", Eqs. 3dconv and kinetic1d) as five kernels that keep
 // fine-grid planes and column tiles on chip across several 1D filters.
 //
 // Every 3D operator of the chain (synthesis S, magic filter MF, its transpose
 // MFT, the kinetic filter T = T_1 + T_2 + T_3, analysis A) is a product, or
 // for T a sum, of 1D operators along the three axes, and 1D operators along
 // different axes commute.  The chain therefore applies axis 3 in column
-// kernels (a tile of all N3 rows x 32 FP32 / 16 FP64 columns at one I2) and
-// axes 1 and 2 in plane kernels (one I3 plane), and groups the filters so
-// that what one kernel loads passes through several of them before it is
-// written back:
+// kernels (tiles of all N3 rows x 32 FP32 / 16 FP64 columns at one I2) and
+// axes 1 and 2 in plane kernels (one I3 plane), grouped so that what one
+// kernel loads passes through several filters before it is written back.
+// The wavelet transform is orthogonal along each axis (A_d S_d = identity,
+// Eq. refinement with the orthogonality of h and g), so with a = S_3 c and
+// s = S_1 S_2 a,
+//   A T_3 s = A_3 T_3 A_1 A_2 S_1 S_2 a = A_3 T_3 a   and   <s, T_3 s> = <a, T_3 a>,
+// and the analysis of the axis-3 kinetic term needs neither s nor A_1 A_2:
 //
 //   FZ_SYN3   (column)  a  = S_3 c                 c gathered from the compressed form
 //   FZ_SKM12  (plane)   s  = S_1 S_2 a;  v = (T_1 + T_2) s;  t = MF_1 MF_2 s
 //   FZ_POT3   (column)  psi_r = MF_3 t;  y_r = V psi_r;  rho += occ psi_r^2;  x = MFT_3 y_r
-//   FZ_MFTV12 (plane)   w  = MFT_1 MFT_2 x + v
-//   FZ_KA3    (column)  z  = w + T_3 s;  b = A_3 z
-//   FZ_ANA12  (plane)   H psi = A_1 A_2 b, scattered into the compressed form
+//   FZ_MFTA12 (plane)   w' = A_1 A_2 (MFT_1 MFT_2 x + v)
+//   FZ_TA3    (column, two I2 rows)  H psi = A_3 (w' + T_3 a), written compressed
 //
-// which gives z = MFT V MF s + T s and H psi = A z (steps 1 to 7 of the
-// chain), Ekin = <s, T s> (partials from FZ_SKM12 and FZ_KA3) and
-// Epot = <psi_r, V psi_r> (FZ_POT3).  Six round trips through HBM instead of
-// the fifteen of the transposing passes: about 64 instead of 140 bytes per
-// orbital point in FP32.
+// which gives H psi = A (MFT V MF s + T s) (steps 1 to 7 of the chain),
+// Ekin = <s, (T_1 + T_2) s> + <a, T_3 a> (partials from FZ_SKM12 and FZ_TA3)
+// and Epot = <psi_r, V psi_r> (FZ_POT3).  Five round trips through HBM
+// instead of the fifteen of the transposing passes: 52 instead of 140 bytes
+// per orbital point in FP32.  The last kernel holds both I2 parities of its
+// tile, so every coarse point's eight coefficients are on chip and the
+// compressed form (scaling block, 7-component wavelet records) is written with
+// consecutive lanes on consecutive addresses.
 //
 // Row pass: a lane owns one row (a warp, 32 rows at the same columns, so the
-// periodic wrap is decided per warp) and FZ_RR consecutive outputs computed
-// from a register window read as 16-byte vectors.  Column pass: a thread owns
-// one 16-byte column vector and FZ_RC consecutive rows; consecutive threads
-// take consecutive vectors of a row.  Both wrap periodically; taps are kernel
-// parameters indexed at compile time, so the inner loops are loads and FMAs.
-// The plane row stride keeps an odd number of 16-byte words per row, so the
-// 8 lanes of each phase of a lane-per-row vector load hit distinct banks.
+// periodic wrap is decided per warp) and 16 (or 8) consecutive outputs
+// computed from a register window read as 16-byte vectors.  Column pass: a
+// thread owns one 16-byte column vector and FZ_RC consecutive rows;
+// consecutive threads take consecutive vectors of a row; wrapped rows come
+// from a shared-memory offset table.  Taps are kernel parameters indexed at
+// compile time, so the inner loops are loads and FMAs.  The plane row stride
+// keeps an odd number of 16-byte words per row, so the 8 lanes of each phase
+// of a lane-per-row vector load hit distinct banks.
 #include <atomic>
 #include <type_traits>
 #include <utility>
@@ -220,9 +227,11 @@ __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* _
 }
 
 // ------------------------------------------------------------ plane kernels
-// threads of a plane kernel: 512 for the analysis (few registers: two CTAs per SM)
+// threads of a column kernel: FZ_TA3 holds two I2 rows per job
 template <int PROG>
-__host__ __device__ constexpr int fz_pthreads() { return PROG == FZ_ANA12 ? 2 * FZ_PTHREADS : FZ_PTHREADS; }
+__host__ __device__ constexpr int fz_cthreads() { return PROG == FZ_TA3 ? 2 * FZ_CTHREADS : FZ_CTHREADS; }
+template <int PROG>
+__host__ __device__ constexpr int fz_pthreads() { return FZ_PTHREADS; }
 
 template <typename T, int PROG>
 __global__ void __launch_bounds__(fz_pthreads<PROG>())
@@ -264,7 +273,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
 
     if constexpr (PROG == FZ_SKM12) {
         Acc<T> e;
-        // s = S_1 S_2 a -> global and X
+        // s = S_1 S_2 a -> X
         row_pass<T, K_SYN>(X, Y, N2, N1, RS, p.tap[0]);
         __syncthreads();
         #pragma unroll 1
@@ -273,10 +282,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
             T acc[RC][VEC];
             col_item<T, K_SYN>(Y, rowoff, r0, cv, p.tap[0], acc);
             #pragma unroll
-            for (int kk = 0; kk < RC; ++kk) {
-                stv(S.out + pbase + (long long)(r0 + kk) * N1 + cv * VEC, acc[kk]);
-                stv(X + (r0 + kk) * RS + cv * VEC, acc[kk]);
-            }
+            for (int kk = 0; kk < RC; ++kk) stv(X + (r0 + kk) * RS + cv * VEC, acc[kk]);
         }
         __syncthreads();
         // v = T_1 s + T_2 s, Ekin part <s, v>
@@ -318,12 +324,12 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
         }
         const double tot = fz_block_sum(e.get(), red);
         if (threadIdx.x == 0) S.part[(long long)o * S.ptiles + S.poff + I3] = tot;
-    } else if constexpr (PROG == FZ_MFTV12) {
-        // w = MFT_1 MFT_2 x + v
+    } else {
+        // FZ_MFTA12: w = MFT_1 MFT_2 x + v, then w' = A_1 A_2 w
         row_pass<T, K_MFT>(X, Y, N2, N1, RS, p.tap[0]);
         __syncthreads();
         // X is free: each thread fetches the v of its own outputs there,
-        // overlapped with its column passes
+        // overlapped with its column passes, and leaves w in its place
         #pragma unroll 1
         for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
             const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
@@ -341,59 +347,45 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
             cp_wait<0>();
             #pragma unroll
             for (int kk = 0; kk < RC; ++kk) {
-                const Vec<T> v = ldv(X + (r0 + kk) * RS + cv * VEC);
+                T* const xw = X + (r0 + kk) * RS + cv * VEC;
+                const Vec<T> v = ldv(xw);
                 T w[VEC];
                 #pragma unroll
                 for (int q = 0; q < VEC; ++q) w[q] = acc[kk][q] + v.v[q];
-                stv(S.out + pbase + (long long)(r0 + kk) * N1 + cv * VEC, w);
+                stv(xw, w);
             }
         }
-    } else {
-        // H psi = A_1 A_2 b into the compressed form: (I1, I2, I3) holds
-        // c^mu at coarse point (I1/2, I2/2, I3/2), mu = a1 + 2 a2 + 4 a3
-        row_pass<T, K_ANA>(X, Y, N2, N1, RS, p.tap[0]);
         __syncthreads();
-        T* const cc = S.out + (long long)o * S.P;
-        T* const cf = cc + S.P / 8;
-        const long long cz = (long long)(I3 >> 1) * S.n2;
-        const int a3 = 4 * (I3 & 1);
+        row_pass<T, K_ANA>(X, Y, N2, N1, RS, p.tap[1]);
+        __syncthreads();
         #pragma unroll 1
         for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
             const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
             T acc[RC][VEC];
-            col_item<T, K_ANA>(Y, rowoff, r0, cv, p.tap[0], acc);
+            col_item<T, K_ANA>(Y, rowoff, r0, cv, p.tap[1], acc);
             #pragma unroll
-            for (int kk = 0; kk < RC; ++kk) {
-                const int I2 = r0 + kk;
-                const long long crow = (cz + (I2 >> 1)) * S.n1;
-                const int a23 = a3 + 2 * (I2 & 1);
-                #pragma unroll
-                for (int q = 0; q < VEC; ++q) {
-                    const int I1 = cv * VEC + q;
-                    const int mu = a23 + (I1 & 1);
-                    const long long ci = crow + (I1 >> 1);
-                    if (mu == 0) cc[ci] = acc[kk][q];
-                    else cf[ci * 7 + mu - 1] = acc[kk][q];
-                }
-            }
+            for (int kk = 0; kk < RC; ++kk)
+                stv(S.out + pbase + (long long)(r0 + kk) * N1 + cv * VEC, acc[kk]);
         }
     }
 }
 
 // ----------------------------------------------------------- column kernels
-// A tile is N3 rows (I3) of LTC = 128 bytes of columns (I1 from c0) at one I2;
-// column-pass item it covers rows 8 (it / 8) .. + 7 of column vector it % 8
+// A tile is N3 rows (I3) of LTC = 128 bytes of columns (I1 from c0) at one I2
+// (FZ_TA3: at I2 = 2 i2 and 2 i2 + 1, one sub-tile each); column-pass item it
+// covers rows 8 (it / 8) .. + 7 of column vector it % 8 of a sub-tile
 // (vectors past a partial last tile are idle).
 template <typename T, int PROG>
-__global__ void __launch_bounds__(FZ_CTHREADS)
+__global__ void __launch_bounds__(fz_cthreads<PROG>())
 fz_col_kernel(const __grid_constant__ FzParams<T> p) {
     constexpr int VEC = 16 / (int)sizeof(T);
     constexpr int RC = FZ_RC;
     constexpr int LTC = fz_ltc<T>();
     constexpr int CV = LTC / VEC;        // 8 column vectors per tile row
+    constexpr int NT = fz_cthreads<PROG>();
     static_assert(CV == 8, "tile rows are 128 bytes");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[FZ_CTHREADS / 32];
+    __shared__ double red[NT / 32];
     __shared__ int rowoff[FZ_MAX_FINE + 2 * FZ_PADR];
     const long long job = blockIdx.x;
     int si = 0;
@@ -401,29 +393,32 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
     while (si + 1 < p.nseg && job >= p.seg[si + 1].blk0) ++si;
     const FzSeg<T>& S = p.seg[si];
     const long long loc = job - S.blk0;
+    constexpr int NSUB = PROG == FZ_TA3 ? 2 : 1;   // I2 rows per job
     const int cb = (int)(loc % S.ncb);
     const long long rest = loc / S.ncb;
-    const int I2 = (int)(rest % S.N2);
-    const int u = (int)(rest / S.N2);   // orbital, or orbital group for FZ_POT3
+    const int I2 = (int)(rest % (S.N2 / NSUB)) * NSUB;
+    const int u = (int)(rest / (S.N2 / NSUB));   // orbital, or orbital group for FZ_POT3
     const int N1 = S.N1, N2 = S.N2, N3 = S.N3, RS = S.RS;
     const long long plane = (long long)N1 * N2;
     const int c0 = cb * LTC;
     const int ncv = min(LTC, N1 - c0) / VEC;
     const long long col0 = (long long)I2 * N1 + c0;   // (I3 = 0, I2, c0) in an orbital
     T* const X = reinterpret_cast<T*>(smem_raw);
-    T* const Y = X + N3 * RS;
-    const int nitems = (N3 / RC) * CV;
-    const int ptile = I2 * S.ncb + cb;
+    T* const Y = X + NSUB * N3 * RS;
+    const int nitems = (N3 / RC) * CV;   // per sub-tile
+    const int ptile = (I2 / NSUB) * S.ncb + cb;
     fill_rowoff(rowoff, N3, RS);
 
-    // tile rows (ncv vectors each) -> dst + I3 RS; thread t copies vector
-    // t % 8 of rows t / 8, t / 8 + 16, ...
+    // tile rows (ncv vectors each) of sub-tiles 0 .. NSUB-1 -> dst + (sub N3 + I3) RS;
+    // thread t copies vector t % 8 of rows t / 8, t / 8 + NT / 8, ...
     auto load_tile = [&](T* dst, const T* src) {
         const int c = threadIdx.x & (CV - 1);
         if (c < ncv)
             #pragma unroll 1
-            for (int r = threadIdx.x / CV; r < N3; r += FZ_CTHREADS / CV)
-                cp_async16(dst + r * RS + c * VEC, src + (long long)r * plane + c * VEC);
+            for (int r = threadIdx.x / CV; r < NSUB * N3; r += NT / CV) {
+                const int sub = r >= N3, rr = r - sub * N3;
+                cp_async16(dst + r * RS + c * VEC, src + sub * N1 + (long long)rr * plane + c * VEC);
+            }
         cp_commit();
     };
 
@@ -440,7 +435,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         const long long nxy = (long long)S.n2 * S.n1;
         if (x < ncols)
             #pragma unroll 1
-            for (int r = threadIdx.x / LTC; r < N3; r += FZ_CTHREADS / LTC) {
+            for (int r = threadIdx.x / LTC; r < N3; r += NT / LTC) {
                 const int mu = (I1 & 1) + a2 + 4 * (r & 1);
                 const long long ci = (long long)(r >> 1) * nxy + cxy;
                 cp_async(X + r * RS + x, (mu == 0) ? cc + ci : cf + ci * 7 + mu - 1);
@@ -458,30 +453,32 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             #pragma unroll
             for (int kk = 0; kk < RC; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
         }
-    } else if constexpr (PROG == FZ_KA3) {
+    } else if constexpr (PROG == FZ_TA3) {
+        // H psi = A_3 (w' + T_3 a) on both I2 rows; Ekin part <a, T_3 a>
         const long long ob = (long long)u * S.P + col0;
-        load_tile(X, S.in + ob);    // w
-        load_tile(Y, S.in2 + ob);   // s
+        load_tile(X, S.in + ob);    // w'
+        load_tile(Y, S.in2 + ob);   // a
         cp_wait<0>();
         __syncthreads();
         Acc<T> e;
-        // z = w + T_3 s in place of w; Ekin part <s, T_3 s>
         #pragma unroll 1
-        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
-            const int k = it >> 3, cv = it & 7, r0 = k * RC;
+        for (int it = threadIdx.x; it < NSUB * nitems; it += blockDim.x) {
+            const int sub = it >= nitems, r = it - sub * nitems;
+            const int k = r >> 3, cv = r & 7, r0 = k * RC;
             if (cv >= ncv) continue;
+            const int so = sub * N3 * RS;
             T acc[RC][VEC];
-            col_item<T, K_KIN>(Y, rowoff, r0, cv, p.tap[0], acc);
+            col_item<T, K_KIN>(Y + so, rowoff, r0, cv, p.tap[0], acc);
             T ei = T(0);
             #pragma unroll
             for (int kk = 0; kk < RC; ++kk) {
-                const int off = (r0 + kk) * RS + cv * VEC;
-                const Vec<T> sv = ldv(Y + off);
+                const int off = so + (r0 + kk) * RS + cv * VEC;
+                const Vec<T> av = ldv(Y + off);
                 const Vec<T> wv = ldv(X + off);
                 T z[VEC];
                 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
-                    ei = fma(sv.v[q], acc[kk][q], ei);
+                    ei = fma(av.v[q], acc[kk][q], ei);
                     z[q] = wv.v[q] + acc[kk][q];
                 }
                 stv(X + off, z);
@@ -489,28 +486,55 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             e.add(ei);
         }
         __syncthreads();
+        // A_3 z -> Y (a is no longer needed)
         #pragma unroll 1
-        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
-            const int k = it >> 3, cv = it & 7, r0 = k * RC;
+        for (int it = threadIdx.x; it < NSUB * nitems; it += blockDim.x) {
+            const int sub = it >= nitems, r = it - sub * nitems;
+            const int k = r >> 3, cv = r & 7, r0 = k * RC;
             if (cv >= ncv) continue;
+            const int so = sub * N3 * RS;
             T acc[RC][VEC];
-            col_item<T, K_ANA>(X, rowoff, r0, cv, p.tap[1], acc);
+            col_item<T, K_ANA>(X + so, rowoff, r0, cv, p.tap[1], acc);
             #pragma unroll
-            for (int kk = 0; kk < RC; ++kk)
-                stv(S.out + ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
+            for (int kk = 0; kk < RC; ++kk) stv(Y + so + (r0 + kk) * RS + cv * VEC, acc[kk]);
+        }
+        __syncthreads();
+        // compressed form of the tile's coarse points (i1 from c0 / 2, i2, every
+        // i3): the scaling coefficients, then the 7-component wavelet records,
+        // each a contiguous run, written by consecutive lanes
+        {
+            T* const cc = S.out + (long long)u * S.P;
+            T* const cf = cc + S.P / 8;
+            const int nci = ncv * VEC / 2;                 // coarse points of the tile row
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            const long long kb = (long long)(I2 >> 1) * S.n1 + (c0 >> 1);
+            const long long nxy = (long long)S.n2 * S.n1;
+            #pragma unroll 1
+            for (int i3 = warp; i3 < N3 / 2; i3 += NT / 32) {
+                const long long k0 = (long long)i3 * nxy + kb;
+                const T* const y0 = Y + (2 * i3) * RS;    // a3 = 0, a2 = 0
+                if (lane < nci) cc[k0 + lane] = y0[2 * lane];
+                T* const fr = cf + 7 * k0;
+                #pragma unroll 1
+                for (int pos = lane; pos < 7 * nci; pos += 32) {
+                    const int i1 = pos / 7;
+                    const int mu = pos - 7 * i1 + 1;       // a1 + 2 a2 + 4 a3
+                    fr[pos] = y0[(mu >> 1 & 1) * N3 * RS + (mu >> 2) * RS + 2 * i1 + (mu & 1)];
+                }
+            }
         }
         const double tot = fz_block_sum(e.get(), red);
         if (threadIdx.x == 0) S.part[(long long)u * S.ptiles + S.poff + ptile] = tot;
     } else {
         // FZ_POT3: the orbitals of group u in order; each thread owns one
-        // item (the launcher keeps nitems <= FZ_CTHREADS), so its density
+        // item (the launcher keeps nitems <= NT), so its density
         // sums stay in registers across the orbitals; the potential tile is
         // staged once per job
         T* const Z = Y + N3 * RS;
         const int o0 = u * S.opg, o1 = min(S.norb, o0 + S.opg);
         // Epot partial of orbital o0 + j from warp w: epw[(j % FZ_EPW) * 4 + w],
         // written out every FZ_EPW orbitals
-        constexpr int NW = FZ_CTHREADS / 32;
+        constexpr int NW = NT / 32;
         double* const epw = reinterpret_cast<double*>(Z + N3 * RS);
         const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RC;
         const bool mine = (int)threadIdx.x < nitems && cv < ncv;
@@ -584,7 +608,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
 
 // ------------------------------------------------------------------ host
 template <int PROG>
-constexpr bool fz_is_plane() { return PROG == FZ_SKM12 || PROG == FZ_MFTV12 || PROG == FZ_ANA12; }
+constexpr bool fz_is_plane() { return PROG == FZ_SKM12 || PROG == FZ_MFTA12; }
 
 constexpr int FZ_SMEM_OPTIN = 224 * 1024;   // under the opt-in limit with the static reduction buffer
 
@@ -617,7 +641,7 @@ cudaError_t fz_launch(const FzParams<T>& p, size_t smem, cudaStream_t st) {
     if constexpr (fz_is_plane<PROG>())
         fz_plane_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(fz_pthreads<PROG>()), smem, st>>>(p);
     else
-        fz_col_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(FZ_CTHREADS), smem, st>>>(p);
+        fz_col_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(fz_cthreads<PROG>()), smem, st>>>(p);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -626,11 +650,13 @@ cudaError_t fz_launch(const FzParams<T>& p, size_t smem, cudaStream_t st) {
 
 template <typename T>
 size_t fz_smem(int prog, int N1, int N2, int N3) {
-    if (prog == FZ_SKM12 || prog == FZ_MFTV12 || prog == FZ_ANA12)
+    if (prog == FZ_SKM12 || prog == FZ_MFTA12)
         return 2 * (size_t)N2 * fz_plane_rs<T>(N1) * sizeof(T);
-    // FZ_POT3 also stages the potential tile and keeps per-warp Epot partials
+    // FZ_POT3 also stages the potential tile and keeps per-warp Epot partials;
+    // FZ_TA3 holds two sub-tiles in each of its two buffers
     if (prog == FZ_POT3)
         return 3 * (size_t)N3 * fz_ltc<T>() * sizeof(T) + (size_t)FZ_EPW * (FZ_CTHREADS / 32) * 8;
+    if (prog == FZ_TA3) return 4 * (size_t)N3 * fz_ltc<T>() * sizeof(T);
     return 2 * (size_t)N3 * fz_ltc<T>() * sizeof(T);
 }
 
@@ -640,9 +666,8 @@ cudaError_t launch_fused(int prog, const FzParams<T>& p, size_t smem, cudaStream
     case FZ_SYN3: return fz_launch<T, FZ_SYN3>(p, smem, st);
     case FZ_SKM12: return fz_launch<T, FZ_SKM12>(p, smem, st);
     case FZ_POT3: return fz_launch<T, FZ_POT3>(p, smem, st);
-    case FZ_MFTV12: return fz_launch<T, FZ_MFTV12>(p, smem, st);
-    case FZ_KA3: return fz_launch<T, FZ_KA3>(p, smem, st);
-    case FZ_ANA12: return fz_launch<T, FZ_ANA12>(p, smem, st);
+    case FZ_MFTA12: return fz_launch<T, FZ_MFTA12>(p, smem, st);
+    case FZ_TA3: return fz_launch<T, FZ_TA3>(p, smem, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -653,9 +678,8 @@ cudaError_t prepare_fused_kernels() {
     if ((e = fz_ensure_attr<T, FZ_SYN3>()) != cudaSuccess) return e;
     if ((e = fz_ensure_attr<T, FZ_SKM12>()) != cudaSuccess) return e;
     if ((e = fz_ensure_attr<T, FZ_POT3>()) != cudaSuccess) return e;
-    if ((e = fz_ensure_attr<T, FZ_MFTV12>()) != cudaSuccess) return e;
-    if ((e = fz_ensure_attr<T, FZ_KA3>()) != cudaSuccess) return e;
-    return fz_ensure_attr<T, FZ_ANA12>();
+    if ((e = fz_ensure_attr<T, FZ_MFTA12>()) != cudaSuccess) return e;
+    return fz_ensure_attr<T, FZ_TA3>();
 }
 
 template size_t fz_smem<float>(int, int, int, int);

@@ -91,19 +91,18 @@ struct PassParams {
 };
 
 // ------------------------------------------------ fused plane/column chain
-// The local Hamiltonian chain as six kernels (fused_kernel.cu): each xy plane
+// The local Hamiltonian chain as five kernels (fused_kernel.cu): each xy plane
 // kernel keeps one fine-grid plane of an orbital in shared memory and applies
 // the axis-1 and axis-2 filters of one or more operators to it; each column
-// kernel keeps an N3 x 32-column (FP64: 16) tile and applies the axis-3
-// filters.  Programs, in chain order:
+// kernel keeps N3 x 32-column (FP64: 16) tiles and applies the axis-3
+// filters.  Programs, in chain order (a = S3 c, s = S1 S2 a):
 enum FzProg {
-    FZ_SYN3 = 0,    // column: gather c from the compressed form, S along axis 3
-    FZ_SKM12 = 1,   // plane:  S (axes 1, 2) -> s;  v = (T1 + T2) s;  t = MF1 MF2 s
-    FZ_POT3 = 2,    // column: psi_r = MF3 t;  V psi_r, rho, Epot;  MFT3 (V psi_r)
-    FZ_MFTV12 = 3,  // plane:  w = MFT1 MFT2 (.) + v
-    FZ_KA3 = 4,     // column: z = w + T3 s (Ekin part);  A along axis 3
-    FZ_ANA12 = 5,   // plane:  A (axes 1, 2), scatter into the compressed form
-    FZ_NPROG = 6
+    FZ_SYN3 = 0,    // column: gather c from the compressed form, a = S3 c
+    FZ_SKM12 = 1,   // plane:  s = S1 S2 a;  v = (T1 + T2) s (Ekin part);  t = MF1 MF2 s
+    FZ_POT3 = 2,    // column: psi_r = MF3 t;  V psi_r, rho, Epot;  x = MFT3 (V psi_r)
+    FZ_MFTA12 = 3,  // plane:  w' = A1 A2 (MFT1 MFT2 x + v)
+    FZ_TA3 = 4,     // column, two I2 rows: H psi = A3 (w' + T3 a) (Ekin part), compressed
+    FZ_NPROG = 5
 };
 constexpr int FZ_PTHREADS = 256;   // plane kernels
 constexpr int FZ_CTHREADS = 128;   // column kernels
@@ -118,8 +117,8 @@ __host__ __device__ constexpr int fz_ltc() { return 128 / (int)sizeof(T); }   //
 template <typename T>
 struct FzSeg {
     const T* in;          // program input (FZ_SYN3: compressed psi)
-    const T* in2;         // FZ_MFTV12: v;  FZ_KA3: s
-    T* out;               // program output (FZ_ANA12: compressed H psi; FZ_SKM12: s)
+    const T* in2;         // FZ_MFTA12: v;  FZ_TA3: a
+    T* out;               // program output (FZ_TA3: compressed H psi)
     T* out2;              // FZ_SKM12: v
     T* out3;              // FZ_SKM12: t
     const T* V;           // FZ_POT3: potential
