@@ -197,12 +197,11 @@ __device__ __forceinline__ void row_pass(const T* __restrict__ src, T* __restric
 // vector cv,
 //   acc[k][e] = sum_t f[k & 1][t] src((r0 + k - HL + off(k & 1) + t) mod nrows, cv VEC + e)
 // the wrapped rows taken from the offset table (one path for every item)
-template <typename T, int KIND>
+template <typename T, int KIND, int RC = FZ_RC>
 __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* __restrict__ rowoff,
                                          int r0, int cv, const T (&f)[2][32],
-                                         T (&acc)[FZ_RC][16 / sizeof(T)]) {
+                                         T (&acc)[RC][16 / sizeof(T)]) {
     constexpr int VEC = 16 / (int)sizeof(T);
-    constexpr int RC = FZ_RC;
     constexpr int NT = KT<KIND>::NT, HL = KT<KIND>::HL;
     constexpr int W = RC + NT - 1 + KT<KIND>::EXTRA;
     static_assert(HL <= FZ_PADR && W - HL - RC <= FZ_PADR, "window beyond the offset table");
@@ -230,6 +229,10 @@ __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* _
 // threads of a column kernel: FZ_TA3 holds two I2 rows per job
 template <int PROG>
 __host__ __device__ constexpr int fz_cthreads() { return PROG == FZ_TA3 ? 2 * FZ_CTHREADS : FZ_CTHREADS; }
+// rows per column-pass item (4 rows and twice the threads in FZ_POT3, which
+// halves its registers, measured slower: 0.69 against 0.56 ms per step)
+template <int PROG>
+__host__ __device__ constexpr int fz_rc() { return FZ_RC; }
 template <int PROG>
 __host__ __device__ constexpr int fz_pthreads() { return FZ_PTHREADS; }
 
@@ -375,11 +378,15 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
 // (FZ_TA3: at I2 = 2 i2 and 2 i2 + 1, one sub-tile each); column-pass item it
 // covers rows 8 (it / 8) .. + 7 of column vector it % 8 of a sub-tile
 // (vectors past a partial last tile are idle).
+// CTAs per SM the register allocation must allow
+template <int PROG>
+__host__ __device__ constexpr int fz_cminb() { return PROG == FZ_SYN3 ? 4 : 3; }
+
 template <typename T, int PROG>
-__global__ void __launch_bounds__(fz_cthreads<PROG>())
+__global__ void __launch_bounds__(fz_cthreads<PROG>(), fz_cminb<PROG>())
 fz_col_kernel(const __grid_constant__ FzParams<T> p) {
     constexpr int VEC = 16 / (int)sizeof(T);
-    constexpr int RC = FZ_RC;
+    constexpr int RC = fz_rc<PROG>();
     constexpr int LTC = fz_ltc<T>();
     constexpr int CV = LTC / VEC;        // 8 column vectors per tile row
     constexpr int NT = fz_cthreads<PROG>();
@@ -509,6 +516,15 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             const long long kb = (long long)(I2 >> 1) * S.n1 + (c0 >> 1);
             const long long nxy = (long long)S.n2 * S.n1;
+            // record position pos = 7 i1 + mu - 1 (mu = a1 + 2 a2 + 4 a3) of the
+            // tile's coarse point i1 <- Y offset from its (a3 = 0, a2 = 0) row
+            int* const roff = rowoff;                      // the offset table is no longer needed
+            __syncthreads();
+            for (int pos = threadIdx.x; pos < 7 * nci; pos += NT) {
+                const int i1 = pos / 7, mu = pos - 7 * i1 + 1;
+                roff[pos] = (mu >> 1 & 1) * N3 * RS + (mu >> 2) * RS + 2 * i1 + (mu & 1);
+            }
+            __syncthreads();
             #pragma unroll 1
             for (int i3 = warp; i3 < N3 / 2; i3 += NT / 32) {
                 const long long k0 = (long long)i3 * nxy + kb;
@@ -516,11 +532,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                 if (lane < nci) cc[k0 + lane] = y0[2 * lane];
                 T* const fr = cf + 7 * k0;
                 #pragma unroll 1
-                for (int pos = lane; pos < 7 * nci; pos += 32) {
-                    const int i1 = pos / 7;
-                    const int mu = pos - 7 * i1 + 1;       // a1 + 2 a2 + 4 a3
-                    fr[pos] = y0[(mu >> 1 & 1) * N3 * RS + (mu >> 2) * RS + 2 * i1 + (mu & 1)];
-                }
+                for (int pos = lane; pos < 7 * nci; pos += 32) fr[pos] = y0[roff[pos]];
             }
         }
         const double tot = fz_block_sum(e.get(), red);
@@ -549,7 +561,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             const T occ = (T)(S.occ ? S.occ[o] : 1.0);
             T acc[RC][VEC];
             if (mine) {
-                col_item<T, K_MF>(X, rowoff, r0, cv, p.tap[0], acc);
+                col_item<T, K_MF, RC>(X, rowoff, r0, cv, p.tap[0], acc);
                 T ei = T(0);
                 #pragma unroll
                 for (int kk = 0; kk < RC; ++kk) {
@@ -571,7 +583,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             // X is free: fetch the next orbital's tile during the MFT pass
             if (o + 1 < o1) load_tile(X, S.in + (long long)(o + 1) * S.P + col0);
             if (mine) {
-                col_item<T, K_MFT>(Y, rowoff, r0, cv, p.tap[1], acc);
+                col_item<T, K_MFT, RC>(Y, rowoff, r0, cv, p.tap[1], acc);
                 T* const ob = S.out + (long long)o * S.P + col0;
                 #pragma unroll
                 for (int kk = 0; kk < RC; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
