@@ -54,6 +54,8 @@ def workload(per_cell):
 
 
 WORKLOAD = workload(PER_CELL)
+# FP32 HBM bytes per orbital point: the fused chain and the transposing passes
+FUSED_BPP, PASSES_BPP = 52.0, 140.0
 # FP64-pipe operations per fine point of one kinetic pass (an FMA counts as one)
 KIN_OPS_PER_POINT_PER_PASS = 29
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of GB300 (2 flops per DFMA)
@@ -319,13 +321,13 @@ def measure_variants(args, W, torch, dev):
     ms32, hp32, ek32, ep32, rho32 = res["f32"]
     ms32p = res["f32_passes"][0]
     pts32 = norb * 8 * n[0] * n[1] * n[2]
-    # HBM bytes per orbital-point the chain moves: fused plane/column kernels
-    # 64 B (4 B per element: c in 8 / 16 / 8 / 12 / 12 / 8 per kernel), the 15
+    # HBM bytes per orbital-point the chain moves: the five fused plane/column
+    # kernels 52 B (4 B per element: 8 / 12 / 8 / 12 / 12 per kernel), the 15
     # transposing passes 140 B (4 B in and out per pass; the kinetic passes
     # also carry K and G, 44 B); the potential, density partials and their
     # reduction add under 1 B per orbital-point at 256 orbitals per cell
     fused = chains["f32"].startswith("fused")
-    bpp = 64.0 if fused else 140.0
+    bpp = FUSED_BPP if fused else PASSES_BPP
     ms64, hp64, ek64, ep64, rho64 = res["f64"]
     mse, hpe, eke, epe, rhoe = res["emu"]
     # oracle on two sampled orbitals (FP64 arithmetic on the FP32-rounded inputs)
@@ -493,7 +495,7 @@ def measure_variants(args, W, torch, dev):
         del plan
     ms_a, chain_a = f32[None]
     pts_h = WORKLOAD["fine_points_per_step"]
-    bpp = 64.0 if chain_a.startswith("fused") else 140.0
+    bpp = FUSED_BPP if chain_a.startswith("fused") else PASSES_BPP
     out["fp32_headline_workload"] = {
         "workload": WORKLOAD["workload"].replace("batched FP64", "batched FP32 convolutions "
                                                  "(compensated/FP64 reductions)"),
