@@ -302,10 +302,12 @@ typedef struct wvl_plan wvl_plan;
 /* Which kernels apply the local Hamiltonian (at most one of the two; neither:
  * the fused kernels for WVL_F32 where every cell allows them, else the 1D
  * passes, and wvl_plan_autotune times both and keeps the faster):
- *   WVL_PLAN_FUSED  six kernels that keep a fine-grid plane (axes 1, 2) or an
- *                   N3 x 128-byte column tile (axis 3) in shared memory across
+ *   WVL_PLAN_FUSED  five kernels that keep a fine-grid plane (axes 1, 2) or
+ *                   N3 x 128-byte column tiles (axis 3) in shared memory across
  *                   several 1D filters of the chain (Sec. "Three dimensional
- *                   operators": each 3D operator is three commuting 1D ones).
+ *                   operators": each 3D operator is three commuting 1D ones;
+ *                   the wavelet transform is orthogonal along each axis).
+ *                   Results equal the passes' up to rounding.
  *                   Needs WVL_F64 or WVL_F32 and every fine extent 2 n_d a
  *                   multiple of 8 in [32, 128] (FP64: planes up to ~112 x 112);
  *                   otherwise wvl_plan_create returns WVL_EUNSUPPORTED.

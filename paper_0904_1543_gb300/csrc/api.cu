@@ -376,7 +376,7 @@ static void mark_shared_rho(std::vector<CellRun<T>>& runs) {
 }
 
 // Which kernels run the local Hamiltonian: the fifteen transposing 1D passes,
-// or the six plane/column kernels of fused_kernel.cu (where every cell fits
+// or the five plane/column kernels of fused_kernel.cu (where every cell fits
 // them).  CHAIN_AUTO takes the fused chain for FP32 and the passes for FP64
 // (bound by the FP64 pipe, where the fused chain saves no arithmetic); a
 // plan's autotuner may replace that choice by a measured one.

@@ -1,4 +1,4 @@
-"""GPU parity of the fused local Hamiltonian chain (the six plane/column
+"""GPU parity of the fused local Hamiltonian chain (the five plane/column
 kernels, WVL_PLAN_FUSED) against the FP64 oracle.
 
 The chain applies the same 1D filters as the transposing passes, grouped by
