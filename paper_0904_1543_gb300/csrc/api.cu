@@ -737,8 +737,10 @@ struct StageClock {
 // MF_1, MF_2), magic filter + potential = POT3 (MF_3, V, rho, MFT_3),
 // transposed magic filter = MFTA12 (MFT_1, MFT_2 and the analysis A_1, A_2),
 // kinetic = TA3 (T_3, A_3, compression); the analysis stage stays empty.
+// OP_ENERGY runs SYN3, SKM12 without v, POT3 without x and TA3 for <a, T_3 a>
+// alone; OP_DENSITY runs SYN3, SKM12 (t only) and POT3 (rho only).
 template <typename T>
-static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStream_t st) {
+static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, cudaStream_t st) {
     static const int kStage[FZ_NPROG] = {ST_SYN, ST_SYN, ST_MF, ST_MFT, ST_KIN};
     StageClock clk{prof, st};
     constexpr int LTC = fz_ltc<T>();
@@ -749,7 +751,10 @@ static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStrea
         std::memcpy(dst, tp.f, sizeof dst);
     };
     std::vector<int> groups(runs.size(), 1);
+    const bool hpsi = op == OP_HPSI, energy = op != OP_DENSITY;
     for (int prog = 0; prog < FZ_NPROG; ++prog) {
+        if (!hpsi && prog == FZ_MFTA12) continue;
+        if (!energy && prog == FZ_TA3) continue;
         clk.begin(kStage[prog]);
         size_t i = 0;
         while (i < runs.size()) {
@@ -798,12 +803,13 @@ static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStrea
                 switch (prog) {
                 case FZ_SYN3: s.in = r.in; s.out = A; break;
                 case FZ_SKM12:
-                    s.in = A; s.out2 = C; s.out3 = D;
-                    s.part = r.kpart; s.ptiles = ktiles; s.poff = 0;
+                    s.in = A; s.out2 = hpsi ? C : nullptr; s.out3 = D;
+                    s.part = energy ? r.kpart : nullptr; s.ptiles = ktiles; s.poff = 0;
                     break;
                 case FZ_POT3: {
-                    s.in = D; s.out = B; s.V = r.V; s.occ = r.occ;
-                    s.part = r.epart; s.ptiles = ctiles; s.poff = 0;
+                    s.in = D; s.out = hpsi ? B : nullptr; s.V = energy ? r.V : nullptr;
+                    s.occ = r.occ;
+                    s.part = energy ? r.epart : nullptr; s.ptiles = ctiles; s.poff = 0;
                     // orbital groups, each adding one density partial of P doubles
                     const long long want = (sizeof(T) == 4 ? 16LL : 4LL) * num_sms();
                     const int gmax = r.rho ? std::min(GMAX, r.norb) : r.norb;
@@ -826,7 +832,7 @@ static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStrea
                 }
                 case FZ_MFTA12: s.in = B; s.in2 = C; s.out = D; break;
                 case FZ_TA3:
-                    s.in = D; s.in2 = A; s.out = r.out;
+                    s.in = hpsi ? D : nullptr; s.in2 = A; s.out = hpsi ? r.out : nullptr;
                     s.part = r.kpart; s.ptiles = ktiles; s.poff = s.N3;
                     break;
                 }
@@ -849,11 +855,11 @@ static wvl_status run_fused(std::vector<CellRun<T>>& runs, Prof* prof, cudaStrea
             e = launch_rho_reduce(r.rpart, r.P, groups[i], r.rho, st);
             if (e != cudaSuccess) return cuda_fail(e, "density reduction");
         }
-        if (r.epot) {
+        if (r.epot && energy) {
             e = launch_reduce_parts(r.epart, nullptr, ctiles, r.norb, r.epot, st);
             if (e != cudaSuccess) return cuda_fail(e, "epot reduction");
         }
-        if (r.ekin) {
+        if (r.ekin && energy) {
             e = launch_reduce_parts(r.kpart, nullptr, r.Nf[2] + ctiles / 2, r.norb, r.ekin, st);
             if (e != cudaSuccess) return cuda_fail(e, "ekin reduction");
         }
@@ -869,7 +875,7 @@ template <typename T>
 static wvl_status run_op(int op, std::vector<CellRun<T>>& runs, const TuneTable* tt,
                          Prof* prof, cudaStream_t st) {
     mark_shared_rho(runs);
-    if (op == OP_HPSI && !runs.empty()) {
+    if ((op == OP_HPSI || op == OP_ENERGY || op == OP_DENSITY) && !runs.empty()) {
         const int ch = runs.front().chain;
         const bool ok = fused_ok(runs);
         if (ch == CHAIN_FUSED && !ok)
@@ -877,7 +883,7 @@ static wvl_status run_op(int op, std::vector<CellRun<T>>& runs, const TuneTable*
                         "in [%d, %d] on a periodic full-grid cell, in FP64 or FP32",
                         FZ_MIN_FINE, FZ_MAX_FINE);
         if (ok && (ch == CHAIN_FUSED || (ch == CHAIN_AUTO && sizeof(T) == 4)))
-            return run_fused<T>(runs, prof, st);
+            return run_fused<T>(op, runs, prof, st);
     }
     std::vector<PassCall<T>> calls = build_calls<T>(op, runs);
     int cur_stage = -1;

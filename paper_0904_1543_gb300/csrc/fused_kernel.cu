@@ -288,7 +288,9 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
             for (int kk = 0; kk < RC; ++kk) stv(X + (r0 + kk) * RS + cv * VEC, acc[kk]);
         }
         __syncthreads();
-        // v = T_1 s + T_2 s, Ekin part <s, v>
+        // v = T_1 s + T_2 s, Ekin part <s, v> (not for the density alone;
+        // v stored for H psi only)
+        if (S.part != nullptr) {
         row_pass<T, K_KIN>(X, Y, N2, N1, RS, p.tap[1]);
         __syncthreads();
         #pragma unroll 1
@@ -308,11 +310,12 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
                     v[q] = acc[kk][q] + t1.v[q];
                     ei = fma(sv.v[q], v[q], ei);
                 }
-                stv(S.out2 + pbase + (long long)(r0 + kk) * N1 + cv * VEC, v);
+                if (S.out2 != nullptr) stv(S.out2 + pbase + (long long)(r0 + kk) * N1 + cv * VEC, v);
             }
             e.add(ei);
         }
         __syncthreads();
+        }
         // t = MF_1 MF_2 s
         row_pass<T, K_MF>(X, Y, N2, N1, RS, p.tap[3]);
         __syncthreads();
@@ -325,8 +328,10 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
             for (int kk = 0; kk < RC; ++kk)
                 stv(S.out3 + pbase + (long long)(r0 + kk) * N1 + cv * VEC, acc[kk]);
         }
-        const double tot = fz_block_sum(e.get(), red);
-        if (threadIdx.x == 0) S.part[(long long)o * S.ptiles + S.poff + I3] = tot;
+        if (S.part != nullptr) {
+            const double tot = fz_block_sum(e.get(), red);
+            if (threadIdx.x == 0) S.part[(long long)o * S.ptiles + S.poff + I3] = tot;
+        }
     } else {
         // FZ_MFTA12: w = MFT_1 MFT_2 x + v, then w' = A_1 A_2 w
         row_pass<T, K_MFT>(X, Y, N2, N1, RS, p.tap[0]);
@@ -462,9 +467,11 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         }
     } else if constexpr (PROG == FZ_TA3) {
         // H psi = A_3 (w' + T_3 a) on both I2 rows; Ekin part <a, T_3 a>
+        // (the energy alone when there is no w')
+        const bool full = S.in != nullptr;
         const long long ob = (long long)u * S.P + col0;
-        load_tile(X, S.in + ob);    // w'
-        load_tile(Y, S.in2 + ob);   // a
+        if (full) load_tile(X, S.in + ob);    // w'
+        load_tile(Y, S.in2 + ob);             // a
         cp_wait<0>();
         __syncthreads();
         Acc<T> e;
@@ -481,18 +488,20 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             for (int kk = 0; kk < RC; ++kk) {
                 const int off = so + (r0 + kk) * RS + cv * VEC;
                 const Vec<T> av = ldv(Y + off);
-                const Vec<T> wv = ldv(X + off);
-                T z[VEC];
                 #pragma unroll
-                for (int q = 0; q < VEC; ++q) {
-                    ei = fma(av.v[q], acc[kk][q], ei);
-                    z[q] = wv.v[q] + acc[kk][q];
+                for (int q = 0; q < VEC; ++q) ei = fma(av.v[q], acc[kk][q], ei);
+                if (full) {
+                    const Vec<T> wv = ldv(X + off);
+                    T z[VEC];
+                    #pragma unroll
+                    for (int q = 0; q < VEC; ++q) z[q] = wv.v[q] + acc[kk][q];
+                    stv(X + off, z);
                 }
-                stv(X + off, z);
             }
             e.add(ei);
         }
         __syncthreads();
+        if (full) {
         // A_3 z -> Y (a is no longer needed)
         #pragma unroll 1
         for (int it = threadIdx.x; it < NSUB * nitems; it += blockDim.x) {
@@ -535,6 +544,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                 for (int pos = lane; pos < 7 * nci; pos += 32) fr[pos] = y0[roff[pos]];
             }
         }
+        }
         const double tot = fz_block_sum(e.get(), red);
         if (threadIdx.x == 0) S.part[(long long)u * S.ptiles + S.poff + ptile] = tot;
     } else {
@@ -551,7 +561,8 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RC;
         const bool mine = (int)threadIdx.x < nitems && cv < ncv;
         Acc<T> racc[RC][VEC];
-        load_tile(Z, S.V + col0);
+        const bool pot = S.V != nullptr, full = S.out != nullptr;
+        if (pot) load_tile(Z, S.V + col0);
         load_tile(X, S.in + (long long)o0 * S.P + col0);
         #pragma unroll 1
         for (int o = o0; o < o1; ++o) {
@@ -566,23 +577,25 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                 #pragma unroll
                 for (int kk = 0; kk < RC; ++kk) {
                     const int off = (r0 + kk) * RS + cv * VEC;
-                    const Vec<T> vv = ldv(Z + off);
-                    T y[VEC];
                     #pragma unroll
-                    for (int q = 0; q < VEC; ++q) {
-                        const T psi = acc[kk][q];
-                        y[q] = vv.v[q] * psi;
-                        ei = fma(y[q], psi, ei);
-                        racc[kk][q].add(occ * psi * psi);
+                    for (int q = 0; q < VEC; ++q) racc[kk][q].add(occ * acc[kk][q] * acc[kk][q]);
+                    if (pot) {
+                        const Vec<T> vv = ldv(Z + off);
+                        T y[VEC];
+                        #pragma unroll
+                        for (int q = 0; q < VEC; ++q) {
+                            y[q] = vv.v[q] * acc[kk][q];
+                            ei = fma(y[q], acc[kk][q], ei);
+                        }
+                        if (full) stv(Y + off, y);
                     }
-                    stv(Y + off, y);
                 }
                 e.add(ei);
             }
             __syncthreads();
             // X is free: fetch the next orbital's tile during the MFT pass
             if (o + 1 < o1) load_tile(X, S.in + (long long)(o + 1) * S.P + col0);
-            if (mine) {
+            if (mine && full) {
                 col_item<T, K_MFT, RC>(Y, rowoff, r0, cv, p.tap[1], acc);
                 T* const ob = S.out + (long long)o * S.P + col0;
                 #pragma unroll
@@ -596,7 +609,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             if (j == FZ_EPW - 1 || o + 1 == o1) {
                 // orbitals o - j .. o: warp partials in a fixed order
                 __syncthreads();
-                if ((int)threadIdx.x <= j) {
+                if ((int)threadIdx.x <= j && S.part != nullptr) {
                     double t = 0.0;
                     #pragma unroll
                     for (int w = 0; w < NW; ++w) t += epw[threadIdx.x * NW + w];

@@ -257,3 +257,24 @@ def test_density_of_interleaved_runs(W, chain, prec):
                        graph=rep == 1)
         check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out,
                              tol if prec == "f64" else 2e-5, tol)
+
+
+@pytest.mark.parametrize("n,norb", [((16, 20, 24), 3), ((24, 16, 20), 20)])
+def test_fused_energy_and_density_f32(W, n, norb):
+    """wvl_energy and wvl_density in FP32 on cells the fused kernels take
+    (their default there: synthesis, the S/T/MF plane kernel without v, the
+    potential kernel without MFT_3, and <a, T_3 a> alone for the energy)
+    against the oracle; 20 orbitals put several in each density group."""
+    import torch
+    g = W.Grid(n)
+    psi = inputs.orbitals(59, norb, n).astype(np.float32)
+    V = inputs.gaussian_potential(59, 0, n).astype(np.float32)
+    occ = np.linspace(0.5, 2.0, norb)
+    hp_r, rho_r, ek_r, ep_r = O.hpsi_batch(psi.astype(np.float64), V.astype(np.float64), occ, n)
+    rho = torch.zeros(g.fine, dtype=torch.float64, device="cuda")
+    ek, ep = W.energy(cuda(psi), cuda(V), cuda(occ), g, rho=rho)
+    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < 1e-5
+    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < 1e-5
+    close(host(rho), rho_r, 1e-5, "rho (energy)")
+    rho2 = W.density(cuda(psi), cuda(occ), g)
+    close(host(rho2), rho_r, 1e-5, "rho (density)")
