@@ -56,6 +56,9 @@ def workload(per_cell):
 WORKLOAD = workload(PER_CELL)
 # FP32 HBM bytes per orbital point: the fused chain and the transposing passes
 FUSED_BPP, PASSES_BPP = 52.0, 140.0
+# FP32 FMAs per orbital point (either chain), and the FP32 FMA rate measured
+# by an FMA-chain probe on the GB300 (MEASURED_PEAKS.json has no FP32 entry)
+FP32_FMA_PER_POINT, FP32_PEAK_TFLOPS = 279.0, 73.8
 # FP64-pipe operations per fine point of one kinetic pass (an FMA counts as one)
 KIN_OPS_PER_POINT_PER_PASS = 29
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of GB300 (2 flops per DFMA)
@@ -508,6 +511,12 @@ def measure_variants(args, W, torch, dev):
                      "frac": bpp * pts_h / (ms_a * 1e-3) / 1e9 / HBM_GBS,
                      "bytes_per_orbital_point": bpp,
                      "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"},
+        "roofline_fp32_pipe": {"bound": "alu", "achieved": 2 * FP32_FMA_PER_POINT * pts_h
+                               / (ms_a * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                               "unit": "TFLOP/s",
+                               "frac": 2 * FP32_FMA_PER_POINT * pts_h / (ms_a * 1e-3) / 1e12
+                               / FP32_PEAK_TFLOPS,
+                               "peak_source": "FP32 FMA-chain probe on this GPU model"},
         "rel_err_hpsi_vs_oracle": eh, "rel_err_energies_vs_oracle": ee,
         "error_sample": "the first orbital of each cell against the FP64 oracle",
     }
