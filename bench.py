@@ -523,6 +523,42 @@ def measure_variants(args, W, torch, dev):
     del psi, hp, rho, Vd
     torch.cuda.empty_cache()
 
+    # ---- single-pass FP64 sweep (one orbital, fine 32^3 .. 256^3): each 3D
+    # operator is three 1D passes; per pass 16 compulsory bytes per point
+    # (read + write) and 2 x taps flops per point
+    sweep = {}
+    gen = torch.Generator(device=dev)
+    for nf in (32, 64, 128, 192, 256):
+        gs = W.Grid((nf // 2,) * 3)
+        pts = nf ** 3
+        gen.manual_seed(9041543 + 1000 + nf)
+        xs = (torch.rand((1, nf, nf, nf), generator=gen, dtype=torch.float64, device=dev) * 2 - 1)
+        cs = xs.reshape(1, -1).clone()
+        res_n = {}
+        for name, taps, fn in (("magicfilter", 16, lambda: W.magicfilter(xs, gs)),
+                               ("magicfilter_T", 16, lambda: W.magicfilter_T(xs, gs)),
+                               ("kinetic", 29, lambda: W.kinetic(xs, gs)),
+                               ("synthesis", 16, lambda: W.synthesis(cs, gs)),
+                               ("analysis", 16, lambda: W.analysis(xs, gs))):
+            ms_op = _time_steps(torch, fn, 5, 3)
+            ms_pass = ms_op / 3
+            t_roof = max(16.0 * pts / (HBM_GBS * 1e9), 2.0 * taps * pts / (FP64_PEAK_TFLOPS * 1e12))
+            res_n[name] = {"ms_per_3d_operator": ms_op, "ms_per_pass": ms_pass,
+                           "gb_per_s_per_pass": 16.0 * pts / (ms_pass * 1e-3) / 1e9,
+                           "fp64_gflop_per_s": 2.0 * taps * pts / (ms_pass * 1e-3) / 1e9,
+                           "roofline_frac": t_roof * 1e3 / ms_pass}
+        sweep[f"{nf}^3"] = res_n
+        del xs, cs
+    out["pass_sweep_fp64"] = {
+        "workload": "single 3D operators (three FP64 1D passes each) on one orbital, periodic, "
+                    "fine 32^3, 64^3, 128^3, 192^3, 256^3, uniform[-1, 1] inputs from seed; "
+                    "32^3 and 64^3 fit in L2",
+        "roofline": "fraction of max(16 B per point / measured HBM bandwidth, 2 x taps flops "
+                    "per point / nominal FP64 peak) per pass; every pass is FP64-pipe bound",
+        "results": sweep,
+    }
+    torch.cuda.empty_cache()
+
     # ---- autograd, coarse 64^3 x 512 orbitals, FP32 forward + backward
     n = (64, 64, 64)
     g = W.Grid(n)

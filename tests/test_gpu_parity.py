@@ -361,3 +361,29 @@ def test_config2_full_size_sampled(W):
         lhs = float(np.sum(Vs[c] * rh))
         rhs = float(np.sum(2.0 * eph[64 * c: 64 * (c + 1)]))
         assert rel(lhs, rhs) < 1e-11
+
+
+@pytest.mark.parametrize("nc,ops", [(128, ("mf", "mft", "kin", "syn", "ana")), (96, ("mf", "kin"))])
+def test_config1_single_passes_full_size(W, nc, ops):
+    """The single-pass sweep's largest grids (fine 256^3 and 192^3, one
+    orbital, uniform[-1, 1] inputs from seed): each 3D operator element by
+    element against the oracle at the FP64 bound."""
+    n = (nc, nc, nc)
+    g = W.Grid(n)
+    x = inputs.random_field(12, nc, (1,) + g.fine)
+    if "mf" in ops:
+        close(host(W.magicfilter(cuda(x), g)[0]), O.magicfilter3d(x[0]), RTOL64, f"mf {nc}")
+    if "mft" in ops:
+        close(host(W.magicfilter_T(cuda(x), g)[0]), O.magicfilter_T3d(x[0]), RTOL64, f"mfT {nc}")
+    if "kin" in ops:
+        out, ek = W.kinetic(cuda(x), g)
+        close(host(out[0]), O.kinetic3d(x[0]), RTOL64, f"kinetic {nc}")
+    if "syn" in ops:
+        c = inputs.orbitals(12, 1, n)
+        s = W.synthesis(cuda(c), g)
+        ref = O.synthesis3d(O.uncompress(c[0], n))
+        close(host(s[0]), ref, RTOL64, f"synthesis {nc}")
+    if "ana" in ops:
+        back = W.analysis(cuda(x), g)
+        ref = O.compress(O.analysis3d(x[0]), n)
+        close(host(back[0]), ref, RTOL64, f"analysis {nc}")
