@@ -36,13 +36,6 @@
  *   max|f| max|x| over the line (the order of FP64 rounding); pointwise
  *   steps and reductions are FP64.  All entry points that take `prec`
  *   accept it; the preconditioner's CG vector updates stay FP64.
- *   WVL_F64_DF -- arrays as WVL_F64; the fused kernels (WVL_PLAN_FUSED)
- *   compute in double-FP32 on the FP32 pipe: each value an unevaluated sum
- *   of two floats (48 significant bits, ~3.6e-15 relative), products split
- *   exactly by FMA, sums by two-sum; inputs converted from FP64 on load and
- *   H psi converted back on store; density and energies reduced in FP64.
- *   Taken by wvl_hpsi_local, wvl_energy, wvl_density and plans, on cells the
- *   fused kernels take; other entry points return WVL_EUNSUPPORTED.
  * Memory: every data pointer is DEVICE memory owned by the caller and must be
  *   16-byte aligned; the library allocates nothing on these calls.  Scratch
  *   space is the caller's workspace `ws` of `ws_bytes` bytes, at least
@@ -74,7 +67,7 @@ typedef enum {
     WVL_EUNSUPPORTED = 5   /* size or option outside what is implemented  */
 } wvl_status;
 
-typedef enum { WVL_F64 = 0, WVL_F32 = 1, WVL_F64_EMU = 2, WVL_F64_DF = 3 } wvl_prec;
+typedef enum { WVL_F64 = 0, WVL_F32 = 1, WVL_F64_EMU = 2 } wvl_prec;
 
 /* Coarse grid and fine spacing h'_d = h_d / 2 (paper Eq. wavefhigh). */
 typedef struct {

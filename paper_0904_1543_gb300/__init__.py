@@ -24,10 +24,10 @@ from . import _build
 __all__ = [
     "WvlError", "Grid", "lib", "filters", "workspace_size", "synthesis", "analysis",
     "magicfilter", "magicfilter_T", "kinetic", "density", "hpsi_local", "energy",
-    "Plan", "ELoc", "device_count", "wait_timeouts", "WVL_F64", "WVL_F32", "WVL_F64_EMU", "WVL_F64_DF",
+    "Plan", "ELoc", "device_count", "wait_timeouts", "WVL_F64", "WVL_F32", "WVL_F64_EMU",
 ]
 
-WVL_F64, WVL_F32, WVL_F64_EMU, WVL_F64_DF = 0, 1, 2, 3
+WVL_F64, WVL_F32, WVL_F64_EMU = 0, 1, 2
 WVL_PLAN_GRAPH, WVL_PLAN_AUTOTUNE, WVL_PLAN_FUSED, WVL_PLAN_PASSES = 1, 2, 4, 8
 WVL_NSTAGE = 6
 STAGES = ("synthesis", "magicfilter+potential", "magicfilter_T", "kinetic", "analysis",
@@ -169,16 +169,13 @@ def filters():
     return {"h": h, "g": g, "w": w, "k0": k0.value, "a": a}
 
 
-def _prec(t, emu=False, df=False):
+def _prec(t, emu=False):
     """WVL_F64 / WVL_F32 from the dtype; emu=True selects WVL_F64_EMU (float64
-    arrays, convolution sums on the tensor cores), df=True WVL_F64_DF (float64
-    arrays, double-FP32 arithmetic in the fused kernels)."""
-    if emu and df:
-        raise ValueError("emu and df exclude each other")
-    if emu or df:
+    arrays, convolution sums on the tensor cores)."""
+    if emu:
         if t.dtype != torch.float64:
-            raise TypeError("emu=True / df=True need float64 arrays")
-        return WVL_F64_EMU if emu else WVL_F64_DF
+            raise TypeError("emu=True needs float64 arrays")
+        return WVL_F64_EMU
     if t.dtype == torch.float64:
         return WVL_F64
     if t.dtype == torch.float32:
@@ -283,17 +280,17 @@ def kinetic(s, grid: Grid, k0=None, out=None, want_ekin=True, emu=False):
     return out, ek
 
 
-def density(psi_c, occ, grid: Grid, rho=None, emu=False, df=False):
+def density(psi_c, occ, grid: Grid, rho=None, emu=False):
     """rho += sum_o occ_o |psi_r,o|^2 (float64, (N3, N2, N1))."""
     norb = _norb(psi_c, grid.ncoef)
     rho = torch.zeros(grid.fine, dtype=torch.float64, device=psi_c.device) if rho is None else rho
     _dev(psi_c, "psi_c"), _dev(occ, "occ"), _dev(rho, "rho")
-    _run(lib().wvl_density, grid, _prec(psi_c, emu, df), norb, psi_c.device, psi_c.data_ptr(),
+    _run(lib().wvl_density, grid, _prec(psi_c, emu), norb, psi_c.device, psi_c.data_ptr(),
          occ.data_ptr(), rho.data_ptr())
     return rho
 
 
-def hpsi_local(psi_c, V, occ, grid: Grid, rho=None, out=None, emu=False, df=False):
+def hpsi_local(psi_c, V, occ, grid: Grid, rho=None, out=None, emu=False):
     """H_loc psi for norb orbitals of one cell; rho += density if given.
     Returns (hpsi_c, ekin, epot)."""
     norb = _norb(psi_c, grid.ncoef)
@@ -304,12 +301,12 @@ def hpsi_local(psi_c, V, occ, grid: Grid, rho=None, out=None, emu=False, df=Fals
         _dev(t, nm)
     if rho is not None:
         _dev(rho, "rho")
-    _run(lib().wvl_hpsi_local, grid, _prec(psi_c, emu, df), norb, psi_c.device, psi_c.data_ptr(),
+    _run(lib().wvl_hpsi_local, grid, _prec(psi_c, emu), norb, psi_c.device, psi_c.data_ptr(),
          V.data_ptr(), occ.data_ptr(), out.data_ptr(), _p(rho), ek.data_ptr(), ep.data_ptr())
     return out, ek, ep
 
 
-def energy(psi_c, V, occ, grid: Grid, rho=None, emu=False, df=False):
+def energy(psi_c, V, occ, grid: Grid, rho=None, emu=False):
     """Per-orbital (ekin, epot) without H psi; rho += density if given."""
     norb = _norb(psi_c, grid.ncoef)
     ek = torch.empty(norb, dtype=torch.float64, device=psi_c.device)
@@ -318,7 +315,7 @@ def energy(psi_c, V, occ, grid: Grid, rho=None, emu=False, df=False):
         _dev(t, nm)
     if rho is not None:
         _dev(rho, "rho")
-    _run(lib().wvl_energy, grid, _prec(psi_c, emu, df), norb, psi_c.device, psi_c.data_ptr(),
+    _run(lib().wvl_energy, grid, _prec(psi_c, emu), norb, psi_c.device, psi_c.data_ptr(),
          V.data_ptr(), occ.data_ptr(), _p(rho), ek.data_ptr(), ep.data_ptr())
     return ek, ep
 

@@ -19,7 +19,6 @@
 
 #include "wvl.h"
 #include "wvl_internal.h"
-#include "df.cuh"
 #include "emu.cuh"
 
 namespace wvl {
@@ -357,7 +356,6 @@ struct CellRun {
     int bx[3] = {0, 0, 0};         // free/surface BC: box extents inside the padded cell
     int bo[3] = {0, 0, 0};         // free/surface BC: padding per side along each axis
     bool emu = false;              // FP64 convolutions on the tensor cores (emu.cuh)
-    bool df = false;               // FP64 arrays, double-FP32 arithmetic on the fused kernels
     int chain = 0;                 // OP_HPSI: CHAIN_AUTO, CHAIN_PASSES or CHAIN_FUSED
     bool rho_shared = false;       // another run of the same call adds into the same rho:
                                    //   the density goes through the run's partials
@@ -741,25 +739,17 @@ struct StageClock {
 // kinetic = TA3 (T_3, A_3, compression); the analysis stage stays empty.
 // OP_ENERGY runs SYN3, SKM12 without v, POT3 without x and TA3 for <a, T_3 a>
 // alone; OP_DENSITY runs SYN3, SKM12 (t only) and POT3 (rho only).
-// K is the kernels' arithmetic type: T, or double-FP32 on FP64 arrays
-template <typename T, typename K = T>
+template <typename T>
 static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, cudaStream_t st) {
-    static_assert(sizeof(K) == sizeof(T), "the working type keeps the storage size");
     static const int kStage[FZ_NPROG] = {ST_SYN, ST_SYN, ST_MF, ST_MFT, ST_KIN};
     StageClock clk{prof, st};
-    constexpr int LTC = fz_ltc<K>();
-    auto taps = [](int kind, double h, K (&dst)[2][32]) {
-        PassParams<double> tp;
+    constexpr int LTC = fz_ltc<T>();
+    auto taps = [](int kind, double h, T (&dst)[2][32]) {
+        PassParams<T> tp;
         std::memset(&tp, 0, sizeof tp);
         fill_taps(tp, kind, h);
-        for (int e = 0; e < 2; ++e)
-            for (int t = 0; t < 32; ++t) {
-                if constexpr (std::is_same<K, df>::value) dst[e][t] = df_from(tp.f[e][t]);
-                else dst[e][t] = (K)tp.f[e][t];
-            }
+        std::memcpy(dst, tp.f, sizeof dst);
     };
-    auto kp = [](const T* q) { return reinterpret_cast<const K*>(q); };
-    auto kq = [](T* q) { return reinterpret_cast<K*>(q); };
     std::vector<int> groups(runs.size(), 1);
     const bool hpsi = op == OP_HPSI, energy = op != OP_DENSITY;
     for (int prog = 0; prog < FZ_NPROG; ++prog) {
@@ -768,7 +758,7 @@ static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, c
         clk.begin(kStage[prog]);
         size_t i = 0;
         while (i < runs.size()) {
-            FzParams<K> p;
+            FzParams<T> p;
             std::memset(&p, 0, sizeof p);
             const CellRun<T>& r0 = runs[i];
             switch (prog) {
@@ -791,7 +781,7 @@ static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, c
                 // the kinetic taps are per launch: one axis spacing per launch
                 if (k > 0 && (r.hg[0] != r0.hg[0] || r.hg[1] != r0.hg[1] || r.hg[2] != r0.hg[2]))
                     break;
-                FzSeg<K>& s = p.seg[k];
+                FzSeg<T>& s = p.seg[k];
                 s.P = r.P;
                 s.N1 = r.Nf[0];
                 s.N2 = r.Nf[1];
@@ -804,20 +794,20 @@ static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, c
                 const int ctiles = s.N2 * s.ncb;
                 const int ktiles = s.N3 + (s.N2 / 2) * s.ncb;   // Ekin partials per orbital
                 const bool plane = prog == FZ_SKM12 || prog == FZ_MFTA12;
-                s.RS = plane ? fz_plane_rs<K>(s.N1) : LTC;
+                s.RS = plane ? fz_plane_rs<T>(s.N1) : LTC;
                 long long units = r.norb;
-                K* const A = kq(r.buf[0]);
-                K* const B = kq(r.buf[1]);
-                K* const C = kq(r.buf[2]);
-                K* const D = kq(r.buf[3]);
+                T* const A = r.buf[0];
+                T* const B = r.buf[1];
+                T* const C = r.buf[2];
+                T* const D = r.buf[3];
                 switch (prog) {
-                case FZ_SYN3: s.in = kp(r.in); s.out = A; break;
+                case FZ_SYN3: s.in = r.in; s.out = A; break;
                 case FZ_SKM12:
                     s.in = A; s.out2 = hpsi ? C : nullptr; s.out3 = D;
                     s.part = energy ? r.kpart : nullptr; s.ptiles = ktiles; s.poff = 0;
                     break;
                 case FZ_POT3: {
-                    s.in = D; s.out = hpsi ? B : nullptr; s.V = energy ? kp(r.V) : nullptr;
+                    s.in = D; s.out = hpsi ? B : nullptr; s.V = energy ? r.V : nullptr;
                     s.occ = r.occ;
                     s.part = energy ? r.epart : nullptr; s.ptiles = ctiles; s.poff = 0;
                     // orbital groups, each adding one density partial of P doubles
@@ -842,17 +832,17 @@ static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, c
                 }
                 case FZ_MFTA12: s.in = B; s.in2 = C; s.out = D; break;
                 case FZ_TA3:
-                    s.in = hpsi ? D : nullptr; s.in2 = A; s.out = hpsi ? kq(r.out) : nullptr;
+                    s.in = hpsi ? D : nullptr; s.in2 = A; s.out = hpsi ? r.out : nullptr;
                     s.part = r.kpart; s.ptiles = ktiles; s.poff = s.N3;
                     break;
                 }
                 s.blk0 = jobs;
                 jobs += units * (plane ? s.N3 : prog == FZ_TA3 ? ctiles / 2 : ctiles);
-                smem = std::max(smem, fz_smem<K>(prog, s.N1, s.N2, s.N3));
+                smem = std::max(smem, fz_smem<T>(prog, s.N1, s.N2, s.N3));
             }
             p.nseg = k;
             p.njobs = jobs;
-            cudaError_t e = launch_fused<K>(prog, p, smem, st);
+            cudaError_t e = launch_fused<T>(prog, p, smem, st);
             if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
         }
     }
@@ -885,19 +875,6 @@ template <typename T>
 static wvl_status run_op(int op, std::vector<CellRun<T>>& runs, const TuneTable* tt,
                          Prof* prof, cudaStream_t st) {
     mark_shared_rho(runs);
-    if (!runs.empty() && runs.front().df) {
-        if constexpr (sizeof(T) == 8) {
-            if (op != OP_HPSI && op != OP_ENERGY && op != OP_DENSITY)
-                return fail(WVL_EUNSUPPORTED, "WVL_F64_DF: only the local Hamiltonian, energies "
-                            "and density");
-            if (!fused_ok(runs))
-                return fail(WVL_EUNSUPPORTED, "WVL_F64_DF runs on the fused kernels: every fine "
-                            "extent a multiple of 8 in [%d, %d], periodic full-grid cells",
-                            FZ_MIN_FINE, FZ_MAX_FINE);
-            return run_fused<T, df>(op, runs, prof, st);
-        }
-        return fail(WVL_EINVAL, "WVL_F64_DF takes FP64 arrays");
-    }
     if ((op == OP_HPSI || op == OP_ENERGY || op == OP_DENSITY) && !runs.empty()) {
         const int ch = runs.front().chain;
         const bool ok = fused_ok(runs);
@@ -944,8 +921,8 @@ static wvl_status run_op(int op, std::vector<CellRun<T>>& runs, const TuneTable*
 
 // ------------------------------------------------------------ validation
 static wvl_status check_prec(int prec) {
-    if (prec != WVL_F64 && prec != WVL_F32 && prec != WVL_F64_EMU && prec != WVL_F64_DF)
-        return fail(WVL_EINVAL, "prec must be WVL_F64, WVL_F32, WVL_F64_EMU or WVL_F64_DF");
+    if (prec != WVL_F64 && prec != WVL_F32 && prec != WVL_F64_EMU)
+        return fail(WVL_EINVAL, "prec must be WVL_F64, WVL_F32 or WVL_F64_EMU");
     return WVL_OK;
 }
 static wvl_status check_grid(const wvl_grid* g) {
@@ -987,12 +964,11 @@ template <typename T>
 static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void* in,
                               void* out, const void* V, const double* occ, double* rho,
                               double* ekin, double* epot, void* ws, size_t ws_bytes,
-                              void* stream, const wvl_region* reg, bool emu, bool df = false) {
+                              void* stream, const wvl_region* reg, bool emu) {
     CellRun<T> r;
     grid_dims(grid, r.n, r.Nf, r.hg, r.P);
     r.norb = norb;
     r.emu = emu;
-    r.df = df;
     if (reg) {
         r.mapc = reg->coarse_index;
         r.mapf = reg->fine_index;
@@ -1193,8 +1169,7 @@ static wvl_status dispatch_single(int op, const wvl_grid* grid, int prec, int no
     g_err[0] = 0;
     if (prec != WVL_F32)
         return single_cell<double>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
-                                   ws_bytes, stream, reg, prec == WVL_F64_EMU,
-                                   prec == WVL_F64_DF);
+                                   ws_bytes, stream, reg, prec == WVL_F64_EMU);
     return single_cell<float>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
                               ws_bytes, stream, reg, false);
 }
@@ -1436,7 +1411,6 @@ wvl_status wvl_precondition(const wvl_grid* grid, int prec, int norb, const void
     WVL_TRY(check_ptr(rr, "rr", false));
     if (ncg < 0 || ncg > 10000) return fail(WVL_EINVAL, "ncg = %d out of range", ncg);
     if (g == x) return fail(WVL_EINVAL, "g and x must not alias");
-    if (prec == WVL_F64_DF) return fail(WVL_EUNSUPPORTED, "WVL_F64_DF: no preconditioner");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (prec != WVL_F32)
         return run_precond<double>(grid, norb, static_cast<const double*>(g), eps, ncg,
@@ -1456,8 +1430,6 @@ static wvl_status bc_checks(const wvl_grid* grid, const int* fa, int prec, int n
         if (fa[d] != 0 && fa[d] != 1) return fail(WVL_EINVAL, "free_axes[%d] must be 0 or 1", d);
     WVL_TRY(check_grid(grid));
     WVL_TRY(check_prec(prec));
-    if (prec == WVL_F64_DF)
-        return fail(WVL_EUNSUPPORTED, "WVL_F64_DF: periodic full-grid cells only");
     wvl_grid g;
     padded_grid(grid, fa, &g);
     WVL_TRY(check_grid(&g));
@@ -1614,9 +1586,7 @@ wvl_status wvl_plan_create(const wvl_grid* cells, int ncell, const int* cell_of_
     for (int o = 0; o < norb; ++o)
         if (cell_of_orb[o] < 0 || cell_of_orb[o] >= ncell)
             return fail(WVL_EINVAL, "cell_of_orb[%d] = %d out of range", o, cell_of_orb[o]);
-    if (prec == WVL_F64_DF && (flags & WVL_PLAN_PASSES))
-        return fail(WVL_EUNSUPPORTED, "WVL_F64_DF runs on the fused kernels only");
-    if ((flags & WVL_PLAN_FUSED) || prec == WVL_F64_DF) {
+    if (flags & WVL_PLAN_FUSED) {
         if (prec == WVL_F64_EMU)
             return fail(WVL_EUNSUPPORTED, "the fused chain has no tensor-core form");
         for (int c = 0; c < ncell; ++c) {
@@ -1701,7 +1671,6 @@ static wvl_status plan_runs(wvl_plan* plan, const void* psi, const void* const* 
         r.ekin = ekin + pr.o0;
         r.epot = epot + pr.o0;
         r.emu = plan->prec == WVL_F64_EMU;
-        r.df = plan->prec == WVL_F64_DF;
         r.chain = plan->chain;
         carve(r, static_cast<char*>(ws) + pr.ws_off);
         runs.push_back(r);
@@ -1754,7 +1723,6 @@ static wvl_status plan_exec(wvl_plan* plan, const void* psi, const void* const* 
     // attributes are set before capture (host-only calls)
     cudaError_t e = (plan->prec == WVL_F64_EMU) ? prepare_emu_kernels() : prepare_pass_kernels<T>();
     if (e == cudaSuccess && plan->prec != WVL_F64_EMU) e = prepare_fused_kernels<T>();
-    if (e == cudaSuccess && plan->prec == WVL_F64_DF) e = prepare_fused_kernels<df>();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -1807,9 +1775,8 @@ static wvl_status plan_tune(wvl_plan* plan, const void* psi, const void* const* 
     plan_runs<T>(plan, psi, V, occ, hpsi, rho, ekin, epot, ws, runs);
     // one full run leaves realistic values in every buffer
     WVL_TRY(run_op<T>(OP_HPSI, runs, &plan->tune, nullptr, st));
-    if (plan->prec == WVL_F64_EMU || plan->prec == WVL_F64_DF) {
-        // the emulated passes have one launch shape, the double-FP32 form one
-        // chain: nothing to tune
+    if (plan->prec == WVL_F64_EMU) {
+        // the emulated passes have one launch shape: nothing to tune
         plan->tuned = true;
         cudaError_t e = cudaStreamSynchronize(st);
         return e == cudaSuccess ? WVL_OK : cuda_fail(e, "autotune");

@@ -45,21 +45,10 @@
 
 #include <cuda_runtime.h>
 
-#include "df.cuh"
 #include "pass_kernel.cuh"
 
 namespace wvl {
-
-// double-FP32 sums (energies per item, the density over a group's orbitals)
-template <> struct Acc<df> {
-    df v{0.f, 0.f};
-    __device__ __forceinline__ void add(df x) { v = df_add(v, x); }
-    __device__ __forceinline__ double get() const { return df_to(v); }
-    __device__ __forceinline__ void reset() { v = {0.f, 0.f}; }
-};
-
 namespace {
-
 
 template <typename T>
 struct Vec {
@@ -69,11 +58,7 @@ struct Vec {
 template <typename T>
 __device__ __forceinline__ Vec<T> ldv(const T* p) {
     Vec<T> r;
-    if constexpr (std::is_same<T, df>::value) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
-        r.v[0] = {q.x, q.y};
-        r.v[1] = {q.z, q.w};
-    } else if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4) {
         const float4 q = *reinterpret_cast<const float4*>(p);
         r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
     } else {
@@ -83,17 +68,12 @@ __device__ __forceinline__ Vec<T> ldv(const T* p) {
     return r;
 }
 
-// stores the normalised values (double-FP32: |lo| <= ulp(hi) / 2)
 template <typename T>
 __device__ __forceinline__ void stv(T* p, const T (&v)[16 / sizeof(T)]) {
-    if constexpr (std::is_same<T, df>::value) {
-        const df a = settle(v[0]), b = settle(v[1]);
-        *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
-    } else if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4)
         *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
+    else
         *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-    }
 }
 
 // compile-time loop: f(integral_constant<int, 0>) ... f(integral_constant<int, N - 1>),
@@ -131,7 +111,7 @@ __device__ __forceinline__ void fir(const T (&win)[NW], const T (&f)[2][32], T (
         static_for<NOUT>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
-            if constexpr (t >= 0 && t < NT) acc[k] = mac(f[k & 1][t], win[j + D], acc[k]);
+            if constexpr (t >= 0 && t < NT) acc[k] = fma(f[k & 1][t], win[j + D], acc[k]);
         });
     });
 }
@@ -181,7 +161,7 @@ __device__ __forceinline__ void row_pass_r(const T* __restrict__ src, T* __restr
         }
         T acc[RR];
         #pragma unroll
-        for (int k = 0; k < RR; ++k) acc[k] = zero<T>();
+        for (int k = 0; k < RR; ++k) acc[k] = T(0);
         fir<T, KIND, RR, D>(win, f, acc);
         T* o = dst + r * RS + c0;
         #pragma unroll
@@ -228,7 +208,7 @@ __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* _
     #pragma unroll
     for (int k = 0; k < RC; ++k)
         #pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[k][e] = zero<T>();
+        for (int e = 0; e < VEC; ++e) acc[k][e] = T(0);
     const T* base = src + cv * VEC;
     const int* ro = rowoff + FZ_PADR + r0 - HL;
     static_for<W>([&](auto jc) {
@@ -239,7 +219,7 @@ __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* _
             constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
             if constexpr (t >= 0 && t < NT) {
                 #pragma unroll
-                for (int e = 0; e < VEC; ++e) acc[k][e] = mac(f[k & 1][t], v.v[e], acc[k][e]);
+                for (int e = 0; e < VEC; ++e) acc[k][e] = fma(f[k & 1][t], v.v[e], acc[k][e]);
             }
         });
     });
@@ -318,7 +298,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
             const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
             T acc[RC][VEC];
             col_item<T, K_KIN>(X, rowoff, r0, cv, p.tap[2], acc);
-            T ei = zero<T>();   // the item's <s, v> (at most 32 products), then compensated
+            T ei = T(0);   // the item's <s, v> (at most 32 products), then compensated
             #pragma unroll
             for (int kk = 0; kk < RC; ++kk) {
                 const int off = (r0 + kk) * RS + cv * VEC;
@@ -327,8 +307,8 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
                 T v[VEC];
                 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
-                    v[q] = add(acc[kk][q], t1.v[q]);
-                    ei = mac(sv.v[q], v[q], ei);
+                    v[q] = acc[kk][q] + t1.v[q];
+                    ei = fma(sv.v[q], v[q], ei);
                 }
                 if (S.out2 != nullptr) stv(S.out2 + pbase + (long long)(r0 + kk) * N1 + cv * VEC, v);
             }
@@ -379,7 +359,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
                 const Vec<T> v = ldv(xw);
                 T w[VEC];
                 #pragma unroll
-                for (int q = 0; q < VEC; ++q) w[q] = add(acc[kk][q], v.v[q]);
+                for (int q = 0; q < VEC; ++q) w[q] = acc[kk][q] + v.v[q];
                 stv(xw, w);
             }
         }
@@ -475,12 +455,6 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         cp_commit();
         cp_wait<0>();
         __syncthreads();
-        if constexpr (std::is_same<T, df>::value) {
-            // the compressed form holds FP64 values: to double-FP32 in place
-            double* const xd = reinterpret_cast<double*>(X);
-            for (int i = threadIdx.x; i < N3 * RS; i += NT) X[i] = df_from(xd[i]);
-            __syncthreads();
-        }
         T* const ob = S.out + (long long)u * S.P + col0;
         #pragma unroll 1
         for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
@@ -509,18 +483,18 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             const int so = sub * N3 * RS;
             T acc[RC][VEC];
             col_item<T, K_KIN>(Y + so, rowoff, r0, cv, p.tap[0], acc);
-            T ei = zero<T>();
+            T ei = T(0);
             #pragma unroll
             for (int kk = 0; kk < RC; ++kk) {
                 const int off = so + (r0 + kk) * RS + cv * VEC;
                 const Vec<T> av = ldv(Y + off);
                 #pragma unroll
-                for (int q = 0; q < VEC; ++q) ei = mac(av.v[q], acc[kk][q], ei);
+                for (int q = 0; q < VEC; ++q) ei = fma(av.v[q], acc[kk][q], ei);
                 if (full) {
                     const Vec<T> wv = ldv(X + off);
                     T z[VEC];
                     #pragma unroll
-                    for (int q = 0; q < VEC; ++q) z[q] = add(wv.v[q], acc[kk][q]);
+                    for (int q = 0; q < VEC; ++q) z[q] = wv.v[q] + acc[kk][q];
                     stv(X + off, z);
                 }
             }
@@ -564,19 +538,10 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             for (int i3 = warp; i3 < N3 / 2; i3 += NT / 32) {
                 const long long k0 = (long long)i3 * nxy + kb;
                 const T* const y0 = Y + (2 * i3) * RS;    // a3 = 0, a2 = 0
-                if constexpr (std::is_same<T, df>::value) {
-                    // H psi is returned in FP64
-                    double* const ccd = reinterpret_cast<double*>(cc);
-                    double* const frd = reinterpret_cast<double*>(cf) + 7 * k0;
-                    if (lane < nci) ccd[k0 + lane] = df_to(y0[2 * lane]);
-                    #pragma unroll 1
-                    for (int pos = lane; pos < 7 * nci; pos += 32) frd[pos] = df_to(y0[roff[pos]]);
-                } else {
-                    if (lane < nci) cc[k0 + lane] = y0[2 * lane];
-                    T* const fr = cf + 7 * k0;
-                    #pragma unroll 1
-                    for (int pos = lane; pos < 7 * nci; pos += 32) fr[pos] = y0[roff[pos]];
-                }
+                if (lane < nci) cc[k0 + lane] = y0[2 * lane];
+                T* const fr = cf + 7 * k0;
+                #pragma unroll 1
+                for (int pos = lane; pos < 7 * nci; pos += 32) fr[pos] = y0[roff[pos]];
             }
         }
         }
@@ -599,37 +564,28 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         const bool pot = S.V != nullptr, full = S.out != nullptr;
         if (pot) load_tile(Z, S.V + col0);
         load_tile(X, S.in + (long long)o0 * S.P + col0);
-        if constexpr (std::is_same<T, df>::value) {
-            if (pot) {
-                // the potential is given in FP64: to double-FP32 in place
-                cp_wait<0>();
-                __syncthreads();
-                double* const zd = reinterpret_cast<double*>(Z);
-                for (int i = threadIdx.x; i < N3 * RS; i += NT) Z[i] = df_from(zd[i]);
-            }
-        }
         #pragma unroll 1
         for (int o = o0; o < o1; ++o) {
             cp_wait<0>();
             __syncthreads();
             Acc<T> e;
-            const T occ = from_double<T>(S.occ ? S.occ[o] : 1.0);
+            const T occ = (T)(S.occ ? S.occ[o] : 1.0);
             T acc[RC][VEC];
             if (mine) {
                 col_item<T, K_MF, RC>(X, rowoff, r0, cv, p.tap[0], acc);
-                T ei = zero<T>();
+                T ei = T(0);
                 #pragma unroll
                 for (int kk = 0; kk < RC; ++kk) {
                     const int off = (r0 + kk) * RS + cv * VEC;
                     #pragma unroll
-                    for (int q = 0; q < VEC; ++q) racc[kk][q].add(mul(mul(occ, acc[kk][q]), acc[kk][q]));
+                    for (int q = 0; q < VEC; ++q) racc[kk][q].add(occ * acc[kk][q] * acc[kk][q]);
                     if (pot) {
                         const Vec<T> vv = ldv(Z + off);
                         T y[VEC];
                         #pragma unroll
                         for (int q = 0; q < VEC; ++q) {
-                            y[q] = mul(vv.v[q], acc[kk][q]);
-                            ei = mac(y[q], acc[kk][q], ei);
+                            y[q] = vv.v[q] * acc[kk][q];
+                            ei = fma(y[q], acc[kk][q], ei);
                         }
                         if (full) stv(Y + off, y);
                     }
@@ -752,9 +708,6 @@ cudaError_t prepare_fused_kernels() {
 }
 
 template size_t fz_smem<float>(int, int, int, int);
-template size_t fz_smem<df>(int, int, int, int);
-template cudaError_t launch_fused<df>(int, const FzParams<df>&, size_t, cudaStream_t);
-template cudaError_t prepare_fused_kernels<df>();
 template size_t fz_smem<double>(int, int, int, int);
 template cudaError_t launch_fused<float>(int, const FzParams<float>&, size_t, cudaStream_t);
 template cudaError_t launch_fused<double>(int, const FzParams<double>&, size_t, cudaStream_t);

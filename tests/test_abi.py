@@ -116,7 +116,7 @@ def test_plan_creation_and_offsets():
     with pytest.raises(W.WvlError):
         W.Plan(cells, [0, 2], prec=0)
     with pytest.raises(W.WvlError):
-        W.Plan(cells, [0], prec=4)
+        W.Plan(cells, [0], prec=3)
 
 
 def test_tensor_core_form_validation():
@@ -126,7 +126,7 @@ def test_tensor_core_form_validation():
     assert W.workspace_size(g, W.WVL_F64_EMU, 3) == W.workspace_size(g, W.WVL_F64, 3)
     L = W.lib()
     sz = ctypes.c_size_t(0)
-    assert L.wvl_workspace_size(ctypes.byref(g.c()), 4, 1, ctypes.byref(sz)) == 1   # EINVAL
+    assert L.wvl_workspace_size(ctypes.byref(g.c()), 3, 1, ctypes.byref(sz)) == 1   # EINVAL
     st = L.wvl_hpsi_local(ctypes.byref(g.c()), W.WVL_F64_EMU, 1, None, None, None, None, None,
                           None, None, None, 0, None)
     assert st == 1                                                             # EINVAL (NULL)
@@ -167,19 +167,3 @@ def test_chain_flags_validation():
     co = (ctypes.c_int * 1)(0)
     assert L.wvl_plan_create(ctypes.byref(g), 1, co, 1, 0, 4 | 8, ctypes.byref(h)) == 1   # EINVAL
     assert L.wvl_plan_create(ctypes.byref(g), 1, co, 1, 0, 16, ctypes.byref(h)) == 1      # EINVAL
-
-
-def test_double_fp32_form_validation():
-    """WVL_F64_DF takes FP64 arrays (the FP64 workspace) and runs on the
-    fused kernels only: plans on cells they do not take, or with
-    WVL_PLAN_PASSES, are refused on the host."""
-    g = W.Grid((16, 20, 24))
-    assert W.workspace_size(g, W.WVL_F64_DF, 3) == W.workspace_size(g, W.WVL_F64, 3)
-    W.Plan([g], [0, 0], prec=W.WVL_F64_DF)
-    W.Plan([g], [0, 0], prec=W.WVL_F64_DF, chain="fused")
-    with pytest.raises(W.WvlError):
-        W.Plan([g], [0, 0], prec=W.WVL_F64_DF, chain="passes")
-    with pytest.raises(W.WvlError):
-        W.Plan([W.Grid((12, 16, 16))], [0], prec=W.WVL_F64_DF)
-    with pytest.raises(W.WvlError):
-        W.Plan([W.Grid((64, 64, 64))], [0], prec=W.WVL_F64_DF)   # FP64 planes too large
