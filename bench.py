@@ -523,6 +523,30 @@ def measure_variants(args, W, torch, dev):
     del psi, hp, rho, Vd
     torch.cuda.empty_cache()
 
+    # ---- one orbital on a coarse 32^3 cell (fine 64^3), FP64: the single
+    # call and a graph-captured plan (launch-bound at this size)
+    n0 = (32, 32, 32)
+    g0 = W.Grid(n0)
+    p0 = torch.from_numpy(inputs.orbital(0, 0, n0)).to(dev)
+    V0 = torch.from_numpy(inputs.gaussian_potential(0, 0, n0)).to(dev)
+    o0 = torch.full((1,), 2.0, dtype=torch.float64, device=dev)
+    r0 = torch.zeros(g0.fine, dtype=torch.float64, device=dev)
+    ms_single = _time_steps(torch, lambda: W.hpsi_local(p0, V0, o0, g0, rho=r0), 20, 5)
+    plan0 = W.Plan([g0], [0], prec=W.WVL_F64, graph=True)
+    h0 = torch.empty_like(p0)
+    e0k = torch.empty(1, dtype=torch.float64, device=dev)
+    e0p = torch.empty_like(e0k)
+    ms_plan = _time_steps(torch, lambda: plan0.hpsi(p0, [V0], o0, hpsi=h0, rho=[r0], ekin=e0k,
+                                                    epot=e0p), 20, 5)
+    out["config0_single_orbital"] = {
+        "workload": "one orbital, periodic coarse 32^3 (fine 64^3), FP64, H psi + density + "
+                    "energies",
+        "ms_single_call": ms_single, "ms_graph_plan": ms_plan,
+        "value": 1.0 / (ms_plan * 1e-3), "unit": UNIT,
+        "checked": "tests/test_gpu_parity.py::test_config0_full (1e-12 against the oracle)",
+    }
+    del plan0
+
     # ---- single-pass FP64 sweep (one orbital, fine 32^3 .. 256^3): each 3D
     # operator is three 1D passes; per pass 16 compulsory bytes per point
     # (read + write) and 2 x taps flops per point
