@@ -229,20 +229,14 @@ __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* _
 // threads of a column kernel: FZ_TA3 holds two I2 rows per job
 template <int PROG>
 __host__ __device__ constexpr int fz_cthreads() { return PROG == FZ_TA3 ? 2 * FZ_CTHREADS : FZ_CTHREADS; }
-// rows per column-pass item (4 rows and twice the threads in FZ_POT3, which
-// halves its registers, measured slower: 0.69 against 0.56 ms per step)
-template <int PROG>
-__host__ __device__ constexpr int fz_rc() { return FZ_RC; }
-template <int PROG>
-__host__ __device__ constexpr int fz_pthreads() { return FZ_PTHREADS; }
 
 template <typename T, int PROG>
-__global__ void __launch_bounds__(fz_pthreads<PROG>())
+__global__ void __launch_bounds__(FZ_PTHREADS)
 fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
     constexpr int VEC = 16 / (int)sizeof(T);
     constexpr int RC = FZ_RC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[fz_pthreads<PROG>() / 32];
+    __shared__ double red[FZ_PTHREADS / 32];
     __shared__ int rowoff[FZ_MAX_FINE + 2 * FZ_PADR];
     const long long job = blockIdx.x;
     int si = 0;
@@ -259,7 +253,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
     const int ncv = N1 / VEC;
     const int nitems = (N2 / RC) * ncv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NWARP = fz_pthreads<PROG>() / 32;
+    constexpr int NWARP = FZ_PTHREADS / 32;
 
     // the plane, row I2 -> X + I2 RS (a warp per row, lanes over its vectors)
     {
@@ -391,7 +385,7 @@ template <typename T, int PROG>
 __global__ void __launch_bounds__(fz_cthreads<PROG>(), fz_cminb<PROG>())
 fz_col_kernel(const __grid_constant__ FzParams<T> p) {
     constexpr int VEC = 16 / (int)sizeof(T);
-    constexpr int RC = fz_rc<PROG>();
+    constexpr int RC = FZ_RC;
     constexpr int LTC = fz_ltc<T>();
     constexpr int CV = LTC / VEC;        // 8 column vectors per tile row
     constexpr int NT = fz_cthreads<PROG>();
@@ -664,7 +658,7 @@ cudaError_t fz_launch(const FzParams<T>& p, size_t smem, cudaStream_t st) {
     if (p.njobs <= 0) return cudaSuccess;
     if (p.njobs > 0x7fffffffLL || smem > (size_t)FZ_SMEM_OPTIN) return cudaErrorInvalidConfiguration;
     if constexpr (fz_is_plane<PROG>())
-        fz_plane_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(fz_pthreads<PROG>()), smem, st>>>(p);
+        fz_plane_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(FZ_PTHREADS), smem, st>>>(p);
     else
         fz_col_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(fz_cthreads<PROG>()), smem, st>>>(p);
     count_launches(1);
