@@ -60,7 +60,7 @@ FUSED_BPP, PASSES_BPP = 52.0, 140.0
 # by an FMA-chain probe on the GB300 (MEASURED_PEAKS.json has no FP32 entry)
 FP32_FMA_PER_POINT, FP32_PEAK_TFLOPS = 279.0, 73.8
 # FP64-pipe operations per fine point of one kinetic pass (an FMA counts as one)
-KIN_OPS_PER_POINT_PER_PASS = 29
+KIN_OPS_PER_POINT_PER_PASS = 27   # FMAs per point of a kinetic pass (the 27 taps above FP64 resolution)
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of GB300 (2 flops per DFMA)
 
 
@@ -781,7 +781,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     # DRAM bytes of one kinetic pass-1 launch from an ncu capture of the small
     # profiling case (36 orbitals, 33.6 M fine points, --per-cell 12), scaled
     # to this launch by the fine points processed; null for any other workload.
-    traffic = (1030.6e6 * pts / 33619968) if (args.per_cell == PER_CELL and args.prec == "f64") else None
+    traffic = (1030.9e6 * pts / 33619968) if (args.per_cell == PER_CELL and args.prec == "f64") else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                 "traffic": traffic, "kernel": "kinetic 1D pass (FP64 DFMA pipe)",

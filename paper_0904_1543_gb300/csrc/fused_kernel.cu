@@ -111,7 +111,7 @@ __device__ __forceinline__ void fir(const T (&win)[NW], const T (&f)[2][32], T (
         static_for<NOUT>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
-            if constexpr (t >= 0 && t < NT) acc[k] = fma(f[k & 1][t], win[j + D], acc[k]);
+            if constexpr (t >= KT<KIND>::SKIP && t < NT - KT<KIND>::SKIP) acc[k] = fma(f[k & 1][t], win[j + D], acc[k]);
         });
     });
 }
@@ -217,7 +217,7 @@ __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* _
         static_for<RC>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
-            if constexpr (t >= 0 && t < NT) {
+            if constexpr (t >= KT<KIND>::SKIP && t < NT - KT<KIND>::SKIP) {
                 #pragma unroll
                 for (int e = 0; e < VEC; ++e) acc[k][e] = fma(f[k & 1][t], v.v[e], acc[k][e]);
             }
