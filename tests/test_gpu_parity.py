@@ -387,3 +387,27 @@ def test_config1_single_passes_full_size(W, nc, ops):
         back = W.analysis(cuda(x), g)
         ref = O.compress(O.analysis3d(x[0]), n)
         close(host(back[0]), ref, RTOL64, f"analysis {nc}")
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_longest_lines_f32(W, axis):
+    """FP32 lines of the largest fine extent (1024 points) along each axis,
+    the other axes at 2 fine points (the transposing passes: the fused
+    kernels take extents of 32 to 128), against the oracle on the
+    FP32-rounded inputs."""
+    import torch
+    n = [1, 1, 1]
+    n[axis] = 512
+    n = tuple(n)
+    g = W.Grid(n, (0.3, 0.25, 0.35))
+    psi = inputs.orbitals(372, 2, n).astype(np.float32)
+    V = inputs.gaussian_potential(372, 0, n).astype(np.float32)
+    occ = np.array([2.0, 1.0])
+    rho = torch.zeros(g.fine, dtype=torch.float64, device="cuda")
+    hp, ek, ep = W.hpsi_local(cuda(psi), cuda(V), cuda(occ), g, rho=rho)
+    hp_r, rho_r, ek_r, ep_r = O.hpsi_batch(psi.astype(np.float64), V.astype(np.float64), occ, n,
+                                           g.h)
+    close(host(hp), hp_r, 2e-5, f"hpsi f32 axis {axis}")
+    close(host(rho), rho_r, 1e-5, f"rho f32 axis {axis}")
+    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < 1e-5
+    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < 1e-5
