@@ -278,3 +278,32 @@ def test_fused_energy_and_density_f32(W, n, norb):
     close(host(rho), rho_r, 1e-5, "rho (energy)")
     rho2 = W.density(cuda(psi), cuda(occ), g)
     close(host(rho2), rho_r, 1e-5, "rho (density)")
+
+
+def test_mixed_eligibility_falls_back_to_passes(W):
+    """An FP32 plan with one cell the fused kernels take and one they do not
+    runs the transposing passes for all (the automatic choice), with the
+    FP32 results against the oracle."""
+    cells = [W.Grid((16, 16, 16)), W.Grid((5, 4, 7))]
+    cell_of_orb = [0, 0, 1, 1]
+    psis = [inputs.orbital(63, o, cells[c].n).astype(np.float32) for o, c in enumerate(cell_of_orb)]
+    Vs = [inputs.gaussian_potential(63, c, cells[c].n).astype(np.float32) for c in range(2)]
+    occ = np.array([2.0, 1.0, 2.0, 0.5])
+    out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, W.WVL_F32, None)
+    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, 2e-5, 1e-5)
+    with pytest.raises(W.WvlError):
+        W.Plan(cells, cell_of_orb, prec=W.WVL_F32, chain="fused")
+
+
+def test_fused_more_cells_than_one_launch_holds(W):
+    """Ten cells (more than the 8 segments of one launch) of different sizes
+    in one FP64 fused plan: every program is split into two launches."""
+    sizes = [(16, 16, 16), (16, 20, 16), (20, 16, 16), (16, 16, 20), (24, 16, 16),
+             (16, 24, 16), (16, 16, 24), (20, 20, 16), (16, 20, 20), (20, 16, 20)]
+    cells = [W.Grid(s) for s in sizes]
+    cell_of_orb = list(range(10))
+    psis = [inputs.orbital(64, o, sizes[o]) for o in range(10)]
+    Vs = [inputs.gaussian_potential(64, c, sizes[c]) for c in range(10)]
+    occ = np.linspace(1.0, 2.0, 10)
+    out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, W.WVL_F64, "fused")
+    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, RTOL64, RTOL64)
