@@ -561,7 +561,7 @@ def measure_variants(args, W, torch, dev):
         res_n = {}
         for name, taps, fn in (("magicfilter", 16, lambda: W.magicfilter(xs, gs)),
                                ("magicfilter_T", 16, lambda: W.magicfilter_T(xs, gs)),
-                               ("kinetic", 29, lambda: W.kinetic(xs, gs)),
+                               ("kinetic", KIN_OPS_PER_POINT_PER_PASS, lambda: W.kinetic(xs, gs)),
                                ("synthesis", 16, lambda: W.synthesis(cs, gs)),
                                ("analysis", 16, lambda: W.analysis(xs, gs))):
             ms_op = _time_steps(torch, fn, 5, 3)
