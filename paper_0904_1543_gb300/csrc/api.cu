@@ -244,6 +244,14 @@ static cudaError_t launch_emu_t(int kind, int mode, const PassParams<double>& p,
 static cudaError_t launch_emu_t(int, int, const PassParams<float>&, long long, cudaStream_t) {
     return cudaErrorInvalidValue;
 }
+static cudaError_t launch_line_exp_t(const double* in, int* lexp, int n1, int n2, int n3,
+                                     int norb, long long P, cudaStream_t st) {
+    return launch_line_exp(in, lexp, n1, n2, n3, norb, P, st);
+}
+static cudaError_t launch_line_exp_t(const float*, int*, int, int, int, int, long long,
+                                     cudaStream_t) {
+    return cudaErrorInvalidValue;
+}
 
 template <typename T>
 static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
@@ -313,6 +321,14 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
         p.nseg = k;
         p.nunits = blk;
         if (emu) {
+            if (c.mode == M_UNCOMP)
+                for (int q = 0; q < k; ++q) {
+                    const Seg<T>& s = p.seg[q];
+                    if (s.lexp == nullptr) continue;
+                    cudaError_t e = launch_line_exp_t(s.in, const_cast<int*>(s.lexp), s.n1, s.n2,
+                                                      c.segs[first + q].Nf[2] / 2, s.norb, s.P, st);
+                    if (e != cudaSuccess) return cuda_fail(e, "line exponent launch");
+                }
             cudaError_t e = launch_emu_t(c.kind, c.mode, p, blk, st);
             if (e == cudaErrorInvalidValue)
                 return fail(WVL_EUNSUPPORTED, "tensor-core pass: filter digit schedule not supported");
@@ -454,7 +470,15 @@ static std::vector<PassCall<T>> build_calls(int op, std::vector<CellRun<T>>& run
     const int A_ = 0, B_ = 1, C_ = 2, D_ = 3;
 
     auto synthesis = [&](bool to_user) {
-        add(K_SYN, M_UNCOMP, 1, ST_SYN, [&](CellRun<T>& r) { return seg_for(r, r.in, B(r, A_)); });
+        add(K_SYN, M_UNCOMP, 1, ST_SYN, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for(r, r.in, B(r, A_));
+            // the tensor-core pass takes its line exponents from a coalesced
+            // read of the compressed form (into buffer C, free until the
+            // kinetic or density passes)
+            if (r.emu && r.mapc == nullptr && r.bx[0] == 0)
+                d.s.lexp = reinterpret_cast<const int*>(B(r, C_));
+            return d;
+        });
         add(K_SYN, M_PLAIN, 2, ST_SYN, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
         add(K_SYN, M_PLAIN, 3, ST_SYN, [&](CellRun<T>& r) {
             return seg_for<T>(r, B(r, B_), to_user ? r.out : B(r, D_));

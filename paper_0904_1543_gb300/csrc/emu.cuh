@@ -226,6 +226,11 @@ __device__ __forceinline__ void digit_floats(long long X, float (&f)[S]) {
 cudaError_t launch_pass_emu(int kind, int mode, const PassParams<double>& p, long long nunits,
                             cudaStream_t st);
 cudaError_t prepare_emu_kernels();
+// Largest biased exponent of every line of synthesis pass 1's input (full-
+// grid compressed form, cell of n1 x n2 x n3 coarse points, norb orbitals of
+// P elements): lexp[orbital][x3 * 2 n2 + x2].
+cudaError_t launch_line_exp(const double* in, int* lexp, int n1, int n2, int n3, int norb,
+                            long long P, cudaStream_t st);
 // bounded waits of the emulated passes that ran out since the last call
 cudaError_t emu_take_timeouts(unsigned* count);
 // one bounded wait that cannot be satisfied, given up after about ms

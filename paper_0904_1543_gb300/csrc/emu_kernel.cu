@@ -457,7 +457,12 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
         const Seg<double>& Sg = p.seg[J.si];
         const int n = Sg.n;
         {
-            // ---------------------------- one exponent per line (whole line, 8 lines in flight per warp)
+            // ---------------------------- one exponent per line: given (synthesis
+            // pass 1 on the full grid), or the whole line read, 8 lines in flight per warp
+            if (MODE == M_UNCOMP && Sg.lexp != nullptr) {
+                for (int r = tid; r < M; r += THREADS)
+                    rowE[r] = scale_of(r < J.lt ? Sg.lexp[(long long)J.orb * Sg.N + J.a0 + r] : 0);
+            } else
 #pragma unroll 1
             for (int i = 0; i < RPW; i += 8) {
                 int eb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -644,6 +649,56 @@ static cudaError_t launch_emu(const Params& ep, long long nunits, cudaStream_t s
 }
 
 }  // namespace emu
+
+// One warp per (orbital, i3, i2) row of coarse points reads the row's scaling
+// coefficients and 7-component wavelet records as contiguous runs; the
+// coefficient c^mu of point (i1, i2, i3) lies on line (x3, x2) = (2 i3 + a3,
+// 2 i2 + a2) of the interleaved array, mu = a1 + 2 a2 + 4 a3, so the row
+// gives the maxima of four lines.
+__global__ void line_exp_kernel(const double* __restrict__ in, int* __restrict__ lexp, int n1,
+                                int n2, int n3, long long P, long long nrows) {
+    const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    const long long rows_orb = (long long)n3 * n2;
+    const int orb = (int)(row / rows_orb);
+    const int rem = (int)(row - orb * rows_orb);
+    const int i3 = rem / n2, i2 = rem - i3 * n2;
+    const double* cc = in + (long long)orb * P;
+    const long long k0 = ((long long)i3 * n2 + i2) * n1;
+    const double* cf = cc + P / 8 + 7 * k0;
+    int m[4] = {0, 0, 0, 0};   // line (a3, a2) -> m[2 a3 + a2]
+    for (int i1 = lane; i1 < n1; i1 += 32) m[0] = max(m[0], emu::bexp(cc[k0 + i1]));
+    for (int pos = lane; pos < 7 * n1; pos += 32) {
+        const int mu = pos % 7 + 1;
+        const int e = emu::bexp(cf[pos]);
+        const int l = 2 * (mu >> 2) + ((mu >> 1) & 1);
+        m[0] = l == 0 ? max(m[0], e) : m[0];
+        m[1] = l == 1 ? max(m[1], e) : m[1];
+        m[2] = l == 2 ? max(m[2], e) : m[2];
+        m[3] = l == 3 ? max(m[3], e) : m[3];
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) m[l] = (int)__reduce_max_sync(0xffffffffu, (unsigned)m[l]);
+    if (lane < 4) {
+        const int a3 = lane >> 1, a2 = lane & 1;
+        const int N2 = 2 * n2, N3 = 2 * n3;
+        const int v = lane == 0 ? m[0] : lane == 1 ? m[1] : lane == 2 ? m[2] : m[3];
+        lexp[(long long)orb * N2 * N3 + (long long)(2 * i3 + a3) * N2 + 2 * i2 + a2] = v;
+    }
+}
+
+cudaError_t launch_line_exp(const double* in, int* lexp, int n1, int n2, int n3, int norb,
+                            long long P, cudaStream_t st) {
+    const long long nrows = (long long)norb * n3 * n2;
+    if (nrows <= 0) return cudaSuccess;
+    const int threads = 256;
+    const long long blocks = (nrows * 32 + threads - 1) / threads;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    line_exp_kernel<<<(unsigned)blocks, threads, 0, st>>>(in, lexp, n1, n2, n3, P, nrows);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pass_emu(int kind, int mode, const PassParams<double>& p, long long nunits,
                             cudaStream_t st) {

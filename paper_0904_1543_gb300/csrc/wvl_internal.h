@@ -58,6 +58,8 @@ struct Seg {
     const double* eps;    // M_KMID pass 1 without in2: K_0 = -eps[o] G (Helmholtz shift)
     const int* mapc;      // M_UNCOMP/M_COMP with a localisation region: coarse point ->
     const int* mapf;      //   position of c^0 / index k of c^{1..7} (ncoarse + 7k), or -1
+    const int* lexp;      // emulated M_UNCOMP: largest biased exponent of each input line,
+                          //   [orbital][line] (null: the pass scans its lines)
     long long clen;       // compressed length of one orbital (orbital stride there)
     long long ncoarse;    // scaling coefficients stored (start of the wavelet block)
     int bx1, bx2, bx3;    // free/surface boundary conditions: box extents inside the
