@@ -1,7 +1,7 @@
 """GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
 identical seeded inputs.
 
-Tolerances.  FP64: the benchmark spec's bound, 1e-12 relative -- normwise
+Tolerances.  FP64: 1e-12 relative, the stated accuracy target -- normwise
 (max|d| / max|ref|) and elementwise where |ref| >= 1e-3 max|ref|; energies
 relative to |E|.  The kernels and the oracle sum the same terms in different
 orders (FMA chains of at most 29 taps per pass, 15 passes), which leaves

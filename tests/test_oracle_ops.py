@@ -91,7 +91,7 @@ def test_mf_kinetic_bruteforce(n):
 @pytest.mark.parametrize("nc", [1, 2, 3, 4, 8, 16])
 def test_synthesis_orthogonal(nc):
     """Periodised fast wavelet transform is orthogonal at every size:
-    analysis o synthesis = identity (spec bound 1e-14)."""
+    analysis o synthesis = identity to 1e-14."""
     A = mat_synthesis(nc)
     assert np.max(np.abs(A.T @ A - np.eye(2 * nc))) < 1e-14
 
