@@ -100,20 +100,63 @@ __device__ __forceinline__ double fz_block_sum(double v, double* red) {
     return t;
 }
 
+// the taps of a row-pass filter that apply (the kinetic a_{+-14} do not)
+template <int KIND>
+__host__ __device__ constexpr bool tap_on(int t) {
+    return t >= KT<KIND>::SKIP && t < KT<KIND>::NT - KT<KIND>::SKIP;
+}
+
+// Tap pairs of the packed FP32 row pass: window element j feeds outputs
+// 2m and 2m + 1 with taps t0 = d - off0 (even filter) and t1 = d - 1 - off1
+// (odd filter), d = j - 2m; a tap that does not apply is 0.
+template <int KIND>
+void fz_tap_pairs(const float (&f)[2][32], float2 (&tp)[32]) {
+    for (int d = 0; d < 32; ++d) {
+        const int t0 = d - KT<KIND>::OFF0, t1 = d - 1 - KT<KIND>::OFF1;
+        tp[d].x = tap_on<KIND>(t0) ? f[0][t0] : 0.f;
+        tp[d].y = tap_on<KIND>(t1) ? f[1][t1] : 0.f;
+    }
+}
+
 // acc[k] += f[k & 1][t] win[j + D] for output k of a chunk whose window
-// element j is input position (first output - HL + j)
+// element j is input position (first output - HL + j).  FP32: outputs 2m,
+// 2m + 1 take one packed FMA per window element, the element broadcast and
+// the two taps a pair from tp (two FMAs per lane per instruction).
 template <typename T, int KIND, int NOUT, int D, int NW>
-__device__ __forceinline__ void fir(const T (&win)[NW], const T (&f)[2][32], T (&acc)[NOUT]) {
+__device__ __forceinline__ void fir(const T (&win)[NW], const T (&f)[2][32],
+                                    const float2 (&tp)[32], T (&acc)[NOUT]) {
     constexpr int NT = KT<KIND>::NT;
     constexpr int W = NOUT + NT - 1 + KT<KIND>::EXTRA;
-    static_for<W>([&](auto jc) {
-        constexpr int j = decltype(jc)::value;
-        static_for<NOUT>([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
-            if constexpr (t >= KT<KIND>::SKIP && t < NT - KT<KIND>::SKIP) acc[k] = fma(f[k & 1][t], win[j + D], acc[k]);
+    if constexpr (sizeof(T) == 4) {
+        static_assert(NOUT % 2 == 0, "output pairs");
+        float2 a2[NOUT / 2];
+        #pragma unroll
+        for (int m = 0; m < NOUT / 2; ++m) a2[m] = make_float2(acc[2 * m], acc[2 * m + 1]);
+        static_for<W>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            const float2 ww = make_float2(win[j + D], win[j + D]);
+            static_for<NOUT / 2>([&](auto mc) {
+                constexpr int d = j - 2 * decltype(mc)::value;
+                constexpr int t0 = d - KT<KIND>::OFF0, t1 = d - 1 - KT<KIND>::OFF1;
+                if constexpr (d >= 0 && d < 32 && (tap_on<KIND>(t0) || tap_on<KIND>(t1)))
+                    a2[decltype(mc)::value] = __ffma2_rn(tp[d], ww, a2[decltype(mc)::value]);
+            });
         });
-    });
+        #pragma unroll
+        for (int m = 0; m < NOUT / 2; ++m) {
+            acc[2 * m] = a2[m].x;
+            acc[2 * m + 1] = a2[m].y;
+        }
+    } else {
+        static_for<W>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            static_for<NOUT>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
+                if constexpr (tap_on<KIND>(t)) acc[k] = fma(f[k & 1][t], win[j + D], acc[k]);
+            });
+        });
+    }
 }
 
 // Row pass over a plane in shared memory:
@@ -121,7 +164,8 @@ __device__ __forceinline__ void fir(const T (&win)[NW], const T (&f)[2][32], T (
 // (the 1D filter of Eq. 1dconvtrans along the row, periodic)
 template <typename T, int KIND, int RR>
 __device__ __forceinline__ void row_pass_r(const T* __restrict__ src, T* __restrict__ dst,
-                                           int nrows, int ncols, int RS, const T (&f)[2][32]) {
+                                           int nrows, int ncols, int RS, const T (&f)[2][32],
+                                           const float2 (&tp)[32]) {
     constexpr int VEC = 16 / (int)sizeof(T);
     constexpr int HL = KT<KIND>::HL;
     constexpr int HLR = (HL + VEC - 1) / VEC * VEC;   // window start, vector aligned
@@ -162,7 +206,7 @@ __device__ __forceinline__ void row_pass_r(const T* __restrict__ src, T* __restr
         T acc[RR];
         #pragma unroll
         for (int k = 0; k < RR; ++k) acc[k] = T(0);
-        fir<T, KIND, RR, D>(win, f, acc);
+        fir<T, KIND, RR, D>(win, f, tp, acc);
         T* o = dst + r * RS + c0;
         #pragma unroll
         for (int q = 0; q < RR / VEC; ++q) {
@@ -188,9 +232,10 @@ __device__ __forceinline__ void fill_rowoff(int* rowoff, int nrows, int RS) {
 // loop overhead per FMA of 8), else 8
 template <typename T, int KIND>
 __device__ __forceinline__ void row_pass(const T* __restrict__ src, T* __restrict__ dst,
-                                         int nrows, int ncols, int RS, const T (&f)[2][32]) {
-    if (ncols % 16 == 0) row_pass_r<T, KIND, 16>(src, dst, nrows, ncols, RS, f);
-    else row_pass_r<T, KIND, FZ_RR>(src, dst, nrows, ncols, RS, f);
+                                         int nrows, int ncols, int RS, const T (&f)[2][32],
+                                         const float2 (&tp)[32]) {
+    if (ncols % 16 == 0) row_pass_r<T, KIND, 16>(src, dst, nrows, ncols, RS, f, tp);
+    else row_pass_r<T, KIND, FZ_RR>(src, dst, nrows, ncols, RS, f, tp);
 }
 
 // One column-pass item: rows r0 .. r0 + FZ_RC - 1 of the 16-byte column
@@ -211,18 +256,47 @@ __device__ __forceinline__ void col_item(const T* __restrict__ src, const int* _
         for (int e = 0; e < VEC; ++e) acc[k][e] = T(0);
     const T* base = src + cv * VEC;
     const int* ro = rowoff + FZ_PADR + r0 - HL;
-    static_for<W>([&](auto jc) {
-        constexpr int j = decltype(jc)::value;
-        const Vec<T> v = ldv(base + ro[j]);
-        static_for<RC>([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
-            if constexpr (t >= KT<KIND>::SKIP && t < NT - KT<KIND>::SKIP) {
-                #pragma unroll
-                for (int e = 0; e < VEC; ++e) acc[k][e] = fma(f[k & 1][t], v.v[e], acc[k][e]);
-            }
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the vector's two column pairs take one packed FMA each
+        // (two FMAs per lane per instruction), which halves the FMA issue
+        float2 a2[RC][2];
+        #pragma unroll
+        for (int k = 0; k < RC; ++k) a2[k][0] = a2[k][1] = make_float2(0.f, 0.f);
+        static_for<W>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            const float4 q = *reinterpret_cast<const float4*>(base + ro[j]);
+            const float2 v01 = make_float2(q.x, q.y), v23 = make_float2(q.z, q.w);
+            static_for<RC>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
+                if constexpr (t >= KT<KIND>::SKIP && t < NT - KT<KIND>::SKIP) {
+                    const float2 ff = make_float2(f[k & 1][t], f[k & 1][t]);
+                    a2[k][0] = __ffma2_rn(ff, v01, a2[k][0]);
+                    a2[k][1] = __ffma2_rn(ff, v23, a2[k][1]);
+                }
+            });
         });
-    });
+        #pragma unroll
+        for (int k = 0; k < RC; ++k) {
+            acc[k][0] = a2[k][0].x;
+            acc[k][1] = a2[k][0].y;
+            acc[k][2] = a2[k][1].x;
+            acc[k][3] = a2[k][1].y;
+        }
+    } else {
+        static_for<W>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            const Vec<T> v = ldv(base + ro[j]);
+            static_for<RC>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                constexpr int t = j - k - ((k & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
+                if constexpr (t >= KT<KIND>::SKIP && t < NT - KT<KIND>::SKIP) {
+                    #pragma unroll
+                    for (int e = 0; e < VEC; ++e) acc[k][e] = fma(f[k & 1][t], v.v[e], acc[k][e]);
+                }
+            });
+        });
+    }
 }
 
 // ------------------------------------------------------------ plane kernels
@@ -271,7 +345,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
     if constexpr (PROG == FZ_SKM12) {
         Acc<T> e;
         // s = S_1 S_2 a -> X
-        row_pass<T, K_SYN>(X, Y, N2, N1, RS, p.tap[0]);
+        row_pass<T, K_SYN>(X, Y, N2, N1, RS, p.tap[0], p.tp[0]);
         __syncthreads();
         #pragma unroll 1
         for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
@@ -285,7 +359,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
         // v = T_1 s + T_2 s, Ekin part <s, v> (not for the density alone;
         // v stored for H psi only)
         if (S.part != nullptr) {
-        row_pass<T, K_KIN>(X, Y, N2, N1, RS, p.tap[1]);
+        row_pass<T, K_KIN>(X, Y, N2, N1, RS, p.tap[1], p.tp[1]);
         __syncthreads();
         #pragma unroll 1
         for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
@@ -311,7 +385,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
         __syncthreads();
         }
         // t = MF_1 MF_2 s
-        row_pass<T, K_MF>(X, Y, N2, N1, RS, p.tap[3]);
+        row_pass<T, K_MF>(X, Y, N2, N1, RS, p.tap[3], p.tp[3]);
         __syncthreads();
         #pragma unroll 1
         for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
@@ -328,7 +402,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
         }
     } else {
         // FZ_MFTA12: w = MFT_1 MFT_2 x + v, then w' = A_1 A_2 w
-        row_pass<T, K_MFT>(X, Y, N2, N1, RS, p.tap[0]);
+        row_pass<T, K_MFT>(X, Y, N2, N1, RS, p.tap[0], p.tp[0]);
         __syncthreads();
         // X is free: each thread fetches the v of its own outputs there,
         // overlapped with its column passes, and leaves w in its place
@@ -358,7 +432,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
             }
         }
         __syncthreads();
-        row_pass<T, K_ANA>(X, Y, N2, N1, RS, p.tap[1]);
+        row_pass<T, K_ANA>(X, Y, N2, N1, RS, p.tap[1], p.tp[1]);
         __syncthreads();
         #pragma unroll 1
         for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
@@ -657,7 +731,20 @@ cudaError_t fz_launch(const FzParams<T>& p, size_t smem, cudaStream_t st) {
     if (err != cudaSuccess) return err;
     if (p.njobs <= 0) return cudaSuccess;
     if (p.njobs > 0x7fffffffLL || smem > (size_t)FZ_SMEM_OPTIN) return cudaErrorInvalidConfiguration;
-    if constexpr (fz_is_plane<PROG>())
+    if constexpr (fz_is_plane<PROG>() && sizeof(T) == 4) {
+        // the row passes' tap pairs (the slots and filters of the row passes
+        // in fz_plane_kernel)
+        FzParams<T> q = p;
+        if constexpr (PROG == FZ_SKM12) {
+            fz_tap_pairs<K_SYN>(q.tap[0], q.tp[0]);
+            fz_tap_pairs<K_KIN>(q.tap[1], q.tp[1]);
+            fz_tap_pairs<K_MF>(q.tap[3], q.tp[3]);
+        } else {
+            fz_tap_pairs<K_MFT>(q.tap[0], q.tp[0]);
+            fz_tap_pairs<K_ANA>(q.tap[1], q.tp[1]);
+        }
+        fz_plane_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(FZ_PTHREADS), smem, st>>>(q);
+    } else if constexpr (fz_is_plane<PROG>())
         fz_plane_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(FZ_PTHREADS), smem, st>>>(p);
     else
         fz_col_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(fz_cthreads<PROG>()), smem, st>>>(p);

@@ -140,6 +140,7 @@ struct FzSeg {
 template <typename T>
 struct FzParams {
     T tap[4][2][32];      // the program's filters, per output parity (see fused_kernel.cu)
+    float2 tp[4][32];     // FP32 row passes: tap pairs of outputs 2m, 2m + 1 (fused_kernel.cu)
     long long njobs;
     int nseg;
     FzSeg<T> seg[MAXSEG];
