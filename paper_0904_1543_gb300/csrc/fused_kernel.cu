@@ -100,24 +100,6 @@ __device__ __forceinline__ double fz_block_sum(double v, double* red) {
     return t;
 }
 
-// the taps of a row-pass filter that apply (the kinetic a_{+-14} do not)
-template <int KIND>
-__host__ __device__ constexpr bool tap_on(int t) {
-    return t >= KT<KIND>::SKIP && t < KT<KIND>::NT - KT<KIND>::SKIP;
-}
-
-// Tap pairs of the packed FP32 row pass: window element j feeds outputs
-// 2m and 2m + 1 with taps t0 = d - off0 (even filter) and t1 = d - 1 - off1
-// (odd filter), d = j - 2m; a tap that does not apply is 0.
-template <int KIND>
-void fz_tap_pairs(const float (&f)[2][32], float2 (&tp)[32]) {
-    for (int d = 0; d < 32; ++d) {
-        const int t0 = d - KT<KIND>::OFF0, t1 = d - 1 - KT<KIND>::OFF1;
-        tp[d].x = tap_on<KIND>(t0) ? f[0][t0] : 0.f;
-        tp[d].y = tap_on<KIND>(t1) ? f[1][t1] : 0.f;
-    }
-}
-
 // acc[k] += f[k & 1][t] win[j + D] for output k of a chunk whose window
 // element j is input position (first output - HL + j).  FP32: outputs 2m,
 // 2m + 1 take one packed FMA per window element, the element broadcast and
@@ -137,8 +119,7 @@ __device__ __forceinline__ void fir(const T (&win)[NW], const T (&f)[2][32],
             const float2 ww = make_float2(win[j + D], win[j + D]);
             static_for<NOUT / 2>([&](auto mc) {
                 constexpr int d = j - 2 * decltype(mc)::value;
-                constexpr int t0 = d - KT<KIND>::OFF0, t1 = d - 1 - KT<KIND>::OFF1;
-                if constexpr (d >= 0 && d < 32 && (tap_on<KIND>(t0) || tap_on<KIND>(t1)))
+                if constexpr (pair_on<KIND>(d))
                     a2[decltype(mc)::value] = __ffma2_rn(tp[d], ww, a2[decltype(mc)::value]);
             });
         });
@@ -736,12 +717,12 @@ cudaError_t fz_launch(const FzParams<T>& p, size_t smem, cudaStream_t st) {
         // in fz_plane_kernel)
         FzParams<T> q = p;
         if constexpr (PROG == FZ_SKM12) {
-            fz_tap_pairs<K_SYN>(q.tap[0], q.tp[0]);
-            fz_tap_pairs<K_KIN>(q.tap[1], q.tp[1]);
-            fz_tap_pairs<K_MF>(q.tap[3], q.tp[3]);
+            tap_pairs<K_SYN>(q.tap[0], q.tp[0]);
+            tap_pairs<K_KIN>(q.tap[1], q.tp[1]);
+            tap_pairs<K_MF>(q.tap[3], q.tp[3]);
         } else {
-            fz_tap_pairs<K_MFT>(q.tap[0], q.tp[0]);
-            fz_tap_pairs<K_ANA>(q.tap[1], q.tp[1]);
+            tap_pairs<K_MFT>(q.tap[0], q.tp[0]);
+            tap_pairs<K_ANA>(q.tap[1], q.tp[1]);
         }
         fz_plane_kernel<T, PROG><<<dim3((unsigned)p.njobs), dim3(FZ_PTHREADS), smem, st>>>(q);
     } else if constexpr (fz_is_plane<PROG>())

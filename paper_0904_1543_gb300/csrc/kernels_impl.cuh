@@ -43,7 +43,13 @@ static cudaError_t launch_one(const PassParams<T>& p, long long nunits, size_t s
     long long grid = persistent ? (long long)occ * nsm : nunits;
     if (grid > nunits) grid = nunits;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    pass_kernel<T, KIND, MODE, R><<<dim3((unsigned)grid), dim3(NTHREADS), smem, st>>>(p);
+    if constexpr (sizeof(T) == 4) {
+        PassParams<T> q = p;
+        tap_pairs<KIND>(q.f, q.tp);
+        pass_kernel<T, KIND, MODE, R><<<dim3((unsigned)grid), dim3(NTHREADS), smem, st>>>(q);
+    } else {
+        pass_kernel<T, KIND, MODE, R><<<dim3((unsigned)grid), dim3(NTHREADS), smem, st>>>(p);
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -37,6 +37,31 @@ template <> struct KT<K_KIN> { static constexpr int NT = 29, OFF0 = 0, OFF1 = 0,
 template <> struct KT<K_SYN> { static constexpr int NT = 16, OFF0 = 0, OFF1 = 1, EXTRA = 1, HL = 8, SKIP = 0; };
 template <> struct KT<K_ANA> { static constexpr int NT = 16, OFF0 = 1, OFF1 = 0, EXTRA = 1, HL = 8, SKIP = 0; };
 
+// the taps of a filter that apply (the kinetic a_{+-14} do not)
+template <int KIND>
+__host__ __device__ constexpr bool tap_on(int t) {
+    return t >= KT<KIND>::SKIP && t < KT<KIND>::NT - KT<KIND>::SKIP;
+}
+
+// Tap pairs of the packed FP32 convolutions: input (window element) j feeds
+// outputs 2m and 2m + 1 of a chunk with taps t0 = d - off0 (even filter) and
+// t1 = d - 1 - off1 (odd filter), d = j - 2m; a tap that does not apply is 0.
+// One fma.rn.f32x2 then updates both outputs (two FMAs per lane per
+// instruction), in the same order of taps as the scalar form.
+template <int KIND>
+void tap_pairs(const float (&f)[2][32], float2 (&tp)[32]) {
+    for (int d = 0; d < 32; ++d) {
+        const int t0 = d - KT<KIND>::OFF0, t1 = d - 1 - KT<KIND>::OFF1;
+        tp[d].x = tap_on<KIND>(t0) ? f[0][t0] : 0.f;
+        tp[d].y = tap_on<KIND>(t1) ? f[1][t1] : 0.f;
+    }
+}
+template <int KIND>
+__host__ __device__ constexpr bool pair_on(int d) {
+    return d >= 0 && d < 32 &&
+           (tap_on<KIND>(d - KT<KIND>::OFF0) || tap_on<KIND>(d - 1 - KT<KIND>::OFF1));
+}
+
 // Row slot of input position 0: the left halo, rounded up to a 16-byte
 // boundary for FP32 so that the line's interior is staged with 16-byte
 // copies; the window of a chunk then starts D = row_hl - HL words later.
@@ -166,13 +191,22 @@ __device__ __forceinline__ void conv_chunk(const T* __restrict__ srow,
             win[4 * q + 2] = v.z;
             win[4 * q + 3] = v.w;
         }
+        // outputs 2m, 2m + 1: one packed FMA per window element
+        static_assert(R % 2 == 0, "output pairs");
+        float2 a2[R / 2];
+        #pragma unroll
+        for (int m = 0; m < R / 2; ++m) a2[m] = make_float2(acc[2 * m], acc[2 * m + 1]);
         #pragma unroll
         for (int j = 0; j < W; ++j) {
+            const float2 ww = make_float2(win[j + D], win[j + D]);
             #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int t = j - r - ((r & 1) ? KT<KIND>::OFF1 : KT<KIND>::OFF0);
-                if (t >= KT<KIND>::SKIP && t < NT - KT<KIND>::SKIP) acc[r] = fmaf(p.f[r & 1][t], win[j + D], acc[r]);
-            }
+            for (int m = 0; m < R / 2; ++m)
+                if (pair_on<KIND>(j - 2 * m)) a2[m] = __ffma2_rn(p.tp[j - 2 * m], ww, a2[m]);
+        }
+        #pragma unroll
+        for (int m = 0; m < R / 2; ++m) {
+            acc[2 * m] = a2[m].x;
+            acc[2 * m + 1] = a2[m].y;
         }
         return;
     }

@@ -84,6 +84,7 @@ struct Seg {
 template <typename T>
 struct PassParams {
     T f[2][32];           // taps per output parity (single-parity kinds: both equal)
+    float2 tp[32];        // FP32: tap pairs of outputs 2m, 2m + 1 (pass_kernel.cuh)
     long long nunits;     // work units over all segments
     int bufelems;         // elements of one staging buffer (two are allocated)
     int hl;               // left halo
