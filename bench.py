@@ -622,6 +622,10 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     cells = [W.Grid(s) for s in SIZES]
     f32 = args.prec == "f32"     # FP32 form of the same workload (profiling)
     emu = args.prec == "f64emu"  # FP64-accurate tensor-core form (profiling)
+    if f32 or emu:
+        WL["workload"] = WL["workload"].replace(
+            "batched FP64", "batched FP32 convolutions (compensated/FP64 reductions)" if f32
+            else "batched FP64 by f16-digit tensor-core emulation")
     pcode = W.WVL_F32 if f32 else (W.WVL_F64_EMU if emu else W.WVL_F64)
     tdt = torch.float32 if f32 else torch.float64
     if f32:
@@ -792,9 +796,30 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         roofline["kernel"] = ("kinetic 1D pass, tensor-core emulation: FP64-equivalent rate "
                               "against the FP64 pipe's peak (the kernel itself is bound by "
                               "integer-pipe issue)")
+    chain_line = [ln for ln in plan.describe().splitlines() if ln.startswith("chain:")][0][7:]
+    if f32:
+        # FP32 form: the whole step against the slower of its HBM bytes and its
+        # FP32 FMAs (the chain's kernels do not split into one dominant kernel)
+        bpp = FUSED_BPP if chain_line.startswith("fused") else PASSES_BPP
+        s_step = ms / args.steps * 1e-3
+        gbs = bpp * pts / s_step / 1e9
+        tfs = 2 * FP32_FMA_PER_POINT * pts / s_step / 1e12
+        if bpp * pts / (HBM_GBS * 1e9) >= 2 * FP32_FMA_PER_POINT * pts / (FP32_PEAK_TFLOPS * 1e12):
+            roofline = {"bound": "hbm", "achieved": gbs, "peak": HBM_GBS, "unit": "GB/s",
+                        "frac": gbs / HBM_GBS, "traffic": None,
+                        "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"}
+        else:
+            roofline = {"bound": "alu", "achieved": tfs, "peak": FP32_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": tfs / FP32_PEAK_TFLOPS, "traffic": None,
+                        "peak_source": "FP32 FMA-chain probe on this GPU model"}
+        roofline["kernel"] = (f"whole FP32 step ({chain_line}): {bpp:.0f} B and "
+                              f"{FP32_FMA_PER_POINT:.0f} FMAs per orbital point")
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "metric": (METRIC.replace("(FP64,", "(FP32 convolutions,") if f32 else
+                   METRIC.replace("(FP64,", "(FP64 by f16-digit tensor-core emulation,") if emu
+                   else METRIC),
+        "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if f32 else ("f64 (f16-digit tensor-core emulation)" if emu else "f64"),
@@ -808,7 +833,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
         "roofline": roofline,
         "clocks": clk,
         "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
-        "chain": [ln for ln in plan.describe().splitlines() if ln.startswith("chain:")][0][7:],
+        "chain": chain_line,
     }
     if rank == 0 and world == 1 and not args.no_variants and args.prec == "f64":
         line["variants"] = measure_variants(args, W, torch, dev)
