@@ -494,13 +494,19 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         const int I1 = c0 + x;
         const long long cxy = (long long)(I2 >> 1) * S.n1 + (I1 >> 1);
         const long long nxy = (long long)S.n2 * S.n1;
+        // the thread's rows r0, r0 + RSTEP, ... share the parity of r0 (RSTEP
+        // is even), so mu is fixed and the source advances by RSTEP / 2 coarse
+        // planes per row: one pointer step per element
+        constexpr int RSTEP = NT / LTC;
+        static_assert(RSTEP % 2 == 0, "rows of one parity per thread");
+        const int r0 = threadIdx.x / LTC;
+        const int mu = (I1 & 1) + a2 + 4 * (r0 & 1);
+        const long long ci0 = (long long)(r0 >> 1) * nxy + cxy;
+        const T* src = (mu == 0) ? cc + ci0 : cf + ci0 * 7 + mu - 1;
+        const long long step = (mu == 0 ? 1 : 7) * (RSTEP / 2) * nxy;
         if (x < ncols)
             #pragma unroll 1
-            for (int r = threadIdx.x / LTC; r < N3; r += NT / LTC) {
-                const int mu = (I1 & 1) + a2 + 4 * (r & 1);
-                const long long ci = (long long)(r >> 1) * nxy + cxy;
-                cp_async(X + r * RS + x, (mu == 0) ? cc + ci : cf + ci * 7 + mu - 1);
-            }
+            for (int r = r0; r < N3; r += RSTEP, src += step) cp_async(X + r * RS + x, src);
         cp_commit();
         cp_wait<0>();
         __syncthreads();
