@@ -434,7 +434,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
 // (vectors past a partial last tile are idle).
 // CTAs per SM the register allocation must allow
 template <int PROG>
-__host__ __device__ constexpr int fz_cminb() { return PROG == FZ_SYN3 ? 4 : 3; }
+__host__ __device__ constexpr int fz_cminb() { return PROG == FZ_SYN3 || PROG == FZ_POT3 ? 4 : 3; }
 
 template <typename T, int PROG>
 __global__ void __launch_bounds__(fz_cthreads<PROG>(), fz_cminb<PROG>())
