@@ -794,8 +794,8 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
                 "peak_source": "nominal GB300 FP64 rate from the recipe table (not measured)"}
     if emu:
         roofline["kernel"] = ("kinetic 1D pass, tensor-core emulation: FP64-equivalent rate "
-                              "against the FP64 pipe's peak (the kernel itself is bound by "
-                              "integer-pipe issue)")
+                              "against the FP64 pipe's peak (the kernel itself is latency-bound "
+                              "around its tensor-core MMAs)")
     chain_line = [ln for ln in plan.describe().splitlines() if ln.startswith("chain:")][0][7:]
     if f32:
         # FP32 form: the whole step against the slower of its HBM bytes and its
