@@ -255,14 +255,8 @@ __device__ __forceinline__ void prefetch_epilogue(const Seg<double>& Sg, int o0,
 #pragma unroll
             for (int c = 0; c < NH; ++c)
                 if (o0 + c < n) pa[c] = Sg.aux[(long long)(o0 + c) * NL + a];
-        // the density so far: the caller's rho, or this group's partial
-        // after the group's first orbital
-        if (Sg.rho != nullptr && (Sg.rho_gstride == 0 || orb != grp * Sg.opg)) {
-            const double* rp = Sg.rho + (long long)grp * Sg.rho_gstride;
-#pragma unroll
-            for (int c = 0; c < NH; ++c)
-                if (o0 + c < n) pc[c] = rp[(long long)(o0 + c) * NL + a];
-        }
+        // the density so far is read in the epilogue: prefetched too, it
+        // would stay live across the MMAs beside V and spill
     }
 }
 
@@ -345,9 +339,14 @@ __device__ __forceinline__ double window_epilogue(const Seg<double>& Sg, uint32_
                     eacc = fma(y, val, eacc);
                 }
                 // the unit owns these density elements: one thread updates
-                // each, orbital after orbital, in a fixed order
-                if (Sg.rho != nullptr)
-                    Sg.rho[(long long)grp * Sg.rho_gstride + oidx] = fma(occ * val, val, pc[c]);
+                // each, orbital after orbital, in a fixed order; the density
+                // so far is the caller's rho, or this group's partial after
+                // the group's first orbital
+                if (Sg.rho != nullptr) {
+                    double* const rp = Sg.rho + (long long)grp * Sg.rho_gstride + oidx;
+                    const double prev = (Sg.rho_gstride == 0 || orb != grp * Sg.opg) ? *rp : 0.0;
+                    *rp = fma(occ * val, val, prev);
+                }
             }
         }
     }
