@@ -220,6 +220,7 @@ def _derive():
         return {
             "hD": hD, "gD": gD, "wD": wD, "aD": aD, "momD": mom,
             "k0": k0, "cands": [(c[0], c[3]) for c in cands],
+            "cand_h": [(c[0], [float(v) for v in c[1]]) for c in cands],
             "choice": pick[0],
         }
 
@@ -372,3 +373,9 @@ def candidates():
     the chosen one."""
     d = _derive()
     return d["cands"], d["choice"]
+
+
+def candidate_filters():
+    """[(root choice, h rounded to FP64 for j = -7..8)] for all 16 spectral
+    factors, in the order of candidates()."""
+    return [(c, np.array(hv)) for c, hv in _derive()["cand_h"]]

@@ -253,3 +253,34 @@ def test_golden_table_reproduced():
     assert int(tab["k0"][0]) == k0
     for name, arr in (("h", F.h()), ("g", F.g()), ("w", w), ("a", F.kinetic_a())):
         assert [float.fromhex(v) for v in tab[name]] == list(arr), name
+
+
+def _published_least_asymmetric():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "least_asymmetric_n8.txt")
+    return np.array([float(v) for v in open(path) if v.strip() and not v.startswith("#")])
+
+
+def test_h_is_the_published_least_asymmetric_filter():
+    """The family member the oracle picks (least asymmetric, N = 8) is the
+    one Daubechies tabulates (tests/golden/least_asymmetric_n8.txt, typed in
+    from the book).  Conventions: the oracle's h_j, j = -7..8, is the table
+    read backwards (a mirror image, which ties on the least-asymmetric
+    criterion, and a shift of the support).  The table's printed digits hold
+    to about 1e-12 (its own orthonormality residual is 1.7e-13), so the
+    match is asserted to 2e-12; every other spectral factor of the family is
+    more than 1e-2 away from the table in either orientation, so a wrong
+    phase criterion or a wrong root of any pair fails here."""
+    tab = _published_least_asymmetric()
+    assert tab.size == F.NTAP
+    assert abs(tab.sum() - math.sqrt(2.0)) < 1e-15
+    h = F.h()
+    assert np.max(np.abs(h - tab[::-1])) < 2e-12
+    _, choice = F.candidates()
+    mirror = tuple(1 - b for b in choice)
+    for c, hc in F.candidate_filters():
+        d = min(np.max(np.abs(hc - tab[::-1])), np.max(np.abs(hc - tab)))
+        if c in (choice, mirror):
+            assert d < 2e-12, c
+        else:
+            assert d > 1e-2, (c, d)
