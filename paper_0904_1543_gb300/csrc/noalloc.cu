@@ -8,7 +8,7 @@
 // of a fixed size, reserved on every GPU that loads the library until the
 // process exits, and calls no allocator at all.
 #include <cstdio>
-#include <mutex>
+#include <cstring>
 
 #include <cuda_runtime.h>
 
@@ -19,11 +19,9 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)WVL_NOALLOC_SCRATCH_BYTES;
 
 // In host code this name is only a host-side stand-in; the kernels get the
-// device address that cudaGetSymbolAddress returns for the current device.
+// device address that cudaGetSymbolAddress returns for the current device
+// and context.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
-
-std::mutex g_mu;
-void* g_addr[64] = {};   // device address of g_scratch, per device ordinal
 
 thread_local char g_msg[256];
 
@@ -39,7 +37,10 @@ extern "C" wvl_status wvl_hpsi_local_noalloc(const wvl_grid* grid, int prec, int
     if (norb == 0) return WVL_OK;
     size_t need = 0;
     wvl_status st = wvl_workspace_size(grid, prec, norb, &need);
-    if (st != WVL_OK) return st;
+    if (st != WVL_OK) {
+        std::snprintf(g_msg, sizeof g_msg, "wvl_hpsi_local_noalloc: %s", wvl_last_error());
+        return st;
+    }
     if (need > kScratchBytes) {
         std::snprintf(g_msg, sizeof g_msg,
                       "wvl_hpsi_local_noalloc: this grid and orbital count need %zu bytes of "
@@ -47,32 +48,24 @@ extern "C" wvl_status wvl_hpsi_local_noalloc(const wvl_grid* grid, int prec, int
                       need, kScratchBytes);
         return WVL_EUNSUPPORTED;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
-        std::snprintf(g_msg, sizeof g_msg, "wvl_hpsi_local_noalloc: cudaGetDevice: %s",
+    // The array's address belongs to the current device's context, so it is
+    // looked up on every call (a host-side table lookup once the module is
+    // loaded): a caller that switches devices, runs under its own driver
+    // context or resets the device always gets the address valid for the
+    // context it calls from.  The first lookup in a context loads the
+    // library's device code there.
+    void* scratch = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&scratch, g_scratch);
+    if (e != cudaSuccess || scratch == nullptr) {
+        std::snprintf(g_msg, sizeof g_msg, "wvl_hpsi_local_noalloc: cudaGetSymbolAddress: %s",
                       cudaGetErrorString(e));
         return WVL_ECUDA;
     }
-    void* scratch = nullptr;
-    {
-        // once per device, with that device current
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (g_addr[dev] == nullptr) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_scratch);
-            if (e != cudaSuccess || p == nullptr) {
-                std::snprintf(g_msg, sizeof g_msg,
-                              "wvl_hpsi_local_noalloc: cudaGetSymbolAddress: %s",
-                              cudaGetErrorString(e));
-                return WVL_ECUDA;
-            }
-            g_addr[dev] = p;
-        }
-        scratch = g_addr[dev];
-    }
     // Nothing in the scratch has to start at zero: every word the chain reads
     // is first written by the same call.
-    return wvl_hpsi_local(grid, prec, norb, psi_c, V, occ, hpsi_c, rho, ekin, epot, scratch,
-                          kScratchBytes, stream);
+    st = wvl_hpsi_local(grid, prec, norb, psi_c, V, occ, hpsi_c, rho, ekin, epot, scratch,
+                        kScratchBytes, stream);
+    if (st != WVL_OK)
+        std::snprintf(g_msg, sizeof g_msg, "wvl_hpsi_local_noalloc: %s", wvl_last_error());
+    return st;
 }
