@@ -103,6 +103,16 @@ wvl_status wvl_wait_timeouts(unsigned* count);
  * No counterpart in the paper.  WVL_EINVAL unless 0 < ms <= 10000. */
 wvl_status wvl_selftest_timeout(double ms, void* stream);
 
+/* Arithmetic-pipe peak of the current device, measured: independent FMA
+ * chains (packed pairs in FP32) on every SM; of the variants with 4, 8 or 16
+ * chains per thread and 1, 2, 4 or 8 CTAs of 256 threads per SM, the fastest
+ * is run for about `seconds` (0 < seconds <= 10), best of three launches
+ * timed with CUDA events on `stream`.  *tflops = 2 x FMAs / s / 1e12 for prec WVL_F64 or
+ * WVL_F32; *ms (nullable) = that launch's duration.  Synchronises the
+ * stream.  The denominator of the library's FP64 and FP32 rooflines; no
+ * counterpart in the paper. */
+wvl_status wvl_fma_peak(int prec, double seconds, double* tflops, double* ms, void* stream);
+
 /*
  * Filters derived by the library (host computation, no GPU needed), FP64.
  *  h[16], g[16]: h_j, g_j for j = -7..8 (Eq. refinement, g_j = (-1)^j h_{1-j});
@@ -174,10 +184,13 @@ wvl_status wvl_hpsi_local(const wvl_grid* grid, int prec, int norb,
  * The scratch is one file-scope device array of WVL_NOALLOC_SCRATCH_BYTES,
  * held on every GPU that loads the library until the process exits; no
  * allocator is called.  Calls whose wvl_workspace_size() exceeds it return
- * WVL_EUNSUPPORTED (detail in wvl_noalloc_last_error()).
- * The first call on a device looks up the array's device address on that
- * device (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call uses the same array and leaves its contents behind
+ * WVL_EUNSUPPORTED.  On any failure wvl_noalloc_last_error() gives the
+ * detail (also that of errors raised by the inner wvl_hpsi_local call).
+ * Every call looks up the array's device address in the calling thread's
+ * current device and context (cudaGetSymbolAddress), so switching devices,
+ * driver-API contexts or a cudaDeviceReset between calls is safe; the first
+ * call in a context loads the library's device code there, so make that
+ * first call before any stream capture.  Every call uses the same array and leaves its contents behind
  * (nothing in it needs to start at zero); calls that overlap on the GPU --
  * on different streams or from several host threads -- race on it.
  * Arguments, layouts and results are those of wvl_hpsi_local. */
@@ -194,6 +207,32 @@ wvl_status wvl_energy(const wvl_grid* grid, int prec, int norb,
                       const void* psi_c, const void* V, const double* occ,
                       double* rho, double* ekin, double* epot,
                       void* ws, size_t ws_bytes, void* stream);
+
+/* The differentiable local energy E_loc(psi, V) = sum_o occ_o (Ekin_o + Epot_o)
+ * (Sec. "Full local hamiltonian"; Sec. "Local density calculation" for rho).
+ * wvl_eloc is its forward: wvl_energy, then the total written to *eloc
+ * (device double, one fixed-order reduction on the device).  ekin, epot:
+ * device double[norb], written; rho nullable, accumulated.
+ * wvl_eloc_backward is its adjoint for an upstream gradient *gbar (device
+ * double):
+ *   dpsi_c[o] = 2 occ_o gbar (H psi)_o   -- E_loc is quadratic in psi with the
+ *       symmetric operator H = A^T (M^T V M + K) A; the whole chain runs again
+ *       (real-space orbitals recomputed, not stored) and its last pass writes
+ *       the scaled result in psi's precision and layout;
+ *   dV = gbar rho                         -- E_loc is linear in V with
+ *       coefficient rho (grid units); rho is the forward's density (device
+ *       double), dV is written in V's precision, [N3][N2][N1].
+ * Either output may be NULL (not computed); rho is required when dV is given.
+ * Workspace: wvl_workspace_size(). */
+wvl_status wvl_eloc(const wvl_grid* grid, int prec, int norb,
+                    const void* psi_c, const void* V, const double* occ,
+                    double* rho, double* ekin, double* epot, double* eloc,
+                    void* ws, size_t ws_bytes, void* stream);
+wvl_status wvl_eloc_backward(const wvl_grid* grid, int prec, int norb,
+                             const void* psi_c, const void* V, const double* occ,
+                             const double* rho, const double* gbar,
+                             void* dpsi_c, void* dV,
+                             void* ws, size_t ws_bytes, void* stream);
 
 /* Preconditioning step (paper Eq. precon, Sec. "Kinetic convolution" with
  * K_0 = -eps s): for each orbital o, ncg iterations of the preconditioned

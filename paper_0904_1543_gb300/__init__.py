@@ -23,7 +23,7 @@ from . import _build
 
 __all__ = [
     "WvlError", "Grid", "lib", "filters", "workspace_size", "synthesis", "analysis",
-    "magicfilter", "magicfilter_T", "kinetic", "density", "hpsi_local", "energy",
+    "magicfilter", "magicfilter_T", "kinetic", "density", "hpsi_local", "energy", "eloc",
     "Plan", "ELoc", "device_count", "wait_timeouts", "WVL_F64", "WVL_F32", "WVL_F64_EMU",
 ]
 
@@ -80,6 +80,7 @@ def _declare(L):
         "wvl_wait_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
         "wvl_selftest_timeout": (ctypes.c_int, [ctypes.c_double, _vp]),
         "wvl_filters": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "wvl_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]),
         "wvl_workspace_size": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_sz)]),
         "wvl_synthesis": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
         "wvl_analysis": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
@@ -91,6 +92,10 @@ def _declare(L):
                                           _vp, _vp, _vp, _sz, _vp]),
         "wvl_energy": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
                                       _vp, _sz, _vp]),
+        "wvl_eloc": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
+                                    _vp, _vp, _sz, _vp]),
+        "wvl_eloc_backward": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                             _vp, _vp, _vp, _vp, _sz, _vp]),
         "wvl_plan_create": (ctypes.c_int, [G, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_uint, ctypes.POINTER(_vp)]),
         "wvl_plan_destroy": (ctypes.c_int, [_vp]),
@@ -157,6 +162,16 @@ def wait_timeouts():
     if st not in (0, 4):
         _check(st)
     return c.value
+
+
+def fma_peak(prec=WVL_F64, seconds=0.2, device=None):
+    """Measured FMA-chain rate of the device's FP64 (prec WVL_F64) or FP32
+    (WVL_F32) pipe in TFLOP/s, and the timed launch's milliseconds."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().wvl_fma_peak(int(prec), float(seconds), ctypes.byref(tf), ctypes.byref(ms),
+                              _stream(dev)))
+    return tf.value, ms.value
 
 
 def filters():
@@ -320,6 +335,23 @@ def energy(psi_c, V, occ, grid: Grid, rho=None, emu=False):
     return ek, ep
 
 
+def eloc(psi_c, V, occ, grid: Grid, rho=None, emu=False):
+    """E_loc = sum_o occ_o (Ekin_o + Epot_o) as a 0-d float64 device tensor,
+    with the per-orbital (ekin, epot); rho += density if given."""
+    norb = _norb(psi_c, grid.ncoef)
+    dev = psi_c.device
+    ek = torch.empty(norb, dtype=torch.float64, device=dev)
+    ep = torch.empty(norb, dtype=torch.float64, device=dev)
+    e = torch.empty((), dtype=torch.float64, device=dev)
+    for t, nm in ((psi_c, "psi_c"), (V, "V"), (occ, "occ")):
+        _dev(t, nm)
+    if rho is not None:
+        _dev(rho, "rho")
+    _run(lib().wvl_eloc, grid, _prec(psi_c, emu), norb, dev, psi_c.data_ptr(), V.data_ptr(),
+         occ.data_ptr(), _p(rho), ek.data_ptr(), ep.data_ptr(), e.data_ptr())
+    return e, ek, ep
+
+
 class Plan:
     """Batched local Hamiltonian for orbitals on cells of different sizes
     (one enqueue of every pass over all cells; optional graph replay and
@@ -405,30 +437,45 @@ class Plan:
 
 class ELoc(torch.autograd.Function):
     """E_loc(psi, V) = sum_o occ_o (Ekin_o + Epot_o) for the orbitals of one
-    cell.  Forward runs steps 1), 2), 3a), 3b) and 4) only (energies, no
-    H psi); backward recomputes the real-space orbitals instead of storing
-    them and applies the full chain: dE/dpsi_o = 2 occ_o H psi_o (the
-    transposed filters are the adjoint kernels), dE/dV = rho."""
+    cell.  Forward: wvl_eloc (steps 1), 2), 3a), 3b) and 4) only -- energies,
+    density and their total on the device, no H psi).  Backward:
+    wvl_eloc_backward, whose adjoint kernels recompute the real-space orbitals
+    instead of storing them and write dE/dpsi_o = 2 occ_o g H psi_o from the
+    last pass of the chain, and dE/dV = g rho.  This class only marshals
+    tensors; the arithmetic is in the library."""
 
     @staticmethod
-    def forward(ctx, psi, V, occ, grid):
-        rho = torch.zeros(grid.fine, dtype=torch.float64, device=psi.device)
-        ek, ep = energy(psi.detach(), V.detach(), occ, grid, rho=rho)
+    def forward(ctx, psi, V, occ, grid, emu=False):
+        psi_d, V_d = psi.detach(), V.detach()
+        norb = _norb(psi_d, grid.ncoef)
+        dev = psi.device
+        rho = torch.zeros(grid.fine, dtype=torch.float64, device=dev)
+        ek = torch.empty(norb, dtype=torch.float64, device=dev)
+        ep = torch.empty(norb, dtype=torch.float64, device=dev)
+        e = torch.empty((), dtype=torch.float64, device=dev)
+        for t, nm in ((psi_d, "psi"), (V_d, "V"), (occ, "occ")):
+            _dev(t, nm)
+        _run(lib().wvl_eloc, grid, _prec(psi_d, emu), norb, dev, psi_d.data_ptr(),
+             V_d.data_ptr(), occ.data_ptr(), rho.data_ptr(), ek.data_ptr(), ep.data_ptr(),
+             e.data_ptr())
         ctx.save_for_backward(psi, V, occ, rho)
         ctx.grid = grid
-        return (occ * (ek + ep)).sum()
+        ctx.emu = emu
+        return e
 
     @staticmethod
     def backward(ctx, g):
         psi, V, occ, rho = ctx.saved_tensors
-        gpsi = gV = None
-        if ctx.needs_input_grad[0]:
-            hp, _, _ = hpsi_local(psi.detach(), V.detach(), occ, ctx.grid)
-            scale = (2.0 * occ * g).to(hp.dtype).view(-1, *([1] * (hp.dim() - 1)))
-            gpsi = hp * scale
-        if ctx.needs_input_grad[1]:
-            gV = (rho * g).to(V.dtype)
-        return gpsi, gV, None, None
+        psi_d, V_d = psi.detach(), V.detach()
+        gb = g.detach().to(device=psi.device, dtype=torch.float64).reshape(1).contiguous()
+        gpsi = torch.empty_like(psi_d) if ctx.needs_input_grad[0] else None
+        gV = torch.empty_like(V_d) if ctx.needs_input_grad[1] else None
+        if gpsi is not None or gV is not None:
+            norb = _norb(psi_d, ctx.grid.ncoef)
+            _run(lib().wvl_eloc_backward, ctx.grid, _prec(psi_d, ctx.emu), norb, psi.device,
+                 psi_d.data_ptr(), V_d.data_ptr(), occ.data_ptr(), rho.data_ptr(),
+                 gb.data_ptr(), _p(gpsi), _p(gV))
+        return gpsi, gV, None, None, None
 
 
 def precondition(g, eps, grid: Grid, ncg=5, x=None, want_residual=True, emu=False):

@@ -365,6 +365,8 @@ struct CellRun {
     double* kpart;
     double* rpart;
     const double* eps = nullptr;   // OP_HELM: per-orbital shift
+    const double* gscale = nullptr;// OP_HPSI: scale H psi of orbital o by 2 occ[o] gscale[0]
+                                   //   in the last pass (the adjoint of E_loc)
     const int* mapc = nullptr;     // localisation region (nullptr: full grid)
     const int* mapf = nullptr;
     long long clen = 0;            // region: compressed length per orbital
@@ -632,7 +634,12 @@ static std::vector<PassCall<T>> build_calls(int op, std::vector<CellRun<T>>& run
         });
         add(K_ANA, M_PLAIN, 1, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), B(r, B_)); });
         add(K_ANA, M_PLAIN, 2, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, B_), B(r, A_)); });
-        add(K_ANA, M_COMP, 3, ST_ANA, [&](CellRun<T>& r) { return seg_for<T>(r, B(r, A_), r.out); });
+        add(K_ANA, M_COMP, 3, ST_ANA, [&](CellRun<T>& r) {
+            SegDesc<T> d = seg_for<T>(r, B(r, A_), r.out);
+            d.s.occ = r.occ;
+            d.s.gscale = r.gscale;
+            return d;
+        });
         break;
     }
     return calls;
@@ -858,6 +865,7 @@ static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, c
                 case FZ_TA3:
                     s.in = hpsi ? D : nullptr; s.in2 = A; s.out = hpsi ? r.out : nullptr;
                     s.part = r.kpart; s.ptiles = ktiles; s.poff = s.N3;
+                    s.occ = r.occ; s.gscale = hpsi ? r.gscale : nullptr;
                     break;
                 }
                 s.blk0 = jobs;
@@ -988,7 +996,8 @@ template <typename T>
 static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void* in,
                               void* out, const void* V, const double* occ, double* rho,
                               double* ekin, double* epot, void* ws, size_t ws_bytes,
-                              void* stream, const wvl_region* reg, bool emu) {
+                              void* stream, const wvl_region* reg, bool emu,
+                              const double* gscale = nullptr) {
     CellRun<T> r;
     grid_dims(grid, r.n, r.Nf, r.hg, r.P);
     r.norb = norb;
@@ -1006,6 +1015,7 @@ static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void
     r.occ = occ;
     r.ekin = ekin;
     r.epot = epot;
+    r.gscale = gscale;
     const size_t need = run_ws_bytes(r.Nf, norb, sizeof(T));
     if (!ws) return fail(WVL_EINVAL, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(WVL_EINVAL, "workspace is not 256-byte aligned");
@@ -1189,13 +1199,14 @@ static wvl_status dispatch_single(int op, const wvl_grid* grid, int prec, int no
                                   const void* in, void* out, const void* V,
                                   const double* occ, double* rho, double* ekin,
                                   double* epot, void* ws, size_t ws_bytes, void* stream,
-                                  const wvl_region* reg = nullptr) {
+                                  const wvl_region* reg = nullptr,
+                                  const double* gscale = nullptr) {
     g_err[0] = 0;
     if (prec != WVL_F32)
         return single_cell<double>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
-                                   ws_bytes, stream, reg, prec == WVL_F64_EMU);
+                                   ws_bytes, stream, reg, prec == WVL_F64_EMU, gscale);
     return single_cell<float>(op, grid, norb, in, out, V, occ, rho, ekin, epot, ws,
-                              ws_bytes, stream, reg, false);
+                              ws_bytes, stream, reg, false, gscale);
 }
 
 static wvl_status check_region(const wvl_grid* grid, const wvl_region* reg) {
@@ -1408,6 +1419,61 @@ wvl_status wvl_energy(const wvl_grid* grid, int prec, int norb, const void* psi_
     WVL_TRY(check_ptr(epot, "epot", true));
     return dispatch_single(OP_ENERGY, grid, prec, norb, psi_c, nullptr, V, occ, rho, ekin,
                            epot, ws, ws_bytes, stream);
+}
+
+wvl_status wvl_eloc(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                    const void* V, const double* occ, double* rho, double* ekin, double* epot,
+                    double* eloc, void* ws, size_t ws_bytes, void* stream) {
+    g_err[0] = 0;
+    WVL_TRY(check_grid(grid));
+    WVL_TRY(check_prec(prec));
+    if (norb < 0) return fail(WVL_EINVAL, "norb < 0");
+    WVL_TRY(check_ptr(eloc, "eloc", true));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (norb > 0) {
+        WVL_TRY(check_ptr(psi_c, "psi_c", true));
+        WVL_TRY(check_ptr(V, "V", true));
+        WVL_TRY(check_ptr(occ, "occ", true));
+        WVL_TRY(check_ptr(rho, "rho", false));
+        WVL_TRY(check_ptr(ekin, "ekin", true));
+        WVL_TRY(check_ptr(epot, "epot", true));
+        WVL_TRY(dispatch_single(OP_ENERGY, grid, prec, norb, psi_c, nullptr, V, occ, rho, ekin,
+                                epot, ws, ws_bytes, stream));
+    }
+    cudaError_t e = launch_eloc_total(occ, ekin, epot, norb, eloc, st);
+    return e == cudaSuccess ? WVL_OK : cuda_fail(e, "E_loc reduction");
+}
+
+wvl_status wvl_eloc_backward(const wvl_grid* grid, int prec, int norb, const void* psi_c,
+                             const void* V, const double* occ, const double* rho,
+                             const double* gbar, void* dpsi_c, void* dV, void* ws,
+                             size_t ws_bytes, void* stream) {
+    g_err[0] = 0;
+    WVL_TRY(check_grid(grid));
+    WVL_TRY(check_prec(prec));
+    if (norb < 0) return fail(WVL_EINVAL, "norb < 0");
+    WVL_TRY(check_ptr(gbar, "gbar", true));
+    WVL_TRY(check_ptr(dpsi_c, "dpsi_c", false));
+    WVL_TRY(check_ptr(dV, "dV", false));
+    if (dV) WVL_TRY(check_ptr(rho, "rho (needed for dV)", true));
+    if (dpsi_c && norb > 0) {
+        WVL_TRY(check_ptr(psi_c, "psi_c", true));
+        WVL_TRY(check_ptr(V, "V", true));
+        WVL_TRY(check_ptr(occ, "occ", true));
+        // the whole chain again (real-space psi recomputed, not stored), its
+        // last pass writing 2 occ gbar H psi; no density, no energies
+        WVL_TRY(dispatch_single(OP_HPSI, grid, prec, norb, psi_c, dpsi_c, V, occ, nullptr,
+                                nullptr, nullptr, ws, ws_bytes, stream, nullptr, gbar));
+    }
+    if (dV) {
+        const long long P = 8LL * grid->n1 * grid->n2 * grid->n3;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        cudaError_t e = prec == WVL_F32
+                            ? launch_scale_density<float>(rho, gbar, P, static_cast<float*>(dV), st)
+                            : launch_scale_density<double>(rho, gbar, P, static_cast<double*>(dV), st);
+        if (e != cudaSuccess) return cuda_fail(e, "dE/dV");
+    }
+    return WVL_OK;
 }
 
 wvl_status wvl_precondition_workspace_size(const wvl_grid* grid, int prec, int norb,

@@ -279,6 +279,9 @@ __device__ __forceinline__ double window_epilogue(const Seg<double>& Sg, uint32_
     const long long obase = (long long)orb * Sg.P;
     double occ = 1.0;
     if (MODE == M_POT) occ = Sg.occ ? Sg.occ[orb] : 1.0;
+    // M_COMP for the adjoint of E_loc: H psi scaled by 2 occ g
+    double osc = 1.0;
+    if (MODE == M_COMP && Sg.gscale != nullptr) osc = 2.0 * Sg.occ[orb] * Sg.gscale[0];
     double eacc = 0.0;
 #pragma unroll
     for (int c8 = 0; c8 < NH / 8; ++c8) {
@@ -310,14 +313,15 @@ __device__ __forceinline__ double window_epilogue(const Seg<double>& Sg, uint32_
                 const int mu = (X1 & 1) + 2 * (X2 & 1) + 4 * (I & 1);
                 const long long ci = ((long long)(I >> 1) * Sg.n2 + (X2 >> 1)) * Sg.n1 + (X1 >> 1);
                 double* cc0 = Sg.out + (long long)orb * Sg.clen;
+                const double sv = Sg.gscale != nullptr ? val * osc : val;
                 if (Sg.mapc == nullptr && Sg.bx1 == 0) {
-                    if (mu == 0) cc0[ci] = val;
-                    else cc0[Sg.ncoarse + ci * 7 + mu - 1] = val;
+                    if (mu == 0) cc0[ci] = sv;
+                    else cc0[Sg.ncoarse + ci * 7 + mu - 1] = sv;
                 } else {
                     const int k = stored_index(Sg, ci, X1 >> 1, X2 >> 1, I >> 1, mu);
                     if (k >= 0) {
-                        if (mu == 0) cc0[k] = val;
-                        else cc0[Sg.ncoarse + (long long)k * 7 + mu - 1] = val;
+                        if (mu == 0) cc0[k] = sv;
+                        else cc0[Sg.ncoarse + (long long)k * 7 + mu - 1] = sv;
                     }
                 }
             } else if (KM) {

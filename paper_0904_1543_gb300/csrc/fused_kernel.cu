@@ -577,6 +577,8 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             T* const cc = S.out + (long long)u * S.P;
             T* const cf = cc + S.P / 8;
             const int nci = ncv * VEC / 2;                 // coarse points of the tile row
+            // the adjoint of E_loc: H psi scaled by 2 occ g
+            const T osc = S.gscale != nullptr ? T(2.0 * S.occ[u] * S.gscale[0]) : T(1);
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             const long long kb = (long long)(I2 >> 1) * S.n1 + (c0 >> 1);
             const long long nxy = (long long)S.n2 * S.n1;
@@ -593,10 +595,10 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             for (int i3 = warp; i3 < N3 / 2; i3 += NT / 32) {
                 const long long k0 = (long long)i3 * nxy + kb;
                 const T* const y0 = Y + (2 * i3) * RS;    // a3 = 0, a2 = 0
-                if (lane < nci) cc[k0 + lane] = y0[2 * lane];
+                if (lane < nci) cc[k0 + lane] = y0[2 * lane] * osc;
                 T* const fr = cf + 7 * k0;
                 #pragma unroll 1
-                for (int pos = lane; pos < 7 * nci; pos += 32) fr[pos] = y0[roff[pos]];
+                for (int pos = lane; pos < 7 * nci; pos += 32) fr[pos] = y0[roff[pos]] * osc;
             }
         }
         }

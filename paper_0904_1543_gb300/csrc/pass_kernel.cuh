@@ -393,6 +393,9 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
         Acc<T> e;   // energy partial of this orbital
         double occ = 0.0;
         if (MODE == M_POT) occ = S.occ ? S.occ[orb] : 1.0;
+        // M_COMP for the adjoint of E_loc: H psi scaled by 2 occ g
+        T osc = T(1);
+        if (MODE == M_COMP && S.gscale != nullptr) osc = T(2.0 * S.occ[orb] * S.gscale[0]);
         // FP32 potential pass: the first orbital of the unit starts the sums
         const bool first_orb = RSM && orb == (int)((cur.unit - S.blk0) / S.tiles) * S.opg;
 
@@ -458,15 +461,16 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                         const long long ci =
                             ((long long)(I >> 1) * S.n2 + (X2 >> 1)) * S.n1 + (X1 >> 1);
                         T* cc0 = S.out + (long long)orb * S.clen;
+                        const T val = S.gscale != nullptr ? acc[r] * osc : acc[r];
                         if (S.mapc == nullptr && S.bx1 == 0) {
-                            if (mu == 0) cc0[ci] = acc[r];
-                            else cc0[S.ncoarse + ci * 7 + mu - 1] = acc[r];
+                            if (mu == 0) cc0[ci] = val;
+                            else cc0[S.ncoarse + ci * 7 + mu - 1] = val;
                         } else {
                             // region or box: only the stored coefficients
                             const int k = stored_index(S, ci, X1 >> 1, X2 >> 1, I >> 1, mu);
                             if (k >= 0) {
-                                if (mu == 0) cc0[k] = acc[r];
-                                else cc0[S.ncoarse + (long long)k * 7 + mu - 1] = acc[r];
+                                if (mu == 0) cc0[k] = val;
+                                else cc0[S.ncoarse + (long long)k * 7 + mu - 1] = val;
                             }
                         }
                     } else if (MODE == M_KMID) {

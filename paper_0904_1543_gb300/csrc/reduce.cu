@@ -33,6 +33,60 @@ __global__ void rho_reduce_kernel(const double* __restrict__ parts, long long P,
     }
 }
 
+// E_loc = sum_o occ[o] (ekin[o] + epot[o]) (Sec. "Full local hamiltonian":
+// the local energy of the occupied orbitals): one CTA, thread t sums the
+// orbitals t, t + 256, ... in order, then a fixed tree over the threads.
+__global__ void eloc_total_kernel(const double* __restrict__ occ,
+                                  const double* __restrict__ ekin,
+                                  const double* __restrict__ epot, int norb,
+                                  double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int o = threadIdx.x; o < norb; o += blockDim.x) s += occ[o] * (ekin[o] + epot[o]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// dE_loc/dV = gbar rho (E_loc is linear in V with coefficient rho in grid
+// units), written in the potential's precision.
+template <typename T>
+__global__ void scale_density_kernel(const double* __restrict__ rho,
+                                     const double* __restrict__ gbar, long long P,
+                                     T* __restrict__ dV) {
+    const double g = *gbar;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride)
+        dV[i] = (T)(g * rho[i]);
+}
+
+cudaError_t launch_eloc_total(const double* occ, const double* ekin, const double* epot,
+                              int norb, double* out, cudaStream_t st) {
+    eloc_total_kernel<<<1, 256, 0, st>>>(occ, ekin, epot, norb, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scale_density(const double* rho, const double* gbar, long long P, T* dV,
+                                 cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    const int threads = 256;
+    long long blocks = (P + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    scale_density_kernel<T><<<(unsigned)blocks, threads, 0, st>>>(rho, gbar, P, dV);
+    count_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t launch_scale_density<double>(const double*, const double*, long long,
+                                                  double*, cudaStream_t);
+template cudaError_t launch_scale_density<float>(const double*, const double*, long long,
+                                                 float*, cudaStream_t);
+
 cudaError_t launch_reduce_parts(const double* part, const double* minus, int tiles,
                                 int norb, double* out, cudaStream_t st) {
     if (norb <= 0) return cudaSuccess;

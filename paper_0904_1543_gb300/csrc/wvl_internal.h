@@ -55,6 +55,8 @@ struct Seg {
     double* rho;          // M_POT: density target (null = none)
     double* part;         // per (orbital, tile) partial sums, [norb][tiles]
     const double* occ;    // M_POT: occupations of the segment's orbitals
+    const double* gscale; // M_COMP: when set, output o is scaled by 2 occ[o] gscale[0]
+                          //   (dE_loc/dpsi = 2 occ g H psi, the adjoint of E_loc)
     const double* eps;    // M_KMID pass 1 without in2: K_0 = -eps[o] G (Helmholtz shift)
     const int* mapc;      // M_UNCOMP/M_COMP with a localisation region: coarse point ->
     const int* mapf;      //   position of c^0 / index k of c^{1..7} (ncoarse + 7k), or -1
@@ -127,7 +129,8 @@ struct FzSeg {
     const T* V;           // FZ_POT3: potential
     double* rho;          // FZ_POT3: density target (null = none)
     long long rho_gstride;// 0 -> rho += ; else group g writes rho[g * stride]
-    const double* occ;    // FZ_POT3: occupations
+    const double* occ;    // FZ_POT3: occupations;  FZ_TA3 with gscale: the scale's occ
+    const double* gscale; // FZ_TA3: when set, H psi of orbital o is scaled by 2 occ[o] gscale[0]
     double* part;         // energy partials [norb][ptiles]; this program writes from poff
     long long P;          // fine points per orbital
     long long blk0;       // first job of the segment in the launch
@@ -208,5 +211,12 @@ cudaError_t launch_reduce_parts(const double* part, const double* minus, int til
                                 int norb, double* out, cudaStream_t st);
 cudaError_t launch_rho_reduce(const double* parts, long long P, int ngroups,
                               double* rho, cudaStream_t st);
+// E_loc = sum_o occ (ekin + epot) into *out (one fixed-order CTA), and
+// dV = gbar rho in the potential's precision (the adjoint of E_loc in V).
+cudaError_t launch_eloc_total(const double* occ, const double* ekin, const double* epot,
+                              int norb, double* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_scale_density(const double* rho, const double* gbar, long long P, T* dV,
+                                 cudaStream_t st);
 
 }  // namespace wvl

@@ -1,6 +1,7 @@
 """GPU parity of free (isolated) boundary conditions against the free-space
 oracle (dense non-circulant operators on an extended grid, no wrap-around).
-FP64 bound 1e-12 as in the other parity tests."""
+FP64 bound 1e-12 as in the other parity tests: normwise (max|d| / max|ref|)
+and elementwise where |ref| >= 1e-3 max|ref|."""
 import numpy as np
 import pytest
 
@@ -9,6 +10,18 @@ from paper_0904_1543_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 RTOL64 = 1e-12
+
+
+def _err(got, ref):
+    """max(normwise, elementwise on |ref| >= 1e-3 max|ref|) relative error."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    sc = np.abs(ref).max()
+    if sc == 0:
+        return float(np.abs(got).max())
+    d = np.abs(got - ref)
+    big = np.abs(ref) >= 1e-3 * sc
+    return float(max(d.max() / sc, (d[big] / np.abs(ref[big])).max()))
 
 
 @pytest.fixture(scope="module")
@@ -37,15 +50,15 @@ def test_hpsi_free(W, n, norb):
     for o in range(norb):
         r = FR.hpsi_local(psi[o], Vx, occ[o], n)
         ref = r["hpsi_c"]
-        assert np.abs(hp[o].cpu().numpy() - ref).max() < RTOL64 * np.abs(ref).max()
+        assert _err(hp[o].cpu().numpy(), ref) < RTOL64
         assert abs(float(ek[o]) - r["ekin"]) < RTOL64 * abs(r["ekin"])
         assert abs(float(ep[o]) - r["epot"]) < RTOL64 * abs(r["epot"])
         rho_ref = rho_ref + r["rho"]
     got = rho.cpu().numpy()
     ref = FR.restrict(rho_ref, 2 * pad)
-    assert np.abs(got - ref).max() < RTOL64 * np.abs(ref).max()
+    assert _err(got, ref) < RTOL64
     rho2 = W.density_free(torch.from_numpy(psi).cuda(), torch.from_numpy(occ).cuda(), g)
-    assert np.abs(rho2.cpu().numpy() - ref).max() < RTOL64 * np.abs(ref).max()
+    assert _err(rho2.cpu().numpy(), ref) < RTOL64
 
 
 @pytest.mark.parametrize("free_axes", [(0, 0, 1), (1, 0, 0), (0, 1, 1), (0, 0, 0)])
@@ -67,9 +80,9 @@ def test_hpsi_mixed_conditions(W, free_axes):
     rho_ref = 0.0
     for o in range(2):
         r = FR.hpsi_local_bc(psi[o], Vx, occ[o], n, free_axes, g.h)
-        assert np.abs(hp[o].cpu().numpy() - r["hpsi_c"]).max() < RTOL64 * np.abs(r["hpsi_c"]).max()
+        assert _err(hp[o].cpu().numpy(), r["hpsi_c"]) < RTOL64
         assert abs(float(ek[o]) - r["ekin"]) < RTOL64 * abs(r["ekin"])
         assert abs(float(ep[o]) - r["epot"]) < RTOL64 * abs(r["epot"])
         rho_ref = rho_ref + r["rho"]
     ref = FR.restrict_bc(rho_ref, n, 2 * pad, free_axes)
-    assert np.abs(rho.cpu().numpy() - ref).max() < RTOL64 * np.abs(ref).max()
+    assert _err(rho.cpu().numpy(), ref) < RTOL64

@@ -4,8 +4,9 @@ kernels, WVL_PLAN_FUSED) against the FP64 oracle.
 The chain applies the same 1D filters as the transposing passes, grouped by
 axis: axis 3 on N3 x 128-byte column tiles, axes 1 and 2 on whole planes in
 shared memory.  FP64 results therefore agree with the oracle to a few 1e-16
-and are held to the 1e-12 bound; FP32 to the FP32 bounds (2e-5 H psi, 1e-5
-density and energies) with the oracle run in FP64 on the FP32-rounded inputs.
+and are held to the 1e-12 bound; FP32 to the FP32 bounds (normwise 2e-6 H psi,
+5e-6 density, 5e-7 energies; elementwise 2e-4) with the oracle run in FP64 on
+the FP32-rounded inputs.
 
 Sizes: fine extents 32 to 128 in steps of 8 with uneven axes (N1 = 40, 48,
 80, 112 leave a partial last column tile), cells of different spacings (one
@@ -21,6 +22,13 @@ from paper_0904_1543_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 RTOL64 = 1e-12
+# FP32 bounds, normwise: H psi, psi_r and single operators 2e-6, density
+# 5e-6, energies 5e-7 relative (observed at most 5.3e-7, 1.2e-6 and 7.4e-8).
+# Elementwise (|ref| >= 1e-3 max|ref|): 2e-4.  An FP32 output's error comes
+# from the rounding of its neighbours' contributions, about u sum|f||x| over
+# the stencil, not from its own size, so an entry at 1e-3 of the maximum
+# carries up to normwise error / 1e-3 (observed at most 1.5e-4).
+RTOL32, RTOL32_RHO, RTOL32_E, ELEM32 = 2e-6, 5e-6, 5e-7, 2e-4
 
 
 def close(got, ref, rtol, what=""):
@@ -36,7 +44,8 @@ def close(got, ref, rtol, what=""):
     norm = d.max() / scale
     elem = (d[big] / np.abs(ref[big])).max()
     assert norm <= rtol, f"{what}: normwise {norm:.3e} > {rtol:.1e}"
-    assert elem <= max(rtol, 10 * rtol if rtol > 1e-9 else rtol), f"{what}: elementwise {elem:.3e}"
+    eb = rtol if rtol <= 1e-9 else ELEM32
+    assert elem <= eb, f"{what}: elementwise {elem:.3e} > {eb:.1e}"
 
 
 def rel(a, b):
@@ -88,7 +97,8 @@ def run_plan(W, cells, cell_of_orb, psi, Vs, occ, prec, chain, rho=True, graph=T
     return (host(hp), host(ek), host(ep), [host(r) for r in rh] if rho else None, plan)
 
 
-def check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, rtol, rtol_e, orbitals=None):
+def check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, rtol, rtol_e, orbitals=None,
+                         rtol_rho=None):
     hp, ek, ep, rho, plan = out
     rho_ref = [np.zeros(c.fine) for c in cells]
     for o, c in enumerate(cell_of_orb):
@@ -103,7 +113,7 @@ def check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, rtol, rtol_e, o
         rho_ref[c] += r["rho"]
     if rho is not None and orbitals is None:
         for c in range(len(cells)):
-            close(rho[c], rho_ref[c], rtol_e, f"rho cell {c}")
+            close(rho[c], rho_ref[c], rtol_e if rtol_rho is None else rtol_rho, f"rho cell {c}")
 
 
 @pytest.mark.parametrize("graph", [False, True])
@@ -164,7 +174,8 @@ def test_fused_f32_uneven_cells(W):
     Vs = [inputs.gaussian_potential(54, c, cells[c].n).astype(np.float32) for c in range(3)]
     occ = np.array([2.0, 1.0, 2.0, 0.5, 2.0, 1.5])
     out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, W.WVL_F32, "fused")
-    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, 2e-5, 1e-5)
+    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, RTOL32, RTOL32_E,
+                         rtol_rho=RTOL32_RHO)
 
 
 def test_fused_f32_single_cell_default(W):
@@ -179,16 +190,16 @@ def test_fused_f32_single_cell_default(W):
     rho = torch.zeros(g.fine, dtype=torch.float64, device="cuda")
     hp, ek, ep = W.hpsi_local(cuda(psi), cuda(V), cuda(occ), g, rho=rho)
     hp_r, rho_r, ek_r, ep_r = O.hpsi_batch(psi.astype(np.float64), V.astype(np.float64), occ, n)
-    close(host(hp), hp_r, 2e-5, "hpsi f32")
-    close(host(rho), rho_r, 1e-5, "rho f32")
-    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < 1e-5
-    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < 1e-5
+    close(host(hp), hp_r, RTOL32, "hpsi f32")
+    close(host(rho), rho_r, RTOL32_RHO, "rho f32")
+    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < RTOL32_E
+    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < RTOL32_E
 
 
 def test_fused_largest_planes(W):
     """FP32 planes of 128 x 128 and FP64 planes of 112 x 112 (the largest each
     form takes), two orbitals each, one checked against the oracle."""
-    for prec, n, dt, tol, tol_e in ((W.WVL_F32, (64, 64, 64), np.float32, 2e-5, 1e-5),
+    for prec, n, dt, tol, tol_e in ((W.WVL_F32, (64, 64, 64), np.float32, RTOL32, RTOL32_E),
                                     (W.WVL_F64, (56, 56, 40), np.float64, RTOL64, RTOL64)):
         cells = [W.Grid(n)]
         psis = [inputs.orbital(56, o, n).astype(dt) for o in range(2)]
@@ -212,7 +223,7 @@ def test_fused_bench_cells_sampled(W, prec):
     Vs = [inputs.gaussian_potential(2, c, sizes[c]).astype(dt) for c in range(3)]
     occ = np.full(192, 2.0)
     out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, p, "fused")
-    tol, tol_e = (RTOL64, RTOL64) if prec == "f64" else (2e-5, 1e-5)
+    tol, tol_e = (RTOL64, RTOL64) if prec == "f64" else (RTOL32, RTOL32_E)
     check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, tol, tol_e,
                          orbitals={5, 64 + 17, 128 + 63})
     hp, ek, ep, rho, _ = out
@@ -220,7 +231,7 @@ def test_fused_bench_cells_sampled(W, prec):
         assert rho[c].min() >= 0
         lhs = float(np.sum(Vs[c].astype(np.float64) * rho[c]))
         rhs = float(np.sum((occ * ep)[64 * c:64 * (c + 1)]))
-        assert rel(lhs, rhs) < (1e-11 if prec == "f64" else 1e-5), (c, lhs, rhs)
+        assert rel(lhs, rhs) < (1e-11 if prec == "f64" else RTOL32_RHO), (c, lhs, rhs)
 
 
 def test_autotuned_chain_choice(W):
@@ -251,12 +262,14 @@ def test_density_of_interleaved_runs(W, chain, prec):
     psis = [inputs.orbital(58, o, cells[c].n).astype(dt) for o, c in enumerate(cell_of_orb)]
     Vs = [inputs.gaussian_potential(58, c, cells[c].n).astype(dt) for c in range(2)]
     occ = np.array([2.0, 1.0, 0.5, 2.0, 1.5, 1.0])
-    tol = RTOL64 if prec == "f64" else 1e-5
     for rep in range(2):
         out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, p, chain,
                        graph=rep == 1)
-        check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out,
-                             tol if prec == "f64" else 2e-5, tol)
+        if prec == "f64":
+            check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, RTOL64, RTOL64)
+        else:
+            check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, RTOL32, RTOL32_E,
+                                 rtol_rho=RTOL32_RHO)
 
 
 @pytest.mark.parametrize("n,norb", [((16, 20, 24), 3), ((24, 16, 20), 20)])
@@ -273,11 +286,11 @@ def test_fused_energy_and_density_f32(W, n, norb):
     hp_r, rho_r, ek_r, ep_r = O.hpsi_batch(psi.astype(np.float64), V.astype(np.float64), occ, n)
     rho = torch.zeros(g.fine, dtype=torch.float64, device="cuda")
     ek, ep = W.energy(cuda(psi), cuda(V), cuda(occ), g, rho=rho)
-    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < 1e-5
-    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < 1e-5
-    close(host(rho), rho_r, 1e-5, "rho (energy)")
+    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < RTOL32_E
+    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < RTOL32_E
+    close(host(rho), rho_r, RTOL32_RHO, "rho (energy)")
     rho2 = W.density(cuda(psi), cuda(occ), g)
-    close(host(rho2), rho_r, 1e-5, "rho (density)")
+    close(host(rho2), rho_r, RTOL32_RHO, "rho (density)")
 
 
 def test_mixed_eligibility_falls_back_to_passes(W):
@@ -290,7 +303,8 @@ def test_mixed_eligibility_falls_back_to_passes(W):
     Vs = [inputs.gaussian_potential(63, c, cells[c].n).astype(np.float32) for c in range(2)]
     occ = np.array([2.0, 1.0, 2.0, 0.5])
     out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, W.WVL_F32, None)
-    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, 2e-5, 1e-5)
+    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, RTOL32, RTOL32_E,
+                         rtol_rho=RTOL32_RHO)
     with pytest.raises(W.WvlError):
         W.Plan(cells, cell_of_orb, prec=W.WVL_F32, chain="fused")
 

@@ -7,9 +7,9 @@ relative to |E|.  The kernels and the oracle sum the same terms in different
 orders (FMA chains of at most 29 taps per pass, 15 passes), which leaves
 differences of a few 1e-16 relative.  FP32: storage and convolutions in
 binary32 (unit roundoff 6e-8); after 15 passes of up to 29 taps the
-normwise error is a few 1e-7, bounded here by 2e-5 (H psi, psi_r) and 1e-5
-(energies, density), with the oracle run in FP64 on the same FP32-rounded
-inputs.
+normwise error is a few 1e-7, bounded here by 2e-6 (H psi, psi_r, single
+operators), 5e-6 (density) and 5e-7 (energies), with the oracle run in FP64
+on the same FP32-rounded inputs (elementwise bound below).
 """
 import numpy as np
 import pytest
@@ -20,6 +20,13 @@ from paper_0904_1543_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 RTOL64 = 1e-12
+# FP32 bounds, normwise: H psi, psi_r and single operators 2e-6, density
+# 5e-6, energies 5e-7 relative (observed at most 5.3e-7, 1.2e-6 and 7.4e-8).
+# Elementwise (|ref| >= 1e-3 max|ref|): 2e-4.  An FP32 output's error comes
+# from the rounding of its neighbours' contributions, about u sum|f||x| over
+# the stencil, not from its own size, so an entry at 1e-3 of the maximum
+# carries up to normwise error / 1e-3 (observed at most 1.5e-4).
+RTOL32, RTOL32_RHO, RTOL32_E, ELEM32 = 2e-6, 5e-6, 5e-7, 2e-4
 
 
 def close(got, ref, rtol, what=""):
@@ -35,7 +42,8 @@ def close(got, ref, rtol, what=""):
     big = np.abs(ref) >= 1e-3 * scale
     elem = (d[big] / np.abs(ref[big])).max()
     assert norm <= rtol, f"{what}: normwise {norm:.3e} > {rtol:.1e}"
-    assert elem <= max(rtol, 10 * rtol if rtol > 1e-9 else rtol), f"{what}: elementwise {elem:.3e}"
+    eb = rtol if rtol <= 1e-9 else ELEM32
+    assert elem <= eb, f"{what}: elementwise {elem:.3e} > {eb:.1e}"
 
 
 def rel(a, b):
@@ -203,10 +211,10 @@ def test_hpsi_local_f32(W, n, norb):
     rho = torch.zeros(g.fine, dtype=torch.float64, device="cuda")
     hp, ek, ep = W.hpsi_local(cuda(psi32), cuda(V32), cuda(occ), g, rho=rho)
     hp_r, rho_r, ek_r, ep_r = O.hpsi_batch(psi32.astype(np.float64), V32.astype(np.float64), occ, n)
-    close(host(hp), hp_r, 2e-5, "hpsi f32")
-    close(host(rho), rho_r, 1e-5, "rho f32")
-    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < 1e-5
-    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < 1e-5
+    close(host(hp), hp_r, RTOL32, "hpsi f32")
+    close(host(rho), rho_r, RTOL32_RHO, "rho f32")
+    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < RTOL32_E
+    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < RTOL32_E
 
 
 def test_f32_full_size_sampled(W):
@@ -242,10 +250,10 @@ def test_f32_full_size_sampled(W):
     for o in (0, norb - 1):
         a, b = plan.offsets[o], plan.offsets[o + 1]
         r = O.hpsi_local(psi[a:b].astype(np.float64), V.astype(np.float64), 2.0, n)
-        close(host(hp[a:b]), r["hpsi_c"], 2e-5, f"f32 orbital {o}")
-        assert rel(float(ek[o]), r["ekin"]) < 1e-5
-        assert rel(float(ep[o]), r["epot"]) < 1e-5
-    close(host(rho32), host(out[W.WVL_F64][3]), 1e-5, "f32 rho")
+        close(host(hp[a:b]), r["hpsi_c"], RTOL32, f"f32 orbital {o}")
+        assert rel(float(ek[o]), r["ekin"]) < RTOL32_E
+        assert rel(float(ep[o]), r["epot"]) < RTOL32_E
+    close(host(rho32), host(out[W.WVL_F64][3]), RTOL32_RHO, "f32 rho")
 
 
 @pytest.mark.parametrize("n", [(4, 4, 4), (9, 7, 5)])
@@ -253,12 +261,12 @@ def test_single_ops_f32(W, n):
     g = W.Grid(n)
     x = inputs.random_field(32, 1, (2,) + g.fine).astype(np.float32)
     x64 = x.astype(np.float64)
-    close(host(W.magicfilter(cuda(x), g)[0]), O.magicfilter3d(x64[0]), 2e-5, "mf f32")
-    close(host(W.magicfilter_T(cuda(x), g)[1]), O.magicfilter_T3d(x64[1]), 2e-5, "mfT f32")
+    close(host(W.magicfilter(cuda(x), g)[0]), O.magicfilter3d(x64[0]), RTOL32, "mf f32")
+    close(host(W.magicfilter_T(cuda(x), g)[1]), O.magicfilter_T3d(x64[1]), RTOL32, "mfT f32")
     out, ek = W.kinetic(cuda(x), g)
-    close(host(out[0]), O.kinetic3d(x64[0]), 2e-5, "kin f32")
+    close(host(out[0]), O.kinetic3d(x64[0]), RTOL32, "kin f32")
     s = W.synthesis(cuda(x.reshape(2, -1)), g)
-    close(host(s[1]), O.synthesis3d(O.uncompress(x64[1].reshape(-1), n)), 2e-5, "syn f32")
+    close(host(s[1]), O.synthesis3d(O.uncompress(x64[1].reshape(-1), n)), RTOL32, "syn f32")
 
 
 # ----------------------------------------------------------------- plans
@@ -407,7 +415,7 @@ def test_longest_lines_f32(W, axis):
     hp, ek, ep = W.hpsi_local(cuda(psi), cuda(V), cuda(occ), g, rho=rho)
     hp_r, rho_r, ek_r, ep_r = O.hpsi_batch(psi.astype(np.float64), V.astype(np.float64), occ, n,
                                            g.h)
-    close(host(hp), hp_r, 2e-5, f"hpsi f32 axis {axis}")
-    close(host(rho), rho_r, 1e-5, f"rho f32 axis {axis}")
-    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < 1e-5
-    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < 1e-5
+    close(host(hp), hp_r, RTOL32, f"hpsi f32 axis {axis}")
+    close(host(rho), rho_r, RTOL32_RHO, f"rho f32 axis {axis}")
+    assert np.max(np.abs(host(ek) - ek_r) / np.abs(ek_r)) < RTOL32_E
+    assert np.max(np.abs(host(ep) - ep_r) / np.abs(ep_r)) < RTOL32_E
