@@ -228,3 +228,23 @@ def energy_gradients(psi, V, occ, n, hgrid=(0.25, 0.25, 0.25)):
     hp, rho, _, _ = hpsi_batch(psi, V, occ, n, hgrid)
     occ = np.asarray(occ, dtype=np.float64)
     return 2.0 * occ[:, None] * hp, rho
+
+
+# --------------------------------------------------------------------------
+# scalar products in compressed form
+# --------------------------------------------------------------------------
+def scalar_products(a, b):
+    """S[i][j] = <a_i|b_j> = sum_k a_i[k] b_j[k] for compressed orbitals (rows
+    of a and b).  The basis functions of Eq. (wavef0) are orthonormal (Sec.
+    "Daubechies basis and wavelet transformation"), so the scalar product of
+    two orbitals is the sum of the products of their coefficients.  Each sum
+    is the correctly rounded sum (math.fsum) of the FP64 products, which are
+    exact when the coefficients are FP32 values."""
+    import math
+    a = np.asarray(a, dtype=np.float64).reshape(len(a), -1)
+    b = np.asarray(b, dtype=np.float64).reshape(len(b), -1)
+    S = np.empty((a.shape[0], b.shape[0]))
+    for i in range(a.shape[0]):
+        for j in range(b.shape[0]):
+            S[i, j] = math.fsum(a[i] * b[j])
+    return S
