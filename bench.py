@@ -14,8 +14,11 @@ flush is needed between steps.
 numpy) on a bounded sample of the same workload (one orbital of each cell per
 step) on the host cores.
 
-Multi-GPU (torchrun): every rank runs its own 192 orbitals (weak scaling, no
-data-path collective); value = all ranks' orbitals / max-over-ranks time.
+Multi-GPU (torchrun): every rank runs its own 192 orbitals of the same three
+cells (weak scaling, the paper's orbital distribution), and each step ends
+with the one exchange that distribution needs: the density (FP64, per cell)
+and the energy sums all-reduced over the ranks; value = all ranks' orbitals /
+max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -104,6 +107,16 @@ def max_over_ranks(times, dist, world, device="cpu"):
     t = torch.tensor(list(times), dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return [float(v) for v in t]
+
+
+def sum_over_ranks(tensors, dist, world):
+    """The one exchange of the orbital distribution (Sec. "Parallel
+    distribution"): every rank's density, and its energy sums, added over the
+    ranks in place (NCCL on GPU ranks, gloo on CPU ranks); a no-op on one rank."""
+    if world <= 1:
+        return
+    for t in tensors:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
 
 
 def job_throughput(norb_per_rank, world, steps, ms):
@@ -370,9 +383,39 @@ def measure_variants(args, W, torch, dev):
     # density over all 256 orbitals against the FP64 GPU form (which matches
     # the oracle to 1e-12 in the parity tests)
     err_rho = float((rho32 - rho64).abs().max() / rho64.abs().max())
+    # orbital scalar products of the FP32 orbitals in compressed form, FP64
+    # products and accumulation: the whole 256 x 256 overlap (symmetric path:
+    # the 36 upper 32 x 32 tiles) and <psi_o|H psi_o>
+    length = 8 * n[0] * n[1] * n[2]
+    ms_ov = _time_steps(torch, lambda: W.overlap(psi32), max(2, args.steps // 3), 2)
+    Sov = W.overlap(psi32).cpu().numpy()
+    ms_dot = _time_steps(torch, lambda: W.dot(psi32, hp32), args.steps, 2)
+    dh = W.dot(psi32, hp32).cpu().numpy()
+    ov_err = 0.0
+    for i, j in ((0, 0), (0, norb - 1), (17, 130), (norb - 1, norb - 1)):
+        a_i = psi32[i].double().cpu().numpy()
+        a_j = psi32[j].double().cpu().numpy()
+        ref = O.scalar_products(a_i[None], a_j[None])[0, 0]
+        ov_err = max(ov_err, abs(Sov[i, j] - ref) / np.sqrt(np.dot(a_i, a_i) * np.dot(a_j, a_j)))
+    tiles = (norb + 31) // 32
+    dfma = tiles * (tiles + 1) // 2 * 1024 * length
+    scalar_products = {
+        "overlap_ms": ms_ov, "dot_ms": ms_dot,
+        "overlap_fp64_tflops": 2.0 * dfma / (ms_ov * 1e-3) / 1e12,
+        "overlap_frac_of_fp64_peak": 2.0 * dfma / (ms_ov * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+        "overlap_rel_err_vs_oracle": float(ov_err),
+        "overlap_symmetric": bool(np.array_equal(Sov, Sov.T)),
+        "dot_psi_hpsi_vs_ekin_plus_epot": float(np.max(np.abs(dh - (ek32 + ep32).cpu().numpy())
+                                                      / np.abs((ek32 + ep32).cpu().numpy()))),
+        "what": "S = <psi_i|psi_j> for all 256 FP32 orbitals (FP64 products and sums; 36 "
+                "upper 32 x 32 tiles of FP64 FMAs), and <psi_o|H psi_o> per orbital; error: "
+                "4 sampled entries against the oracle's correctly rounded sums, relative to "
+                "sqrt(<psi_i|psi_i> <psi_j|psi_j>)",
+    }
     out["fp32_batched"] = {
         "workload": "256 orbitals, periodic coarse 48^3 (fine 96^3), FP32 convolutions, "
-                    "compensated/FP64 reductions, one autotuned graph-captured plan",
+                    "FP64 reductions, one autotuned graph-captured plan",
+        "scalar_products": scalar_products,
         "value": norb / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
         "chain": chains["f32"],
         "fp32_passes_same_workload": {"value": norb / (ms32p * 1e-3), "ms_per_step": ms32p},
@@ -525,7 +568,7 @@ def measure_variants(args, W, torch, dev):
     bpp = FUSED_BPP if chain_a.startswith("fused") else PASSES_BPP
     out["fp32_headline_workload"] = {
         "workload": WORKLOAD["workload"].replace("batched FP64", "batched FP32 convolutions "
-                                                 "(compensated/FP64 reductions)"),
+                                                 "(FP64 reductions)"),
         "value": len(cell_of_orb) / (ms_a * 1e-3), "unit": UNIT, "ms_per_step": ms_a,
         "chain": chain_a,
         "passes_same_workload": {"value": len(cell_of_orb) / (f32["passes"][0] * 1e-3),
@@ -540,7 +583,7 @@ def measure_variants(args, W, torch, dev):
                                "unit": "TFLOP/s",
                                "frac": 2 * FP32_FMA_PER_POINT * pts_h / (ms_a * 1e-3) / 1e12
                                / FP32_PEAK_TFLOPS,
-                               "peak_source": "FP32 FMA-chain probe on this GPU model"},
+                               "peak_source": PEAK_SOURCE + " (FP32)"},
         "rel_err_hpsi_vs_oracle": eh, "rel_err_energies_vs_oracle": ee,
         "error_sample": "the first orbital of each cell against the FP64 oracle",
     }
@@ -649,7 +692,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     emu = args.prec == "f64emu"  # FP64-accurate tensor-core form (profiling)
     if f32 or emu:
         WL["workload"] = WL["workload"].replace(
-            "batched FP64", "batched FP32 convolutions (compensated/FP64 reductions)" if f32
+            "batched FP64", "batched FP32 convolutions (FP64 reductions)" if f32
             else "batched FP64 by f16-digit tensor-core emulation")
     pcode = W.WVL_F32 if f32 else (W.WVL_F64_EMU if emu else W.WVL_F64)
     tdt = torch.float32 if f32 else torch.float64
@@ -669,9 +712,18 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     if not args.no_autotune:
         plan.autotune(psi, V, occ, hpsi=hp, rho=rho)
     stream = torch.cuda.current_stream(dev)
+    # several ranks: each holds its own orbitals of the same cells; a step
+    # ends with the density and energy sums over the ranks
+    en_sum = torch.zeros(2, dtype=torch.float64, device=dev)
 
     def step():
+        if world > 1:
+            for r in rho:
+                r.zero_()
         plan.hpsi(psi, V, occ, hpsi=hp, rho=rho, ekin=ek, epot=ep)
+        if world > 1:
+            torch.stack([ek.sum(), ep.sum()], out=en_sum)
+            sum_over_ranks(rho + [en_sum], dist, world)
 
     # ---- device-resident timed region (graph replay)
     gpu_id = local
@@ -775,6 +827,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
                 r.zero_()
             b["plan"].hpsi(b["psi"], b["V"], b["occ"], hpsi=b["hp"], rho=b["rho"],
                            ekin=b["ek"], epot=b["ep"])
+            sum_over_ranks(b["rho"], dist, world)
             b["ev_comp"].record(comp)
             s_out.wait_event(b["ev_comp"])
             with torch.cuda.stream(s_out):

@@ -24,9 +24,12 @@
  * Orbitals of one call are contiguous, orbital o at offset o * 8 n1 n2 n3
  *   (compressed) or o * P (fine).
  * Precision: WVL_F64 -- every array is double.  WVL_F32 -- coefficient, fine
- *   and potential arrays are float; rho, occ and energies stay double, and
- *   every reduction (rho over orbitals, Ekin, Epot) is carried at least in
- *   compensated single (~48-bit) inside a thread and in double above it.
+ *   and potential arrays are float, and so are the convolutions; rho, occ and
+ *   energies stay double.  Energies accumulate in double (each term an FP32
+ *   chain of at most 32 products of convolution outputs, converted exactly);
+ *   scalar products (wvl_overlap, wvl_dot) form every product and sum in
+ *   double; rho over orbitals is carried per thread in compensated single
+ *   (~48-bit) and in double from there on.
  *   WVL_F64_EMU -- arrays as WVL_F64; every 1D convolution sum of the
  *   passes (Eqs. 1dconvtrans, kinetic1d) is evaluated on the FP16 tensor
  *   cores instead of the FP64 pipe: operands split into six signed 10-bit
@@ -233,6 +236,28 @@ wvl_status wvl_eloc_backward(const wvl_grid* grid, int prec, int norb,
                              const double* rho, const double* gbar,
                              void* dpsi_c, void* dV,
                              void* ws, size_t ws_bytes, void* stream);
+
+/* Orbital scalar products in compressed form (Sec. "Daubechies basis and
+ * wavelet transformation": the basis functions of Eq. wavef0 are
+ * orthonormal, so <psi_i|psi_j> is the sum of the products of the
+ * coefficients, taken on the compressed vectors).  Precision `prec` gives the
+ * element type of a and b (float for WVL_F32, else double); every product is
+ * formed in FP64 (an FP32 x FP32 product is exact there) and accumulated in
+ * FP64 by a fixed-order two-stage reduction, so repeated calls give
+ * identical results.
+ *   wvl_overlap: S[i][j] = <a_i|b_j>, a: [na][len], b: [nb][len] (device),
+ *     S: device double [na][nb], written.  When a == b and na == nb only the
+ *     upper block triangle is computed and mirrored.
+ *   wvl_dot: d[o] = <a_o|b_o> for o < n (norms, <psi|H psi>), d: device
+ *     double[n], written.
+ * len may be any compressed length (full grid 8 n1 n2 n3, or a region's
+ * ncoarse + 7 nfine).  Workspace: wvl_overlap_workspace_size() (enough for
+ * both calls with these sizes). */
+wvl_status wvl_overlap_workspace_size(int prec, int na, int nb, long long len, size_t* bytes);
+wvl_status wvl_overlap(int prec, int na, const void* a, int nb, const void* b, long long len,
+                       double* S, void* ws, size_t ws_bytes, void* stream);
+wvl_status wvl_dot(int prec, int n, const void* a, const void* b, long long len, double* d,
+                   void* ws, size_t ws_bytes, void* stream);
 
 /* Preconditioning step (paper Eq. precon, Sec. "Kinetic convolution" with
  * K_0 = -eps s): for each orbital o, ncg iterations of the preconditioned

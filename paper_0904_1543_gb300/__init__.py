@@ -23,7 +23,7 @@ from . import _build
 
 __all__ = [
     "WvlError", "Grid", "lib", "filters", "workspace_size", "synthesis", "analysis",
-    "magicfilter", "magicfilter_T", "kinetic", "density", "hpsi_local", "energy", "eloc",
+    "magicfilter", "magicfilter_T", "kinetic", "density", "hpsi_local", "energy", "eloc", "overlap", "dot",
     "Plan", "ELoc", "device_count", "wait_timeouts", "WVL_F64", "WVL_F32", "WVL_F64_EMU",
 ]
 
@@ -96,6 +96,12 @@ def _declare(L):
                                     _vp, _vp, _sz, _vp]),
         "wvl_eloc_backward": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
                                              _vp, _vp, _vp, _vp, _sz, _vp]),
+        "wvl_overlap_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_longlong, ctypes.POINTER(_sz)]),
+        "wvl_overlap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                       ctypes.c_longlong, _vp, _vp, _sz, _vp]),
+        "wvl_dot": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_longlong, _vp,
+                                   _vp, _sz, _vp]),
         "wvl_plan_create": (ctypes.c_int, [G, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_uint, ctypes.POINTER(_vp)]),
         "wvl_plan_destroy": (ctypes.c_int, [_vp]),
@@ -350,6 +356,50 @@ def eloc(psi_c, V, occ, grid: Grid, rho=None, emu=False):
     _run(lib().wvl_eloc, grid, _prec(psi_c, emu), norb, dev, psi_c.data_ptr(), V.data_ptr(),
          occ.data_ptr(), _p(rho), ek.data_ptr(), ep.data_ptr(), e.data_ptr())
     return e, ek, ep
+
+
+def _overlap_ws(prec, na, nb, ln, device):
+    need = _sz(0)
+    _check(lib().wvl_overlap_workspace_size(prec, na, nb, ln, ctypes.byref(need)))
+    st = _stream(device)
+    ws, wsb = _workspace(need.value, device, st)
+    return ws, wsb, st
+
+
+def overlap(a, b=None):
+    """Scalar products <a_i|b_j> of compressed orbitals (rows of a and b; b
+    defaults to a) as a float64 (na, nb) device tensor: FP64 products and
+    accumulation whatever the coefficients' precision."""
+    b = a if b is None else b
+    if a.dtype != b.dtype:
+        raise TypeError("a and b must have the same dtype")
+    a2 = a.reshape(a.shape[0], -1)
+    b2 = b.reshape(b.shape[0], -1)
+    if a2.shape[1] != b2.shape[1]:
+        raise ValueError("a and b must have the same length per orbital")
+    _dev(a2, "a"), _dev(b2, "b")
+    na, nb, ln = a2.shape[0], b2.shape[0], a2.shape[1]
+    S = torch.empty((na, nb), dtype=torch.float64, device=a.device)
+    prec = _prec(a)
+    ws, wsb, st = _overlap_ws(prec, na, nb, ln, a.device)
+    _check(lib().wvl_overlap(prec, na, a2.data_ptr(), nb, b2.data_ptr(), ln, S.data_ptr(), ws,
+                             wsb, st))
+    return S
+
+
+def dot(a, b):
+    """Per-orbital scalar products <a_o|b_o> (float64, FP64 accumulation)."""
+    if a.shape != b.shape or a.dtype != b.dtype:
+        raise ValueError("a and b must have the same shape and dtype")
+    a2 = a.reshape(a.shape[0], -1)
+    b2 = b.reshape(b.shape[0], -1)
+    _dev(a2, "a"), _dev(b2, "b")
+    n, ln = a2.shape
+    d = torch.empty(n, dtype=torch.float64, device=a.device)
+    prec = _prec(a)
+    ws, wsb, st = _overlap_ws(prec, n, n, ln, a.device)
+    _check(lib().wvl_dot(prec, n, a2.data_ptr(), b2.data_ptr(), ln, d.data_ptr(), ws, wsb, st))
+    return d
 
 
 class Plan:

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libwvl.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["api.cu", "kernels_f64.cu", "kernels_f32.cu", "emu_kernel.cu", "fused_kernel.cu",
-              "reduce.cu", "noalloc.cu", "pcg.cu", "probe.cu"]
+              "reduce.cu", "noalloc.cu", "pcg.cu", "probe.cu", "overlap.cu"]
 CPP_SOURCES = ["filters.cpp"]
 HEADERS = ["wvl_internal.h", "taps.h", "pass_kernel.cuh", "kernels_impl.cuh", "emu.cuh"]
 

@@ -33,6 +33,9 @@ static wvl_status fail(wvl_status s, const char* fmt, ...) {
     va_end(ap);
     return s;
 }
+wvl_status set_error(wvl_status s, const char* msg) { return fail(s, "%s", msg); }
+void clear_error() { g_err[0] = 0; }
+
 static wvl_status cuda_fail(cudaError_t e, const char* where) {
     return fail(WVL_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }

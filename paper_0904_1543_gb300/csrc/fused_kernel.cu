@@ -347,7 +347,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
             const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
             T acc[RC][VEC];
             col_item<T, K_KIN>(X, rowoff, r0, cv, p.tap[2], acc);
-            T ei = T(0);   // the item's <s, v> (at most 32 products), then compensated
+            T ei = T(0);   // the item's <s, v> (at most 32 products), then added in FP64
             #pragma unroll
             for (int kk = 0; kk < RC; ++kk) {
                 const int off = (r0 + kk) * RS + cv * VEC;
@@ -617,7 +617,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         double* const epw = reinterpret_cast<double*>(Z + N3 * RS);
         const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RC;
         const bool mine = (int)threadIdx.x < nitems && cv < ncv;
-        Acc<T> racc[RC][VEC];
+        RhoAcc<T> racc[RC][VEC];
         const bool pot = S.V != nullptr, full = S.out != nullptr;
         if (pot) load_tile(Z, S.V + col0);
         load_tile(X, S.in + (long long)o0 * S.P + col0);

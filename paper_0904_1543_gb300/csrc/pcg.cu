@@ -4,8 +4,8 @@
 //
 // Every orbital has its own scalars (alpha, beta, r.z) kept on the device, so
 // the iteration never synchronises with the host.  Dot products are two-stage
-// and deterministic: per-block partials (compensated in FP32 mode), then the
-// fixed-order warp reduction of reduce.cu.
+// and deterministic: per-block partials (products and sums in FP64 in both
+// modes), then the fixed-order warp reduction of reduce.cu.
 #include <cuda_runtime.h>
 
 #include "pass_kernel.cuh"

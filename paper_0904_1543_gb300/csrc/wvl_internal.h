@@ -6,6 +6,8 @@
 
 #include <cuda_runtime_api.h>
 
+#include "wvl.h"
+
 namespace wvl {
 
 // Filters of the method, derived on the host (filters.cpp).
@@ -36,8 +38,8 @@ enum Mode {
 
 constexpr int MAXSEG = 8;      // cells (segments) per launch
 constexpr int NTHREADS = 128;  // threads per CTA (4 warps)
-// register-resident density outputs per thread in M_POT: 32 FP64 sums, or 16
-// compensated FP32 pairs (keeps the FP32 kernel at <= 128 registers)
+// register-resident density outputs per thread in the FP64 M_POT pass (the
+// FP32 pass keeps its compensated density sums in shared memory)
 template <typename T>
 __host__ __device__ constexpr int pot_out() { return sizeof(T) == 8 ? 32 : 16; }
 constexpr int MAX_FINE = 1024; // largest fine extent of one axis
@@ -205,6 +207,9 @@ cudaError_t launch_pcg(int which, const PcgParams& q, T* a, T* b, T* c, T* d, co
 
 // Kernel-launch counter behind wvl_kernel_launches().
 void count_launches(unsigned long long k);
+// Status with a detail string for wvl_last_error() (thread-local), and its reset.
+wvl_status set_error(wvl_status s, const char* msg);
+void clear_error();
 
 // ekin/epot finalisation and density reduction.
 cudaError_t launch_reduce_parts(const double* part, const double* minus, int tiles,

@@ -1,7 +1,7 @@
 """The N > 1 path of bench.py on CPU ranks (gloo, world size 2): disjoint
 orbital ownership per rank, max-over-ranks timing, whole-job throughput, and
-the density sum over ranks that an SCF code would need (fixed order, so the
-result is the same on every rank)."""
+the exchange each multi-rank step ends with (bench.sum_over_ranks: the
+density and the energy sums over the ranks, the same result on every rank)."""
 import os
 import socket
 
@@ -43,9 +43,11 @@ def _worker(rank, world, port, out):
         rho = np.zeros((8, 4, 6))
         for o in owned:
             rho += O.hpsi_local(inputs.orbital(7, o, n), V, 2.0, n)["rho"]
+        # the exchange of bench.py's multi-rank step: density and energy sums
         t = torch.from_numpy(rho)
-        dist.all_reduce(t)
-        out[rank] = (owned, mx, thr, t.numpy().copy())
+        en = torch.tensor([float(rank + 1), 0.5], dtype=torch.float64)
+        bench.sum_over_ranks([t, en], dist, world)
+        out[rank] = (owned, mx, thr, t.numpy().copy(), en.numpy().copy())
     finally:
         dist.destroy_process_group()
 
@@ -58,8 +60,9 @@ def test_two_cpu_ranks():
     out = manager.dict()
     mp.start_processes(_worker, args=(world, port, out), nprocs=world, join=True,
                        start_method="spawn")
-    owned0, mx0, thr0, rho0 = out[0]
-    owned1, mx1, thr1, rho1 = out[1]
+    owned0, mx0, thr0, rho0, en0 = out[0]
+    owned1, mx1, thr1, rho1, en1 = out[1]
+    assert np.array_equal(en0, en1) and list(en0) == [3.0, 1.0]
     assert set(owned0).isdisjoint(owned1)
     assert owned0 + owned1 == [0, 1, 2, 3]
     assert mx0 == mx1 == [11.0, 20.0]
