@@ -617,7 +617,9 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         double* const epw = reinterpret_cast<double*>(Z + N3 * RS);
         const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RC;
         const bool mine = (int)threadIdx.x < nitems && cv < ncv;
-        RhoAcc<T> racc[RC][VEC];
+        constexpr bool PK = sizeof(T) == 4;   // FP32: compensated pairs, two columns at once
+        FF2 rp[PK ? RC : 1][PK ? 2 : 1];
+        RhoAcc<T> racc[PK ? 1 : RC][PK ? 1 : VEC];
         const bool pot = S.V != nullptr, full = S.out != nullptr;
         if (pot) load_tile(Z, S.V + col0);
         load_tile(X, S.in + (long long)o0 * S.P + col0);
@@ -631,11 +633,24 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             if (mine) {
                 col_item<T, K_MF, RC>(X, rowoff, r0, cv, p.tap[0], acc);
                 T ei = T(0);
+                if constexpr (PK) {
+                    const float2 oc = make_float2(occ, occ);
+                    #pragma unroll
+                    for (int kk = 0; kk < RC; ++kk) {
+                        const float2 a01 = make_float2(acc[kk][0], acc[kk][1]);
+                        const float2 a23 = make_float2(acc[kk][2], acc[kk][3]);
+                        ff2_add(rp[kk][0], __fmul2_rn(__fmul2_rn(oc, a01), a01));
+                        ff2_add(rp[kk][1], __fmul2_rn(__fmul2_rn(oc, a23), a23));
+                    }
+                } else {
+                    #pragma unroll
+                    for (int kk = 0; kk < RC; ++kk)
+                        #pragma unroll
+                        for (int q = 0; q < VEC; ++q) racc[kk][q].add(occ * acc[kk][q] * acc[kk][q]);
+                }
                 #pragma unroll
                 for (int kk = 0; kk < RC; ++kk) {
                     const int off = (r0 + kk) * RS + cv * VEC;
-                    #pragma unroll
-                    for (int q = 0; q < VEC; ++q) racc[kk][q].add(occ * acc[kk][q] * acc[kk][q]);
                     if (pot) {
                         const Vec<T> vv = ldv(Z + off);
                         T y[VEC];
@@ -681,8 +696,11 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
                     const long long g = (long long)(r0 + kk) * plane + col0 + cv * VEC + q;
-                    if (S.rho_gstride == 0) rb[g] += racc[kk][q].get();
-                    else rb[g] = racc[kk][q].get();
+                    double v;
+                    if constexpr (PK) v = ff2_get(rp[kk][q >> 1], q & 1);
+                    else v = racc[kk][q].get();
+                    if (S.rho_gstride == 0) rb[g] += v;
+                    else rb[g] = v;
                 }
         }
     }

@@ -50,6 +50,23 @@ __device__ __forceinline__ void ff_add(FF& a, float x) {
     a.lo += e;
 }
 
+// two compensated pairs at once with packed FP32 arithmetic (two adds per
+// lane per instruction): the same two-sum, s - a computed as s + (-1) a
+struct FF2 { float2 hi{0.f, 0.f}, lo{0.f, 0.f}; };
+__device__ __forceinline__ void ff2_add(FF2& a, float2 x) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 s = __fadd2_rn(a.hi, x);
+    const float2 bb = __ffma2_rn(a.hi, m1, s);     // s - hi
+    const float2 t = __ffma2_rn(bb, m1, s);        // s - bb
+    const float2 e1 = __ffma2_rn(t, m1, a.hi);     // hi - (s - bb)
+    const float2 e2 = __ffma2_rn(bb, m1, x);       // x - bb
+    a.lo = __fadd2_rn(a.lo, __fadd2_rn(e1, e2));
+    a.hi = s;
+}
+__device__ __forceinline__ double ff2_get(const FF2& a, int c) {
+    return c ? (double)a.hi.y + (double)a.lo.y : (double)a.hi.x + (double)a.lo.x;
+}
+
 // energy accumulator: FP64 in both forms
 template <typename T> struct Acc;
 template <> struct Acc<double> {
