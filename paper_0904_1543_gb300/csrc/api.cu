@@ -140,6 +140,7 @@ template <typename T>
 struct SegDesc {
     Seg<T> s{};
     int Nf[3] = {0, 0, 0};
+    int gn = 0, gN = 0;      // free lines: the pass's output line length and line count
     double hax = 0.0;        // spacing of the pass axis (kinetic)
     double* user_rho = nullptr;
     double* rho_part = nullptr;
@@ -280,6 +281,10 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
             if (c.kind == K_KIN && i > first && d.hax != hax) break;
             Seg<T>& s = d.s;
             pass_dims(d.Nf, c.pass, s.n, s.N);
+            if (d.gn > 0) {
+                s.n = d.gn;
+                s.N = d.gN;
+            }
             if (emu) {
                 // units: 128-line tiles (the kernel walks their output windows)
                 s.nwin = (s.n + emu::window_n(c.kind) - 1) / emu::window_n(c.kind);
@@ -312,8 +317,14 @@ static wvl_status exec_call(PassCall<T>& c, const Tune& tn, cudaStream_t st) {
                     s.rho_gstride = 0;
                 } else {
                     s.rho = d.rho_part;
-                    s.rho_gstride = s.P;
+                    s.rho_gstride = s.vN1 > 0 ? s.vP : s.P;
                 }
+            }
+            if (c.mode == M_POT && s.vN1 > 0 && s.rho != nullptr && s.rho_gstride > 0) {
+                // free lines cover part of the grid of rho only: the groups'
+                // partials start at zero everywhere, as the reduction adds them all
+                cudaError_t e = cudaMemsetAsync(s.rho, 0, (size_t)d.groups * s.vP * sizeof(double), st);
+                if (e != cudaSuccess) return cuda_fail(e, "density partials");
             }
             s.blk0 = blk;
             blk += units * s.tiles;
@@ -380,6 +391,12 @@ struct CellRun {
     int chain = 0;                 // OP_HPSI: CHAIN_AUTO, CHAIN_PASSES or CHAIN_FUSED
     bool rho_shared = false;       // another run of the same call adds into the same rho:
                                    //   the density goes through the run's partials
+    // free boundary conditions computed on supports that grow pass by pass
+    // (grow_seg): the box's coarse extents and which axes are free; the cell
+    // fields (n, Nf, P) are those of the padded cell that V and rho cover
+    bool grow = false;
+    int gb[3] = {0, 0, 0};
+    bool gfree[3] = {false, false, false};
 };
 
 // Runs that add into one density array must not do so from one launch (their
@@ -462,13 +479,94 @@ static SegDesc<T> seg_for(const CellRun<T>& c, const T* in, T* out) {
     return d;
 }
 
+// Free boundary conditions on growing supports.  Along a free axis with b
+// box coarse points (fine [0, 2b)) each array of the chain is nonzero, or
+// needed, only on a fine interval [lo, lo + len):
+//   C   the box's coefficients (interleaved coarse layout)   [0, 2b)
+//   S   s = synthesis, and y, the kinetic terms K_p and z  [-8, 2b + 8)
+//       (h_j, j = -7..8, moves coarse point j to fine 2j - 7 .. 2j + 8, so s
+//       is nonzero on [-7, 2b + 6]; the analysis of outputs on the box reads
+//       that interval back; the interval starts on an even point because
+//       the synthesis and analysis taps follow the parity of the fine point)
+//   PSI psi_r = MF s and V psi_r                          [-14, 2b + 15)
+//       (magic filter taps k = -7..8 widen [-7, 2b + 6] by 7 / 8; the
+//       transposed filter maps this interval back onto S)
+//   BOX the analysis output, the box                      [0, 2b)
+// so each 1D pass reads a line of the source interval, zero outside it
+// (free lines), and writes the target interval.  Periodic axes keep the
+// whole periodic line [0, 2b) at every stage.  V and rho live on the cell
+// padded by WVL_FREE_PAD coarse points per side along the free axes.
+enum GrowDom { GD_C = 0, GD_S = 1, GD_PSI = 2, GD_BOX = 3 };
+static void grow_dom(int dom, int b, bool fr, int& lo, int& len) {
+    if (!fr || dom == GD_C || dom == GD_BOX) { lo = 0; len = 2 * b; return; }
+    if (dom == GD_S) { lo = -8; len = 2 * b + 16; return; }
+    lo = -14;
+    len = 2 * b + 29;
+}
+
+template <typename T>
+static void grow_seg(SegDesc<T>& d, const CellRun<T>& r, int kind, int mode, int pass) {
+    int from = GD_S, to = GD_S;
+    switch (kind) {
+    case K_SYN: from = GD_C; to = GD_S; break;
+    case K_MF: from = GD_S; to = GD_PSI; break;
+    case K_MFT: from = GD_PSI; to = GD_S; break;
+    case K_KIN: from = GD_S; to = GD_S; break;
+    case K_ANA: from = GD_S; to = GD_BOX; break;
+    }
+    int flo[3], flen[3], tlo[3], tlen[3];
+    for (int a = 0; a < 3; ++a) {
+        grow_dom(from, r.gb[a], r.gfree[a], flo[a], flen[a]);
+        grow_dom(to, r.gb[a], r.gfree[a], tlo[a], tlen[a]);
+    }
+    // pass 1 runs along x over the source extents, pass 2 along y with x
+    // already at the target, pass 3 along z with x and y at the target
+    const int ax = pass - 1;
+    int N;
+    if (pass == 1) N = flen[2] * flen[1];
+    else if (pass == 2) N = tlen[0] * flen[2];
+    else N = tlen[1] * tlen[0];
+    Seg<T>& s = d.s;
+    d.gn = tlen[ax];
+    d.gN = N;
+    s.P = (long long)tlen[ax] * N;
+    s.Pin = (long long)flen[ax] * N;
+    if (r.gfree[ax]) {
+        s.nin = flen[ax];
+        s.inoff = tlo[ax] - flo[ax];
+    }
+    // index decoding of the modes that need it: M_UNCOMP lines (x3, x2) of
+    // the box, M_COMP / M_POT outputs (X1, X2) in pass 3
+    s.N2 = flen[1];
+    s.N1 = tlen[0];
+    s.n1 = r.gb[0];
+    s.n2 = r.gb[1];
+    s.ncoarse = (long long)r.gb[0] * r.gb[1] * r.gb[2];
+    s.clen = 8 * s.ncoarse;
+    s.bx1 = s.bx2 = s.bx3 = 0;
+    s.bo1 = s.bo2 = s.bo3 = 0;
+    if (mode == M_POT) {
+        // V and rho on the padded cell (origin -2 WVL_FREE_PAD along free axes)
+        s.vN1 = r.Nf[0];
+        s.vN2 = r.Nf[1];
+        s.vP = r.P;
+        s.vo1 = tlo[0] + (r.gfree[0] ? 2 * WVL_FREE_PAD : 0);
+        s.vo2 = tlo[1] + (r.gfree[1] ? 2 * WVL_FREE_PAD : 0);
+        s.vo3 = tlo[2] + (r.gfree[2] ? 2 * WVL_FREE_PAD : 0);
+    }
+}
+
 template <typename T>
 static std::vector<PassCall<T>> build_calls(int op, std::vector<CellRun<T>>& runs) {
     std::vector<PassCall<T>> calls;
     auto add = [&](int kind, int mode, int pass, int stage, auto&& make) {
         PassCall<T> c{kind, mode, pass, stage, {}};
         c.emu = !runs.empty() && runs.front().emu;
-        for (auto& r : runs) c.segs.push_back(make(r));
+        for (auto& r : runs) {
+            SegDesc<T> d = make(r);
+            if (r.grow) grow_seg(d, r, kind, mode, pass);
+            c.segs.push_back(d);
+        }
         calls.push_back(std::move(c));
     };
     auto B = [](CellRun<T>& r, int k) { return r.buf[k]; };
@@ -738,7 +836,8 @@ template <typename T>
 static bool fused_ok(const std::vector<CellRun<T>>& runs) {
     if (runs.empty()) return false;
     for (const auto& r : runs)
-        if (r.emu || r.mapc != nullptr || r.bx[0] > 0 || !fused_cell_ok<T>(r.Nf)) return false;
+        if (r.emu || r.mapc != nullptr || r.bx[0] > 0 || r.grow || !fused_cell_ok<T>(r.Nf))
+            return false;
     return true;
 }
 
@@ -1063,12 +1162,23 @@ static wvl_status bc_cell(int op, const wvl_grid* box, const int fa[3], int norb
     r.occ = occ;
     r.ekin = ekin;
     r.epot = epot;
-    r.bx[0] = box->n1;
-    r.bx[1] = box->n2;
-    r.bx[2] = box->n3;
-    for (int d = 0; d < 3; ++d) r.bo[d] = fa[d] ? FREE_PAD : 0;
     r.ncoarse = (long long)box->n1 * box->n2 * box->n3;
     r.clen = 8 * r.ncoarse;
+    if (emu) {
+        // the tensor-core passes run the periodic operator on the padded
+        // cell, restricted to the box
+        r.bx[0] = box->n1;
+        r.bx[1] = box->n2;
+        r.bx[2] = box->n3;
+        for (int d = 0; d < 3; ++d) r.bo[d] = fa[d] ? FREE_PAD : 0;
+    } else {
+        // every pass on the support its stage needs (grow_seg)
+        r.grow = true;
+        r.gb[0] = box->n1;
+        r.gb[1] = box->n2;
+        r.gb[2] = box->n3;
+        for (int d = 0; d < 3; ++d) r.gfree[d] = fa[d] != 0;
+    }
     const size_t need = run_ws_bytes(r.Nf, norb, sizeof(T));
     if (!ws) return fail(WVL_EINVAL, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(WVL_EINVAL, "workspace is not 256-byte aligned");

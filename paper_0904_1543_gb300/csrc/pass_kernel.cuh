@@ -307,6 +307,37 @@ __device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* b
             continue;
         }
         const int a = a0 + r;
+        if (S.nin > 0) {
+            // free lines: row slot j holds input element j - hl + inoff of a
+            // line of nin, zero outside it (no wrap)
+            const int nin = S.nin;
+            if (MODE == M_UNCOMP) {
+                // the box's interleaved coarse array, line a = (x3, x2) of it
+                const int x3 = a / S.N2, x2 = a - x3 * S.N2;
+                const int mu23 = 2 * (x2 & 1) + 4 * (x3 & 1);
+                const T* cc = S.in + (long long)J.orb * S.clen;
+                const T* cf = cc + S.ncoarse;
+                const long long cb = ((long long)(x3 >> 1) * S.n2 + (x2 >> 1)) * S.n1;
+                #pragma unroll 1
+                for (int j = lane; j < rowlen; j += 32) {
+                    const int x = j - hl + S.inoff;
+                    const bool ok = (unsigned)x < (unsigned)nin;
+                    const int mu = mu23 + (x & 1);
+                    const long long ci = cb + (x >> 1);
+                    const T* src = !ok ? cc : ((mu == 0) ? cc + ci : cf + ci * 7 + mu - 1);
+                    cp_async_or_zero(row + j, src, ok);
+                }
+            } else {
+                const T* src = S.in + (long long)J.orb * S.Pin + (long long)a * nin;
+                #pragma unroll 1
+                for (int j = lane; j < rowlen; j += 32) {
+                    const int x = j - hl + S.inoff;
+                    const bool ok = (unsigned)x < (unsigned)nin;
+                    cp_async_or_zero(row + j, ok ? src + x : src, ok);
+                }
+            }
+            continue;
+        }
         // source position of row slot j is x = (j - hl) mod n
         int x = lane - hl;
         while (x < 0) x += n;
@@ -441,6 +472,18 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
         if (MODE == M_COMP && S.gscale != nullptr) osc = T(2.0 * S.occ[orb] * S.gscale[0]);
         // FP32 potential pass: the first orbital of the unit starts the sums
         const bool first_orb = RSM && orb == (int)((cur.unit - S.blk0) / S.tiles) * S.opg;
+        // index of output I of this line in V and rho: (I + vo3) vplane + vline,
+        // the output's own index I N + a unless V and rho live on another grid
+        // (free lines)
+        long long vline = a0 + line, vplane = N;
+        int vo3 = 0;
+        if (MODE == M_POT && S.vN1 > 0) {
+            const int aa = a0 + line, X2 = aa / S.N1, X1 = aa - X2 * S.N1;
+            vline = (long long)(X2 + S.vo2) * S.vN1 + (X1 + S.vo1);
+            vplane = (long long)S.vN1 * S.vN2;
+            vo3 = S.vo3;
+        }
+        auto vidx = [&](int I) -> long long { return (long long)(I + vo3) * vplane + vline; };
 
         // K_{p-1} of the thread's next chunk, fetched one chunk ahead
         T kv[R];
@@ -527,7 +570,7 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                     } else if (MODE == M_POT) {
                         const T psi = acc[r];
                         if (S.aux) {
-                            const T y = S.aux[oidx] * psi;
+                            const T y = S.aux[vidx(I)] * psi;
                             if (S.out) S.out[obase + oidx] = y;
                             ech = fma(y, psi, ech);
                         }
@@ -564,7 +607,7 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                         if (I >= n) continue;
                         const float2 q = rsm[I * LT + line];
                         const double v = (double)q.x + (double)q.y;
-                        const long long oidx = (long long)I * N + a0 + line;
+                        const long long oidx = vidx(I);
                         if (S.rho_gstride == 0) S.rho[oidx] += v;
                         else S.rho[grp * S.rho_gstride + oidx] = v;
                     }
@@ -578,7 +621,7 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                     for (int r = 0; r < R; ++r) {
                         const int I = c * R + r;
                         if (c < nchunks && I < n) {
-                            const long long oidx = (long long)I * N + a0 + line;
+                            const long long oidx = vidx(I);
                             if (S.rho_gstride == 0) S.rho[oidx] += racc[RSM ? 0 : cc][RSM ? 0 : r].get();
                             else S.rho[grp * S.rho_gstride + oidx] = racc[RSM ? 0 : cc][RSM ? 0 : r].get();
                         }

@@ -68,6 +68,12 @@ struct Seg {
     long long ncoarse;    // scaling coefficients stored (start of the wavelet block)
     int bx1, bx2, bx3;    // free/surface boundary conditions: box extents inside the
     int bo1, bo2, bo3;    //   padded cell and its offsets (coarse points); bx1 = 0 otherwise
+    int nin;              // free lines (no wrap; 0 = periodic lines): input line length;
+    int inoff;            //   row slot j holds input element j - hl + inoff, zero outside
+    long long Pin;        //   [0, nin); Pin = input elements per orbital
+    int vN1, vN2;         // M_POT on free lines: V and rho live on another grid (extents
+    int vo1, vo2, vo3;    //   vN1, vN2, vP elements); output (X1, X2, I) sits there at
+    long long vP;         //   (X1 + vo1, X2 + vo2, I + vo3); vN1 = 0: same layout as the output
     long long P;          // elements per orbital
     long long rho_gstride;// M_POT: 0 -> rho += (direct), else group g writes rho[g*stride]
     long long blk0;       // first work unit of the segment in the launch

@@ -86,3 +86,38 @@ def test_hpsi_mixed_conditions(W, free_axes):
         rho_ref = rho_ref + r["rho"]
     ref = FR.restrict_bc(rho_ref, n, 2 * pad, free_axes)
     assert _err(rho.cpu().numpy(), ref) < RTOL64
+
+
+@pytest.mark.parametrize("dt", ["float64", "float32"])
+def test_free_growing_supports_groups(W, dt):
+    """Free conditions computed on supports that grow pass by pass: a ragged
+    box, more orbitals than one density group, FP64 and FP32 (FP32 bounds of
+    the other parity tests: 2e-6 H psi, 5e-6 rho, 5e-7 energies), H psi, the
+    energies and the density against the free-space oracle."""
+    import torch
+    n = (6, 5, 7)
+    norb = 6
+    g = W.Grid(n, (0.25, 0.2, 0.3))
+    pad = W.FREE_PAD
+    padded = tuple(v + 2 * pad for v in n)
+    psi = inputs.orbitals(113, norb, n).astype(dt)
+    Vp = inputs.gaussian_potential(113, 0, padded).astype(dt)
+    occ = np.array([2.0, 1.0, 2.0, 0.5, 1.5, 2.0])
+    rho = torch.zeros(W.free_fine(g), dtype=torch.float64, device="cuda")
+    hp, ek, ep = W.hpsi_local_free(torch.from_numpy(psi).cuda(), torch.from_numpy(Vp).cuda(),
+                                   torch.from_numpy(occ).cuda(), g, rho=rho)
+    tol, tol_rho, tol_e = (RTOL64, RTOL64, RTOL64) if dt == "float64" else (2e-6, 5e-6, 5e-7)
+    Vx = FR.extend(Vp.astype(np.float64), n, 2 * pad)
+    rho_ref = 0.0
+    for o in range(norb):
+        r = FR.hpsi_local(psi[o].astype(np.float64), Vx, occ[o], n, g.h)
+        d = np.abs(hp[o].double().cpu().numpy() - r["hpsi_c"]).max() / np.abs(r["hpsi_c"]).max()
+        assert d < tol, (o, d)
+        if dt == "float64":
+            assert _err(hp[o].cpu().numpy(), r["hpsi_c"]) < RTOL64
+        assert abs(float(ek[o]) - r["ekin"]) < tol_e * abs(r["ekin"])
+        assert abs(float(ep[o]) - r["epot"]) < tol_e * abs(r["epot"])
+        rho_ref = rho_ref + r["rho"]
+    ref = FR.restrict(rho_ref, 2 * pad)
+    d = np.abs(rho.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert d < tol_rho, d
