@@ -473,17 +473,26 @@ def measure_variants(args, W, torch, dev):
     del psi64
     # ---- localisation regions: 64 orbitals on the periodic 48^3 cell, each
     # stored on a ball of radius 20 (scaling) / 10 (wavelets) coarse points
-    cm, fm = inputs.sphere_masks(n, (24, 24, 24), 20.0, 10.0)
-    reg = W.Region(g, cm, fm)
     nr = 64
-    pr = inputs.vectors_device(5, nr, reg.clen, dev)
     occr = torch.full((nr,), 2.0, dtype=torch.float64, device=dev)
-    ms_r = _time_steps(torch, lambda: W.hpsi_local_region(pr, V64, occr, g, reg), 3, 2)
+    regions = []
+    for rc, rf in ((20.0, 10.0), (12.0, 6.0), (8.0, 5.0)):
+        cm, fm = inputs.sphere_masks(n, (24, 24, 24), rc, rf)
+        reg = W.Region(g, cm, fm)
+        pr = inputs.vectors_device(5, nr, reg.clen, dev)
+        ms_r = _time_steps(torch, lambda: W.hpsi_local_region(pr, V64, occr, g, reg), 3, 2)
+        regions.append({"coarse_radius": rc, "fine_radius": rf,
+                        "stored_fraction": reg.clen / (8 * n[0] * n[1] * n[2]),
+                        "bounding_box": list(reg.len),
+                        "value": nr / (ms_r * 1e-3), "unit": UNIT, "ms_per_step": ms_r})
     out["region_fp64"] = {
         "workload": "local Hamiltonian on region-compressed orbitals, 64 orbitals on a periodic "
-                    "coarse 48^3 cell, coarse region a ball of radius 20, fine region radius 10, FP64",
-        "value": nr / (ms_r * 1e-3), "unit": UNIT, "ms_per_step": ms_r,
-        "stored_fraction": reg.clen / (8 * n[0] * n[1] * n[2]),
+                    "coarse 48^3 cell, coarse and fine regions balls of the radii below, FP64; "
+                    "along axes where the region's bounding box leaves >= 15 coarse points to "
+                    "the cell the chain runs on that box",
+        "value": regions[0]["value"], "unit": UNIT, "ms_per_step": regions[0]["ms_per_step"],
+        "stored_fraction": regions[0]["stored_fraction"],
+        "by_region_size": regions,
         "checked": "tests/test_gpu_region.py (1e-12 against the oracle)",
     }
     # ---- free boundary conditions: 64 orbitals on a 32^3 box (padded cell 48^3)

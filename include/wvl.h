@@ -328,6 +328,13 @@ typedef struct {
     const int* coarse_index;
     const int* fine_index;
     long long ncoarse, nfine;
+    /* Optional periodic bounding box of the region (wvl_region_bounds):
+     * along axis d every region point has a coarse coordinate in
+     * lo[d] .. lo[d] + len[d] - 1 (mod n_d).  len[d] = 0: not given.  Along
+     * axes where len[d] <= n_d - 15 the chain is computed on that box plus
+     * the supports its filters reach (no periodic image of the box couples
+     * to it), so the work shrinks with the region; results are the same. */
+    int lo[3], len[3];
 } wvl_region;
 
 /* Host helper: index arrays (HOST int32 [n1 n2 n3]) and counts from two
@@ -335,6 +342,12 @@ typedef struct {
 wvl_status wvl_region_index(const wvl_grid* grid, const unsigned char* coarse_mask,
                             const unsigned char* fine_mask, int* coarse_index,
                             int* fine_index, long long* ncoarse, long long* nfine);
+
+/* Host helper: the smallest periodic bounding box (lo, len: HOST int[3]) of
+ * the union of the two masks, per axis the complement of the longest
+ * periodic run of coordinates no region point occupies (len 0: empty). */
+wvl_status wvl_region_bounds(const wvl_grid* grid, const unsigned char* coarse_mask,
+                             const unsigned char* fine_mask, int* lo, int* len);
 
 /* The entry points above, with region-compressed coefficient arrays. */
 wvl_status wvl_synthesis_region(const wvl_grid* grid, const wvl_region* region, int prec,

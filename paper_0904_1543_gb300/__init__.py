@@ -559,7 +559,7 @@ def precondition(g, eps, grid: Grid, ncg=5, x=None, want_residual=True, emu=Fals
 
 class _Region(ctypes.Structure):
     _fields_ = [("coarse_index", _vp), ("fine_index", _vp), ("ncoarse", ctypes.c_longlong),
-                ("nfine", ctypes.c_longlong)]
+                ("nfine", ctypes.c_longlong), ("lo", ctypes.c_int * 3), ("len", ctypes.c_int * 3)]
 
 
 def _declare_region(L):
@@ -568,6 +568,7 @@ def _declare_region(L):
     Gp, Rp = ctypes.POINTER(_Grid), ctypes.POINTER(_Region)
     sig = {
         "wvl_region_index": [Gp, _vp, _vp, _vp, _vp, _vp, _vp],
+        "wvl_region_bounds": [Gp, _vp, _vp, _vp, _vp],
         "wvl_synthesis_region": [Gp, Rp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp],
         "wvl_analysis_region": [Gp, Rp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _sz, _vp],
         "wvl_density_region": [Gp, Rp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _vp],
@@ -586,7 +587,9 @@ class Region:
     (n3, n2, n1) for the points that keep their scaling coefficient (coarse)
     and their seven wavelet coefficients (fine)."""
 
-    def __init__(self, grid: Grid, coarse_mask, fine_mask, device="cuda"):
+    def __init__(self, grid: Grid, coarse_mask, fine_mask, device="cuda", bounds=True):
+        """bounds=True also passes the region's periodic bounding box, so
+        that the library computes on it where it is small enough."""
         import numpy as np
         L = lib()
         _declare_region(L)
@@ -601,6 +604,13 @@ class Region:
         _check(L.wvl_region_index(ctypes.byref(grid.c()), cm.ctypes.data, fm.ctypes.data,
                                   ci.ctypes.data, fi.ctypes.data, ctypes.byref(nc),
                                   ctypes.byref(nf)))
+        self.lo, self.len = (0, 0, 0), (0, 0, 0)
+        if bounds:
+            lo = (ctypes.c_int * 3)()
+            ln = (ctypes.c_int * 3)()
+            _check(L.wvl_region_bounds(ctypes.byref(grid.c()), cm.ctypes.data, fm.ctypes.data,
+                                       lo, ln))
+            self.lo, self.len = tuple(lo), tuple(ln)
         self.grid = grid
         self.coarse_index = torch.from_numpy(ci).to(device)
         self.fine_index = torch.from_numpy(fi).to(device)
@@ -609,7 +619,7 @@ class Region:
 
     def c(self):
         return _Region(self.coarse_index.data_ptr(), self.fine_index.data_ptr(), self.ncoarse,
-                       self.nfine)
+                       self.nfine, (ctypes.c_int * 3)(*self.lo), (ctypes.c_int * 3)(*self.len))
 
 
 def _run_region(name, grid, region, prec, norb, device, *ptrs):

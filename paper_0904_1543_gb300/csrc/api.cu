@@ -397,6 +397,8 @@ struct CellRun {
     bool grow = false;
     int gb[3] = {0, 0, 0};
     bool gfree[3] = {false, false, false};
+    int go[3] = {0, 0, 0};         // region runs: the box origin in the cell (coarse)
+    int vlo[3] = {0, 0, 0};        // fine coordinate, relative to the box, of V's index 0
 };
 
 // Runs that add into one density array must not do so from one launch (their
@@ -541,18 +543,32 @@ static void grow_seg(SegDesc<T>& d, const CellRun<T>& r, int kind, int mode, int
     s.N1 = tlen[0];
     s.n1 = r.gb[0];
     s.n2 = r.gb[1];
-    s.ncoarse = (long long)r.gb[0] * r.gb[1] * r.gb[2];
-    s.clen = 8 * s.ncoarse;
     s.bx1 = s.bx2 = s.bx3 = 0;
     s.bo1 = s.bo2 = s.bo3 = 0;
+    if (r.mapc != nullptr) {
+        // a region's box inside the periodic cell: index lookups in the cell
+        s.go1 = r.go[0];
+        s.go2 = r.go[1];
+        s.go3 = r.go[2];
+        s.gc1 = r.n[0];
+        s.gc2 = r.n[1];
+        s.gc3 = r.n[2];
+    } else {
+        s.ncoarse = (long long)r.gb[0] * r.gb[1] * r.gb[2];
+        s.clen = 8 * s.ncoarse;
+    }
     if (mode == M_POT) {
-        // V and rho on the padded cell (origin -2 WVL_FREE_PAD along free axes)
+        // V and rho on the cell (region) or the padded cell (free conditions),
+        // whose index 0 sits at fine coordinate vlo of the box
         s.vN1 = r.Nf[0];
         s.vN2 = r.Nf[1];
+        s.vN3 = r.Nf[2];
         s.vP = r.P;
-        s.vo1 = tlo[0] + (r.gfree[0] ? 2 * WVL_FREE_PAD : 0);
-        s.vo2 = tlo[1] + (r.gfree[1] ? 2 * WVL_FREE_PAD : 0);
-        s.vo3 = tlo[2] + (r.gfree[2] ? 2 * WVL_FREE_PAD : 0);
+        int vo[3];
+        for (int a = 0; a < 3; ++a) vo[a] = ((tlo[a] - r.vlo[a]) % r.Nf[a] + r.Nf[a]) % r.Nf[a];
+        s.vo1 = vo[0];
+        s.vo2 = vo[1];
+        s.vo3 = vo[2];
     }
 }
 
@@ -1109,6 +1125,28 @@ static wvl_status single_cell(int op, const wvl_grid* grid, int norb, const void
         r.mapf = reg->fine_index;
         r.ncoarse = reg->ncoarse;
         r.clen = reg->ncoarse + 7 * reg->nfine;
+        // a region whose periodic bounding box leaves at least 15 coarse
+        // points to the cell along an axis is computed on that box along it
+        // (free lines, grow_seg): H couples coarse points at most 15 apart,
+        // so no periodic image of the box reaches it and the periodic
+        // operator restricted to the region is the box's free-space one
+        bool any = false;
+        int box[3], lo[3];
+        for (int d = 0; d < 3; ++d) {
+            const bool fr = reg->len[d] > 0 && reg->len[d] <= r.n[d] - 15 && !emu;
+            box[d] = fr ? reg->len[d] : r.n[d];
+            lo[d] = fr ? reg->lo[d] : 0;
+            any = any || fr;
+            r.gfree[d] = fr;
+        }
+        if (any) {
+            r.grow = true;
+            for (int d = 0; d < 3; ++d) {
+                r.gb[d] = box[d];
+                r.go[d] = lo[d];
+                r.vlo[d] = -2 * lo[d];
+            }
+        }
     }
     r.in = static_cast<const T*>(in);
     r.out = static_cast<T*>(out);
@@ -1177,7 +1215,10 @@ static wvl_status bc_cell(int op, const wvl_grid* box, const int fa[3], int norb
         r.gb[0] = box->n1;
         r.gb[1] = box->n2;
         r.gb[2] = box->n3;
-        for (int d = 0; d < 3; ++d) r.gfree[d] = fa[d] != 0;
+        for (int d = 0; d < 3; ++d) {
+            r.gfree[d] = fa[d] != 0;
+            r.vlo[d] = fa[d] ? -2 * FREE_PAD : 0;
+        }
     }
     const size_t need = run_ws_bytes(r.Nf, norb, sizeof(T));
     if (!ws) return fail(WVL_EINVAL, "workspace is NULL");
@@ -1330,6 +1371,11 @@ static wvl_status check_region(const wvl_grid* grid, const wvl_region* reg) {
     if (reg->ncoarse < 0 || reg->ncoarse > m || reg->nfine < 0 || reg->nfine > m)
         return fail(WVL_EINVAL, "region counts out of range (ncoarse %lld, nfine %lld, %lld points)",
                     reg->ncoarse, reg->nfine, m);
+    const int n[3] = {grid->n1, grid->n2, grid->n3};
+    for (int d = 0; d < 3; ++d)
+        if (reg->len[d] < 0 || reg->len[d] > n[d] || reg->lo[d] < 0 || reg->lo[d] >= n[d])
+            return fail(WVL_EINVAL, "region box out of range on axis %d (lo %d, len %d)", d + 1,
+                        reg->lo[d], reg->len[d]);
     return WVL_OK;
 }
 
@@ -1718,6 +1764,36 @@ wvl_status wvl_region_index(const wvl_grid* grid, const unsigned char* coarse_ma
     }
     *ncoarse = c;
     *nfine = f;
+    return WVL_OK;
+}
+
+wvl_status wvl_region_bounds(const wvl_grid* grid, const unsigned char* coarse_mask,
+                             const unsigned char* fine_mask, int* lo, int* len) {
+    g_err[0] = 0;
+    WVL_TRY(check_grid(grid));
+    if (!coarse_mask || !fine_mask || !lo || !len) return fail(WVL_EINVAL, "NULL argument");
+    const int n[3] = {grid->n1, grid->n2, grid->n3};
+    for (int d = 0; d < 3; ++d) {
+        // coordinates along axis d that some region point occupies
+        std::vector<char> occ(n[d], 0);
+        for (int i3 = 0; i3 < n[2]; ++i3)
+            for (int i2 = 0; i2 < n[1]; ++i2)
+                for (int i1 = 0; i1 < n[0]; ++i1) {
+                    const long long p = ((long long)i3 * n[1] + i2) * n[0] + i1;
+                    if (coarse_mask[p] || fine_mask[p]) occ[d == 0 ? i1 : d == 1 ? i2 : i3] = 1;
+                }
+        // the box is the complement of the longest periodic run of free coordinates
+        int best = 0, best_end = -1;
+        for (int s = 0; s < n[d]; ++s) {
+            if (occ[s]) continue;
+            int l = 0;
+            while (l < n[d] && !occ[(s + l) % n[d]]) ++l;
+            if (l > best) { best = l; best_end = (s + l) % n[d]; }
+        }
+        if (best == n[d]) { lo[d] = 0; len[d] = 0; continue; }   // empty region
+        lo[d] = best == 0 ? 0 : best_end;
+        len[d] = n[d] - best;
+    }
     return WVL_OK;
 }
 

@@ -245,6 +245,20 @@ __device__ __forceinline__ int stored_index(const Seg<T>& S, long long ci, int i
     return (mu == 0) ? S.mapc[ci] : S.mapf[ci];
 }
 
+// Linear coarse index, in the compressed layout's cell, of coarse point
+// (j1, j2, j3) of the arrays a pass works on: the same point, or with free
+// lines over a region's box, the box point shifted by the box origin and
+// wrapped into the periodic cell.
+template <typename T>
+__device__ __forceinline__ long long cell_ci(const Seg<T>& S, int j1, int j2, int j3) {
+    if (S.gc1 == 0) return ((long long)j3 * S.n2 + j2) * S.n1 + j1;
+    int g1 = j1 + S.go1, g2 = j2 + S.go2, g3 = j3 + S.go3;
+    if (g1 >= S.gc1) g1 -= S.gc1;
+    if (g2 >= S.gc2) g2 -= S.gc2;
+    if (g3 >= S.gc3) g3 -= S.gc3;
+    return ((long long)g3 * S.gc2 + g2) * S.gc1 + g1;
+}
+
 // ------------------------------------------------------------------- jobs
 struct Job {
     long long unit;   // global work unit
@@ -321,10 +335,15 @@ __device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* b
                 #pragma unroll 1
                 for (int j = lane; j < rowlen; j += 32) {
                     const int x = j - hl + S.inoff;
-                    const bool ok = (unsigned)x < (unsigned)nin;
+                    bool ok = (unsigned)x < (unsigned)nin;
                     const int mu = mu23 + (x & 1);
-                    const long long ci = cb + (x >> 1);
-                    const T* src = !ok ? cc : ((mu == 0) ? cc + ci : cf + ci * 7 + mu - 1);
+                    long long k = cb + (x >> 1);
+                    if (ok && S.mapc != nullptr) {
+                        // region: the point's position in the stored vector, -1 off it
+                        k = stored_index(S, cell_ci(S, x >> 1, x2 >> 1, x3 >> 1), 0, 0, 0, mu);
+                        ok = k >= 0;
+                    }
+                    const T* src = !ok ? cc : ((mu == 0) ? cc + k : cf + k * 7 + mu - 1);
                     cp_async_or_zero(row + j, src, ok);
                 }
             } else {
@@ -364,7 +383,7 @@ __device__ __forceinline__ void stage(const PassParams<T>& p, const Job& J, T* b
                 #pragma unroll 1
                 for (int j = lane; j < rowlen; j += 32) {
                     const int mu = mu23 + (x & 1);
-                    const long long ci = cb + (x >> 1);
+                    const long long ci = S.gc1 ? cell_ci(S, x >> 1, x2 >> 1, x3 >> 1) : cb + (x >> 1);
                     const int k = stored_index(S, ci, x >> 1, x2 >> 1, x3 >> 1, mu);
                     const T* src = (k < 0) ? cc : ((mu == 0) ? cc + k : cf + (long long)k * 7 + mu - 1);
                     cp_async_or_zero(row + j, src, k >= 0);
@@ -476,14 +495,22 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
         // the output's own index I N + a unless V and rho live on another grid
         // (free lines)
         long long vline = a0 + line, vplane = N;
-        int vo3 = 0;
+        int vo3 = 0, vn3 = 0x7fffffff;
         if (MODE == M_POT && S.vN1 > 0) {
             const int aa = a0 + line, X2 = aa / S.N1, X1 = aa - X2 * S.N1;
-            vline = (long long)(X2 + S.vo2) * S.vN1 + (X1 + S.vo1);
+            int w1 = X1 + S.vo1, w2 = X2 + S.vo2;
+            if (w1 >= S.vN1) w1 -= S.vN1;
+            if (w2 >= S.vN2) w2 -= S.vN2;
+            vline = (long long)w2 * S.vN1 + w1;
             vplane = (long long)S.vN1 * S.vN2;
             vo3 = S.vo3;
+            vn3 = S.vN3;
         }
-        auto vidx = [&](int I) -> long long { return (long long)(I + vo3) * vplane + vline; };
+        auto vidx = [&](int I) -> long long {
+            int z = I + vo3;
+            if (z >= vn3) z -= vn3;
+            return (long long)z * vplane + vline;
+        };
 
         // K_{p-1} of the thread's next chunk, fetched one chunk ahead
         T kv[R];
@@ -554,7 +581,8 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                             else cc0[S.ncoarse + ci * 7 + mu - 1] = val;
                         } else {
                             // region or box: only the stored coefficients
-                            const int k = stored_index(S, ci, X1 >> 1, X2 >> 1, I >> 1, mu);
+                            const long long cg = S.gc1 ? cell_ci(S, X1 >> 1, X2 >> 1, I >> 1) : ci;
+                            const int k = stored_index(S, cg, X1 >> 1, X2 >> 1, I >> 1, mu);
                             if (k >= 0) {
                                 if (mu == 0) cc0[k] = val;
                                 else cc0[S.ncoarse + (long long)k * 7 + mu - 1] = val;

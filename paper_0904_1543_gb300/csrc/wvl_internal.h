@@ -71,9 +71,13 @@ struct Seg {
     int nin;              // free lines (no wrap; 0 = periodic lines): input line length;
     int inoff;            //   row slot j holds input element j - hl + inoff, zero outside
     long long Pin;        //   [0, nin); Pin = input elements per orbital
-    int vN1, vN2;         // M_POT on free lines: V and rho live on another grid (extents
-    int vo1, vo2, vo3;    //   vN1, vN2, vP elements); output (X1, X2, I) sits there at
-    long long vP;         //   (X1 + vo1, X2 + vo2, I + vo3); vN1 = 0: same layout as the output
+    int vN1, vN2, vN3;    // M_POT on free lines: V and rho live on another grid (extents
+    int vo1, vo2, vo3;    //   vN1, vN2, vN3, vP elements); output (X1, X2, I) sits there at
+    long long vP;         //   (X1 + vo1, X2 + vo2, I + vo3) modulo the extents; vN1 = 0: same
+                          //   layout as the output
+    int go1, go2, go3;    // free lines over a region's box: the box origin in the cell and
+    int gc1, gc2, gc3;    //   the cell's coarse extents (region index lookups, with wrap);
+                          //   gc1 = 0 otherwise
     long long P;          // elements per orbital
     long long rho_gstride;// M_POT: 0 -> rho += (direct), else group g writes rho[g*stride]
     long long blk0;       // first work unit of the segment in the launch

@@ -90,3 +90,52 @@ def test_full_region_matches_full_grid(W):
     b = W.hpsi_local(torch.from_numpy(psi).cuda(), V, occ, g)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("dt", ["float64", "float32"])
+def test_hpsi_region_on_its_box(W, dt):
+    """A small region in a larger periodic cell, wrapping around two faces:
+    along x and z its periodic bounding box leaves at least 15 coarse points
+    to the cell, so the chain runs on that box (free lines) there and on
+    whole periodic lines along y.  H psi, energies and the density against
+    the oracle (periodic operator on the whole cell, restricted to the
+    region), and against the same call without the box."""
+    import torch
+    n = (24, 20, 26)
+    g = W.Grid(n, (0.25, 0.3, 0.2))
+    cm, fm = RG.sphere_masks(n, (1, 10, 24), 3.6, 2.2)
+    reg = W.Region(g, cm, fm)
+    assert reg.len[0] <= n[0] - 15 and reg.len[2] <= n[2] - 15 and reg.len[1] > n[1] - 15
+    assert reg.lo[0] > reg.len[0] and reg.lo[2] > reg.len[2]   # the boxes wrap
+    full = W.Region(g, cm, fm, bounds=False)
+    norb = 5
+    psi = inputs.random_field(92, 1, (norb, reg.clen)).astype(dt)
+    V = inputs.gaussian_potential(92, 0, n).astype(dt)
+    occ = np.array([2.0, 1.0, 0.5, 2.0, 1.5])
+    tol, tol_rho, tol_e = (RTOL64, RTOL64, RTOL64) if dt == "float64" else (2e-6, 5e-6, 5e-7)
+    out = {}
+    for name, rg in (("box", reg), ("cell", full)):
+        rho = torch.zeros(g.fine, dtype=torch.float64, device="cuda")
+        hp, ek, ep = W.hpsi_local_region(torch.from_numpy(psi).cuda(), torch.from_numpy(V).cuda(),
+                                         torch.from_numpy(occ).cuda(), g, rg, rho=rho)
+        rho2 = W.density_region(torch.from_numpy(psi).cuda(), torch.from_numpy(occ).cuda(), g, rg)
+        out[name] = (hp.double().cpu().numpy(), ek.cpu().numpy(), ep.cpu().numpy(),
+                     rho.cpu().numpy(), rho2.cpu().numpy())
+    hp, ek, ep, rho, rho2 = out["box"]
+    rho_ref = np.zeros(g.fine)
+    for o in range(norb):
+        r = RG.hpsi_local(psi[o].astype(np.float64), V.astype(np.float64), occ[o], n, cm, fm, g.h)
+        d = np.abs(hp[o] - r["hpsi_c"]).max() / np.abs(r["hpsi_c"]).max()
+        assert d < tol, (o, d)
+        if dt == "float64":
+            assert _rel(hp[o], r["hpsi_c"]) < RTOL64
+        assert abs(ek[o] - r["ekin"]) < tol_e * abs(r["ekin"])
+        assert abs(ep[o] - r["epot"]) < tol_e * abs(r["epot"])
+        rho_ref += r["rho"]
+    for got in (rho, rho2):
+        assert np.abs(got - rho_ref).max() < tol_rho * np.abs(rho_ref).max()
+    if dt == "float64":
+        assert _rel(rho, rho_ref) < RTOL64
+    # the box and the whole cell agree to rounding
+    hc = out["cell"][0]
+    assert np.abs(hp - hc).max() < (1e-13 if dt == "float64" else 2e-6) * np.abs(hc).max()
