@@ -627,12 +627,11 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         for (int o = o0; o < o1; ++o) {
             cp_wait<0>();
             __syncthreads();
-            Acc<T> e;
+            T ei = T(0);   // this thread's Epot terms of the orbital (at most 32 products)
             const T occ = (T)(S.occ ? S.occ[o] : 1.0);
             T acc[RC][VEC];
             if (mine) {
                 col_item<T, K_MF, RC>(X, rowoff, r0, cv, p.tap[0], acc);
-                T ei = T(0);
                 if constexpr (PK) {
                     const float2 oc = make_float2(occ, occ);
                     #pragma unroll
@@ -662,7 +661,6 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                         if (full) stv(Y + off, y);
                     }
                 }
-                e.add(ei);
             }
             __syncthreads();
             // X is free: fetch the next orbital's tile during the MFT pass
@@ -673,9 +671,26 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                 #pragma unroll
                 for (int kk = 0; kk < RC; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
             }
-            double ew = e.get();
-            #pragma unroll
-            for (int sh = 16; sh > 0; sh >>= 1) ew += __shfl_down_sync(0xffffffffu, ew, sh);
+            // the warp's sum of the threads' terms: FP64 in the FP64 form; in the
+            // FP32 form a compensated FP32 pair (about 48 bits) through the
+            // shuffle tree, FP64 from the warp on -- a tree of FP64 additions
+            // per orbital kept the FP64 pipe of GB300 80 % busy
+            double ew;
+            if constexpr (PK) {
+                FF f{ei, 0.f};
+                #pragma unroll
+                for (int sh = 16; sh > 0; sh >>= 1) {
+                    const float oh = __shfl_down_sync(0xffffffffu, f.hi, sh);
+                    const float ol = __shfl_down_sync(0xffffffffu, f.lo, sh);
+                    ff_add(f, oh);
+                    f.lo += ol;
+                }
+                ew = (double)f.hi + (double)f.lo;
+            } else {
+                ew = ei;
+                #pragma unroll
+                for (int sh = 16; sh > 0; sh >>= 1) ew += __shfl_down_sync(0xffffffffu, ew, sh);
+            }
             const int j = (o - o0) % FZ_EPW;
             if ((threadIdx.x & 31) == 0) epw[j * NW + (threadIdx.x >> 5)] = ew;
             if (j == FZ_EPW - 1 || o + 1 == o1) {
