@@ -25,11 +25,13 @@
  *   (compressed) or o * P (fine).
  * Precision: WVL_F64 -- every array is double.  WVL_F32 -- coefficient, fine
  *   and potential arrays are float, and so are the convolutions; rho, occ and
- *   energies stay double.  Energies accumulate in double (each term an FP32
- *   chain of at most 32 products of convolution outputs, converted exactly);
- *   scalar products (wvl_overlap, wvl_dot) form every product and sum in
- *   double; rho over orbitals is carried per thread in compensated single
- *   (~48-bit) and in double from there on.
+ *   energies stay double.  Energies accumulate in double: each term is an
+ *   FP32 chain of at most 32 products of convolution outputs, converted
+ *   exactly (the fused potential kernel first sums a warp's 32 chains in a
+ *   compensated single pair, ~48-bit); scalar products (wvl_overlap,
+ *   wvl_dot) form every product and sum in double; rho over orbitals is
+ *   carried per thread in compensated single (~48-bit) and in double from
+ *   there on.
  *   WVL_F64_EMU -- arrays as WVL_F64; every 1D convolution sum of the
  *   passes (Eqs. 1dconvtrans, kinetic1d) is evaluated on the FP16 tensor
  *   cores instead of the FP64 pipe: operands split into six signed 10-bit
