@@ -885,7 +885,7 @@ def _run_ours(args, W, torch, dist, rank, world, local, dev):
     # DRAM bytes of one kinetic pass-1 launch from an ncu capture of the small
     # profiling case (36 orbitals, 33.6 M fine points, --per-cell 12), scaled
     # to this launch by the fine points processed; null for any other workload.
-    traffic = (1030.9e6 * pts / 33619968) if (args.per_cell == PER_CELL and args.prec == "f64") else None
+    traffic = (1029.2e6 * pts / 33619968) if (args.per_cell == PER_CELL and args.prec == "f64") else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                 "traffic": traffic, "kernel": "kinetic 1D pass (FP64 DFMA pipe)",

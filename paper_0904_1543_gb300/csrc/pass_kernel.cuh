@@ -545,6 +545,12 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                 if (KM && kline != nullptr) load_run<T, R>(kline, (c + nslots) * R, n, kvec, kv);
                 conv_chunk<T, KIND, R>(srow_line + i0, p, acc);
                 if (!line_ok) continue;
+                if (MODE == M_COMP && S.gscale != nullptr) {
+                    // the adjoint of E_loc: H psi scaled by 2 occ g (a uniform branch,
+                    // so the plain analysis pass pays nothing for it)
+                    #pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] *= osc;
+                }
                 if (MODE == M_PLAIN || MODE == M_UNCOMP) {
                     // transposed store: output I of this line at I * N
                     T* op = S.out + obase + (long long)i0 * N + a0 + line;
@@ -575,7 +581,7 @@ pass_kernel(const __grid_constant__ PassParams<T> p) {
                         const long long ci =
                             ((long long)(I >> 1) * S.n2 + (X2 >> 1)) * S.n1 + (X1 >> 1);
                         T* cc0 = S.out + (long long)orb * S.clen;
-                        const T val = S.gscale != nullptr ? acc[r] * osc : acc[r];
+                        const T val = acc[r];
                         if (S.mapc == nullptr && S.bx1 == 0) {
                             if (mu == 0) cc0[ci] = val;
                             else cc0[S.ncoarse + ci * 7 + mu - 1] = val;
