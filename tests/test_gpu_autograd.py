@@ -156,3 +156,38 @@ def test_eloc_entry_points(W, emu):
     assert d < 1e-11, d
     d = np.abs(tV2.grad.cpu().numpy() + 0.75 * gV_r).max() / np.abs(0.75 * gV_r).max()
     assert d < 1e-11, d
+
+
+def test_eloc_fp32_full_size_sampled(W):
+    """The autograd workload at full size: 512 FP32 orbitals on a coarse 64^3
+    cell (fine 128^3), forward and backward through ELoc as the benchmark
+    runs it.  Two sampled orbitals' dE/dpsi = 2 occ H psi against the oracle
+    (FP64 on the FP32-rounded inputs) at the FP32 bound; dE/dV = rho against
+    the library's density entry point; and sum_I V rho = sum_o occ Epot with
+    the per-orbital energies, a property that holds at any size."""
+    import torch
+    n = (64, 64, 64)
+    g = W.Grid(n)
+    norb = 512
+    dev = torch.device("cuda")
+    p = inputs.orbitals_device(4, norb, n, dev, torch.float32).requires_grad_(True)
+    V = torch.from_numpy(inputs.gaussian_potential(4, 0, n)).to(dev).float().requires_grad_(True)
+    occ = torch.full((norb,), 2.0, dtype=torch.float64, device=dev)
+    E = W.ELoc.apply(p, V, occ, g)
+    E.backward()
+    Vh = V.detach().double().cpu().numpy()
+    for o in (3, 511):
+        r = O.hpsi_local(p[o].detach().double().cpu().numpy(), Vh, 2.0, n)
+        ref = 2.0 * 2.0 * r["hpsi_c"]
+        d = np.abs(p.grad[o].double().cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert d < 2e-6, (o, d)
+    with torch.no_grad():
+        rho = W.density(p.detach(), occ, g)
+        ek, ep = W.energy(p.detach(), V.detach(), occ, g)
+    assert float((V.grad.double() - rho).abs().max() / rho.abs().max()) < 5e-6
+    lhs = float((V.detach().double() * rho).sum())
+    rhs = float((occ * ep).sum())
+    assert abs(lhs - rhs) < 5e-6 * abs(rhs)
+    assert abs(float(E.detach()) - float((occ * (ek + ep)).sum())) < 5e-7 * abs(float(E.detach()))
+    del p, V, E, rho
+    torch.cuda.empty_cache()
