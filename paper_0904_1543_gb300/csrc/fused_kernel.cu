@@ -571,8 +571,11 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         }
         __syncthreads();
         // compressed form of the tile's coarse points (i1 from c0 / 2, i2, every
-        // i3): the scaling coefficients, then the 7-component wavelet records,
-        // each a contiguous run, written by consecutive lanes
+        // i3): per i3 a run of 7 nci wavelet coefficients (records of the
+        // components mu = 1..7) and a run of nci scaling coefficients, both
+        // 16-byte aligned; lane g of a warp writes 16-byte group g of the
+        // two runs (the wavelet run first), reading its elements from Y at
+        // offsets that depend on g only
         {
             T* const cc = S.out + (long long)u * S.P;
             T* const cf = cc + S.P / 8;
@@ -582,24 +585,29 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             const long long kb = (long long)(I2 >> 1) * S.n1 + (c0 >> 1);
             const long long nxy = (long long)S.n2 * S.n1;
-            // record position pos = 7 i1 + mu - 1 (mu = a1 + 2 a2 + 4 a3) of the
-            // tile's coarse point i1 <- Y offset from its (a3 = 0, a2 = 0) row
-            int* const roff = rowoff;                      // the offset table is no longer needed
-            __syncthreads();
-            for (int pos = threadIdx.x; pos < 7 * nci; pos += NT) {
+            const int ngw = 7 * nci / VEC, ngs = nci / VEC;   // 16-byte groups of the runs
+            const bool wav = lane < ngw, act = lane < ngw + ngs;
+            // element pos of the wavelet run is record position 7 i1 + mu - 1
+            // (mu = a1 + 2 a2 + 4 a3) of coarse point i1, at Y offset
+            // a2 N3 RS + a3 RS + 2 i1 + a1 from the tile's (a3 = 0) row 2 i3;
+            // element pos of the scaling run is coarse point pos (mu = 0)
+            int yo[VEC];
+            #pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                const int pos = (wav ? lane : lane - ngw) * VEC + q;
                 const int i1 = pos / 7, mu = pos - 7 * i1 + 1;
-                roff[pos] = (mu >> 1 & 1) * N3 * RS + (mu >> 2) * RS + 2 * i1 + (mu & 1);
+                yo[q] = wav ? (mu >> 1 & 1) * N3 * RS + (mu >> 2) * RS + 2 * i1 + (mu & 1) : 2 * pos;
             }
-            __syncthreads();
-            #pragma unroll 1
-            for (int i3 = warp; i3 < N3 / 2; i3 += NT / 32) {
-                const long long k0 = (long long)i3 * nxy + kb;
-                const T* const y0 = Y + (2 * i3) * RS;    // a3 = 0, a2 = 0
-                if (lane < nci) cc[k0 + lane] = y0[2 * lane] * osc;
-                T* const fr = cf + 7 * k0;
+            if (act)
                 #pragma unroll 1
-                for (int pos = lane; pos < 7 * nci; pos += 32) fr[pos] = y0[roff[pos]] * osc;
-            }
+                for (int i3 = warp; i3 < N3 / 2; i3 += NT / 32) {
+                    const long long k0 = (long long)i3 * nxy + kb;
+                    const T* const y0 = Y + (2 * i3) * RS;
+                    T v[VEC];
+                    #pragma unroll
+                    for (int q = 0; q < VEC; ++q) v[q] = y0[yo[q]] * osc;
+                    stv(wav ? cf + 7 * k0 + lane * VEC : cc + k0 + (lane - ngw) * VEC, v);
+                }
         }
         }
         const double tot = fz_block_sum(e.get(), red);
