@@ -66,12 +66,17 @@ constexpr int OUT_EXP = 2 * QBITS - DBITS * (2 * S - DMAX) - TSHIFT;
 __host__ __device__ constexpr int window_n(int kind) { return kind == K_KIN ? 16 : 32; }
 __host__ __device__ constexpr int window_k(int kind) { return 48; }
 __host__ __device__ constexpr int window_ha(int kind) { return kind == K_KIN ? 16 : 8; }
-__host__ __device__ constexpr int lbo_b(int kind) { return window_n(kind) * 16; }
+// The filter operand holds the S digit planes side by side along N, then a
+// zero block: per 8-position chunk, rows (output j of digit fp) at fp N + j,
+// (S + 1) N rows of 16 bytes.  One MMA per data digit dq then covers the
+// filter digits fp = 0 .. S - dq at once (N (S + 1 - dq) columns), each
+// landing in the accumulator of its diagonal dq + fp.
+__host__ __device__ constexpr int lbo_b(int kind) { return (S + 1) * window_n(kind) * 16; }
 __host__ __device__ constexpr int tmem_cols(int kind) { return MAXACC * window_n(kind); }
 __host__ __device__ constexpr int plane_a_bytes(int kind, int mode) { return window_k(kind) / 8 * lboa(mode); }
-__host__ __device__ constexpr int plane_b_bytes(int kind) { return window_k(kind) / 8 * lbo_b(kind); }
+__host__ __device__ constexpr int b_bytes(int kind) { return window_k(kind) / 8 * lbo_b(kind); }
 __host__ __device__ constexpr int smem_bytes(int kind, int mode) {
-    return S * (plane_a_bytes(kind, mode) + plane_b_bytes(kind));
+    return S * plane_a_bytes(kind, mode) + b_bytes(kind);
 }
 
 // Schedule of one launch: which (filter digit p, data digit q) pairs go to

@@ -151,18 +151,24 @@ __device__ __forceinline__ bool next_job(const PassParams<double>& p, int mode, 
     return true;
 }
 
-// The 26 digit pairs x 3 K-steps of one window, unrolled (the canonical
-// schedule: diagonal d = 2..8 accumulates in tensor-memory columns
-// (d - 2) N.., pairs (filter digit fp, data digit d - 2 - fp)).  K-step k
-// reads the data planes' slab slot (slot0 + k) mod 3, the filter planes'
-// K-step k.  Shared-memory descriptors are base + compile-time offsets.
+// The 26 digit pairs of the canonical schedule (diagonal d = 2..8, i.e.
+// dq + fp = d - 2 <= 6, accumulating in tensor-memory columns (d - 2) N..)
+// as 6 data digits x 3 K-steps: the MMA of data digit dq multiplies it by the
+// filter digits fp = 0 .. 6 - dq side by side (N (7 - dq) columns from column
+// dq N), so one instruction adds the products of every pair with that dq to
+// their diagonals.  The first one (dq = 0, K-step 0) also meets the zero
+// block (fp = 6) and so starts all seven accumulators.  Every exact
+// diagonal's partial sums stay integers below 2^24 in any order, so the
+// order of the pairs does not change the result.  K-step k reads the data
+// planes' slab slot (slot0 + k) mod 3; the shared-memory descriptors are base
+// + compile-time offsets.
 template <int KIND, int MODE>
 __device__ __forceinline__ void issue_window_mmas(uint32_t tm, uint32_t a_base, uint32_t b_base,
                                                   int slot0) {
     constexpr int LBOA = lboa(MODE);
-    constexpr int APL = plane_a_bytes(KIND, MODE), BPL = plane_b_bytes(KIND);
+    constexpr int APL = plane_a_bytes(KIND, MODE);
     constexpr int N = window_n(KIND), LBOB = lbo_b(KIND), K = window_k(KIND);
-    constexpr uint32_t IDESC = idesc_f16(M, N);
+    static_assert(S == 6 && DMAX - 2 == S, "one block per filter digit plus the zero block");
     const uint64_t a0d = mdesc(a_base, LBOA, 128), b0d = mdesc(b_base, LBOB, 128);
     uint32_t aoff[K / 16];
 #pragma unroll
@@ -172,18 +178,12 @@ __device__ __forceinline__ void issue_window_mmas(uint32_t tm, uint32_t a_base, 
         aoff[k] = (uint32_t)(sl * 2 * LBOA) >> 4;
     }
 #pragma unroll
-    for (int d = 2; d <= DMAX; ++d) {
+    for (int dq = 0; dq < S; ++dq) {
+        const uint32_t idesc = idesc_f16(M, N * (S + 1 - dq));
 #pragma unroll
-        for (int fp = 0; fp < S; ++fp) {
-            const int dq = d - 2 - fp;
-            if (dq < 0 || dq >= S) continue;
-            const bool first = fp == (d - 2 - (S - 1) > 0 ? d - 2 - (S - 1) : 0);
-#pragma unroll
-            for (int k = 0; k < K / 16; ++k)
-                mma(tm + (d - 2) * N, a0d + (uint64_t)(((uint32_t)(dq * APL) >> 4) + aoff[k]),
-                    b0d + (uint64_t)((fp * BPL + 2 * k * LBOB) >> 4), IDESC,
-                    (first && k == 0) ? 0u : 1u);
-        }
+        for (int k = 0; k < K / 16; ++k)
+            mma(tm + dq * N, a0d + (uint64_t)(((uint32_t)(dq * APL) >> 4) + aoff[k]),
+                b0d + (uint64_t)((2 * k * LBOB) >> 4), idesc, (dq == 0 && k == 0) ? 0u : 1u);
     }
 }
 
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 emu_pass_kernel(const __grid_constant__ Params ep) {
     constexpr int K = window_k(KIND), HA = window_ha(KIND);
     constexpr int LBOA = lboa(MODE);
-    constexpr int APL = plane_a_bytes(KIND, MODE), BPL = plane_b_bytes(KIND);
+    constexpr int APL = plane_a_bytes(KIND, MODE);
     constexpr int NT = KT<KIND>::NT;
     constexpr int N = window_n(KIND), LBOB = lbo_b(KIND), TCOLS = tmem_cols(KIND);
     constexpr int NH = N / 2;                // outputs per epilogue thread
@@ -384,7 +384,7 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
     static_assert(K == 48 && N % 16 == 0 && (HA - (KIND == K_KIN ? 0 : 8)) % 16 == 0, "window");
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* const Asm = sm;                // [S][APL]: NSLOT slab slots of 2 chunks
-    unsigned char* const Bsm = sm + S * APL;      // [S][BPL]
+    unsigned char* const Bsm = sm + S * APL;      // K / 8 chunks of (S + 1) N rows
     __shared__ uint32_t tslot;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int rowE[M];
@@ -405,10 +405,11 @@ emu_pass_kernel(const __grid_constant__ Params ep) {
         const double f = (t >= 0 && t < NT) ? p.f[e][t] : 0.0;
         int d[S];
         digits(quantize(f, Ef), d);
+        unsigned char* const b = Bsm + (k >> 3) * LBOB + j * 16 + (k & 7) * 2;
 #pragma unroll
         for (int q = 0; q < S; ++q)
-            *reinterpret_cast<__half*>(Bsm + q * BPL + (k >> 3) * LBOB + j * 16 + (k & 7) * 2) =
-                __int2half_rn(d[q]);
+            *reinterpret_cast<__half*>(b + q * N * 16) = __int2half_rn(d[q]);
+        *reinterpret_cast<__half*>(b + S * N * 16) = __float2half(0.f);   // the zero block
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&mbar)), "r"(1));
