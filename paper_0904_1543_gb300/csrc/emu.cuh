@@ -206,21 +206,31 @@ inline bool build_sched(const double (&f)[2][32], int nt, Sched& s) {
 }
 
 #ifdef __CUDACC__
-// The same digits as digits(), each as an exact float: adding 512 to every
-// lower digit position makes the lower digits plain 10-bit fields of
-// Y = X + sum_k 512 1024^k (no carry chain); a field y becomes the float
-// y - 512 through the bit pattern of 2^23 + y.
-__device__ __forceinline__ void digit_floats(long long X, float (&f)[S]) {
+#include <cuda_fp16.h>
+
+// The digits of two inputs, as digits() gives them, digit q of both as one
+// FP16x2 word (X0's in the low half).  Adding 512 to every lower digit
+// position makes the lower digits plain 10-bit fields of
+// Y = X + sum_k 512 1024^k (no carry chain); the field y = digit + 512 in
+// [0, 1024] (the top one: the top digit + 512) becomes the FP16 value 1024 + y
+// through the bit pattern 0x6400 + y (y = 1024 carries into the exponent:
+// 2048), and one packed FP16 subtraction of 1536 leaves the digit, exactly.
+__device__ __forceinline__ void digit_pairs(long long X0, long long X1, uint32_t (&h)[S]) {
     constexpr long long C = 512LL * (1 + (1LL << 10) + (1LL << 20) + (1LL << 30) + (1LL << 40));
     static_assert(S == 6, "digit layout");
-    const long long Y = X + C;
+    const long long Y0 = X0 + C, Y1 = X1 + C;
+    const __half2 off = __halves2half2(__ushort_as_half((unsigned short)0x6600),
+                                       __ushort_as_half((unsigned short)0x6600));   // 1536
+    auto pack = [&](unsigned y0, unsigned y1) {
+        const unsigned w = (0x6400u + y0) | ((0x6400u + y1) << 16);
+        const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&w), off);
+        return *reinterpret_cast<const uint32_t*>(&d);
+    };
 #pragma unroll
-    for (int k = 0; k < S - 1; ++k) {
-        const unsigned y = (unsigned)(Y >> (DBITS * k)) & 1023u;
-        f[S - 1 - k] = __int_as_float(0x4B000000 | (int)y) - 8389120.0f;   // 2^23 + 512
-    }
-    const int top = (int)(Y >> (DBITS * (S - 1)));                          // [-512, 512]
-    f[0] = __int_as_float(0x4B000000 | (top + 1024)) - 8389632.0f;          // 2^23 + 1024
+    for (int k = 0; k < S - 1; ++k)
+        h[S - 1 - k] = pack((unsigned)(Y0 >> (DBITS * k)) & 1023u, (unsigned)(Y1 >> (DBITS * k)) & 1023u);
+    h[0] = pack((unsigned)((int)(Y0 >> (DBITS * (S - 1))) + 512),
+                (unsigned)((int)(Y1 >> (DBITS * (S - 1))) + 512));
 }
 #endif
 

@@ -192,15 +192,11 @@ __device__ __forceinline__ void issue_window_mmas(uint32_t tm, uint32_t a_base, 
 template <int LBOA>
 __device__ __forceinline__ void store_pair_digits(unsigned char* Asm, int apl, int chunk, int r,
                                                   int pair4, double v0, double v1, int E) {
-    float f0[S], f1[S];
-    digit_floats(quantize(v0, E), f0);
-    digit_floats(quantize(v1, E), f1);
+    uint32_t h[S];
+    digit_pairs(quantize(v0, E), quantize(v1, E), h);
     unsigned char* dst = Asm + chunk * LBOA + r * 16 + pair4 * 4;
 #pragma unroll
-    for (int q = 0; q < S; ++q) {
-        const __half2 h2 = __floats2half2_rn(f0[q], f1[q]);
-        *reinterpret_cast<uint32_t*>(dst + q * apl) = *reinterpret_cast<const uint32_t*>(&h2);
-    }
+    for (int q = 0; q < S; ++q) *reinterpret_cast<uint32_t*>(dst + q * apl) = h[q];
 }
 
 // The epilogue's other inputs for this thread's outputs (line er, outputs
