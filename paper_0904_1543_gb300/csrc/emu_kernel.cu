@@ -11,10 +11,12 @@
 //      line by its largest exponent (taken once per unit), and writes six
 //      FP16 digit planes into a ring of three slab slots in shared memory, in
 //      the MMA's K-major layout (8 x 16 B core matrices);
-//   2. issues, from one thread, the 26 digit-pair x 3 K-step MMAs
-//      (M = 128, N, K = 16) into seven FP32 accumulators in tensor memory and
-//      commits them to an mbarrier, polled with a bound; meanwhile every
-//      thread loads the epilogue's other inputs;
+//   2. issues, from one thread, 6 data digits x 3 K-steps of MMAs
+//      (M = 128, K = 16), each over the filter digits side by side along N,
+//      adding the 26 digit pairs' products into seven FP32 accumulators
+//      (one per diagonal, N columns each) in tensor memory, and commits them
+//      to an mbarrier, polled with a bound; meanwhile every thread loads the
+//      epilogue's other inputs;
 //   3. reads the accumulators (warp w: lines 32 (w % 4) + lane, half of the
 //      outputs), recombines them into 64-bit integers, scales to FP64 and
 //      runs the pass's epilogue (transposed store, compressed scatter, V psi
