@@ -614,118 +614,131 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         if (threadIdx.x == 0) S.part[(long long)u * S.ptiles + S.poff + ptile] = tot;
     } else {
         // FZ_POT3: the orbitals of group u in order; each thread owns one
-        // item (the launcher keeps nitems <= NT), so its density
-        // sums stay in registers across the orbitals; the potential tile is
-        // staged once per job
-        T* const Z = Y + N3 * RS;
-        const int o0 = u * S.opg, o1 = min(S.norb, o0 + S.opg);
-        // Epot partial of orbital o0 + j from warp w: epw[(j % FZ_EPW) * 4 + w],
-        // written out every FZ_EPW orbitals
-        constexpr int NW = NT / 32;
-        double* const epw = reinterpret_cast<double*>(Z + N3 * RS);
-        const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RC;
-        const bool mine = (int)threadIdx.x < nitems && cv < ncv;
-        constexpr bool PK = sizeof(T) == 4;   // FP32: compensated pairs, two columns at once
-        FF2 rp[PK ? RC : 1][PK ? 2 : 1];
-        RhoAcc<T> racc[PK ? 1 : RC][PK ? 1 : VEC];
-        const bool pot = S.V != nullptr, full = S.out != nullptr;
-        if (pot) load_tile(Z, S.V + col0);
-        load_tile(X, S.in + (long long)o0 * S.P + col0);
-        #pragma unroll 1
-        for (int o = o0; o < o1; ++o) {
-            cp_wait<0>();
-            __syncthreads();
-            T ei = T(0);   // this thread's Epot terms of the orbital (at most 32 products)
-            const T occ = (T)(S.occ ? S.occ[o] : 1.0);
-            T acc[RC][VEC];
-            if (mine) {
-                col_item<T, K_MF, RC>(X, rowoff, r0, cv, p.tap[0], acc);
-                if constexpr (PK) {
-                    const float2 oc = make_float2(occ, occ);
-                    #pragma unroll
-                    for (int kk = 0; kk < RC; ++kk) {
-                        const float2 a01 = make_float2(acc[kk][0], acc[kk][1]);
-                        const float2 a23 = make_float2(acc[kk][2], acc[kk][3]);
-                        ff2_add(rp[kk][0], __fmul2_rn(__fmul2_rn(oc, a01), a01));
-                        ff2_add(rp[kk][1], __fmul2_rn(__fmul2_rn(oc, a23), a23));
-                    }
-                } else {
-                    #pragma unroll
-                    for (int kk = 0; kk < RC; ++kk)
-                        #pragma unroll
-                        for (int q = 0; q < VEC; ++q) racc[kk][q].add(occ * acc[kk][q] * acc[kk][q]);
-                }
-                #pragma unroll
-                for (int kk = 0; kk < RC; ++kk) {
-                    const int off = (r0 + kk) * RS + cv * VEC;
-                    if (pot) {
-                        const Vec<T> vv = ldv(Z + off);
-                        T y[VEC];
-                        #pragma unroll
-                        for (int q = 0; q < VEC; ++q) {
-                            y[q] = vv.v[q] * acc[kk][q];
-                            ei = fma(y[q], acc[kk][q], ei);
-                        }
-                        if (full) stv(Y + off, y);
-                    }
-                }
-            }
-            __syncthreads();
-            // X is free: fetch the next orbital's tile during the MFT pass
-            if (o + 1 < o1) load_tile(X, S.in + (long long)(o + 1) * S.P + col0);
-            if (mine && full) {
-                col_item<T, K_MFT, RC>(Y, rowoff, r0, cv, p.tap[1], acc);
-                T* const ob = S.out + (long long)o * S.P + col0;
-                #pragma unroll
-                for (int kk = 0; kk < RC; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
-            }
-            // the warp's sum of the threads' terms: FP64 in the FP64 form; in the
-            // FP32 form a compensated FP32 pair (about 48 bits) through the
-            // shuffle tree, FP64 from the warp on -- a tree of FP64 additions
-            // per orbital kept the FP64 pipe of GB300 80 % busy
-            double ew;
-            if constexpr (PK) {
-                FF f{ei, 0.f};
-                #pragma unroll
-                for (int sh = 16; sh > 0; sh >>= 1) {
-                    const float oh = __shfl_down_sync(0xffffffffu, f.hi, sh);
-                    const float ol = __shfl_down_sync(0xffffffffu, f.lo, sh);
-                    ff_add(f, oh);
-                    f.lo += ol;
-                }
-                ew = (double)f.hi + (double)f.lo;
-            } else {
-                ew = ei;
-                #pragma unroll
-                for (int sh = 16; sh > 0; sh >>= 1) ew += __shfl_down_sync(0xffffffffu, ew, sh);
-            }
-            const int j = (o - o0) % FZ_EPW;
-            if ((threadIdx.x & 31) == 0) epw[j * NW + (threadIdx.x >> 5)] = ew;
-            if (j == FZ_EPW - 1 || o + 1 == o1) {
-                // orbitals o - j .. o: warp partials in a fixed order
+        // item, so its density sums stay in registers across the orbitals;
+        // the potential tile is staged once per job.  An item is RP rows of
+        // a 16-byte column vector: N3 / 16 rows where N3 is a multiple of 16
+        // from 64 up (FP32), so that the N3 / RP x 8 items fill the CTA's 128
+        // threads (8 rows: 80 and 96 of them busy on 80- and 96-row tiles);
+        // else 8 (the magic filter and its transpose take the same taps for
+        // both output parities, so any RP works)
+        auto pot3 = [&](auto rpc) {
+            constexpr int RP = decltype(rpc)::value;
+            T* const Z = Y + N3 * RS;
+            const int o0 = u * S.opg, o1 = min(S.norb, o0 + S.opg);
+            // Epot partial of orbital o0 + j from warp w: epw[(j % FZ_EPW) * 4 + w],
+            // written out every FZ_EPW orbitals
+            constexpr int NW = NT / 32;
+            double* const epw = reinterpret_cast<double*>(Z + N3 * RS);
+            const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RP;
+            const bool mine = (int)threadIdx.x < (N3 / RP) * CV && cv < ncv;
+            constexpr bool PK = sizeof(T) == 4;   // FP32: compensated pairs, two columns at once
+            FF2 rp[PK ? RP : 1][PK ? 2 : 1];
+            RhoAcc<T> racc[PK ? 1 : RP][PK ? 1 : VEC];
+            const bool pot = S.V != nullptr, full = S.out != nullptr;
+            if (pot) load_tile(Z, S.V + col0);
+            load_tile(X, S.in + (long long)o0 * S.P + col0);
+            #pragma unroll 1
+            for (int o = o0; o < o1; ++o) {
+                cp_wait<0>();
                 __syncthreads();
-                if ((int)threadIdx.x <= j && S.part != nullptr) {
-                    double t = 0.0;
+                T ei = T(0);   // this thread's Epot terms of the orbital (at most 32 products)
+                const T occ = (T)(S.occ ? S.occ[o] : 1.0);
+                T acc[RP][VEC];
+                if (mine) {
+                    col_item<T, K_MF, RP>(X, rowoff, r0, cv, p.tap[0], acc);
+                    if constexpr (PK) {
+                        const float2 oc = make_float2(occ, occ);
+                        #pragma unroll
+                        for (int kk = 0; kk < RP; ++kk) {
+                            const float2 a01 = make_float2(acc[kk][0], acc[kk][1]);
+                            const float2 a23 = make_float2(acc[kk][2], acc[kk][3]);
+                            ff2_add(rp[kk][0], __fmul2_rn(__fmul2_rn(oc, a01), a01));
+                            ff2_add(rp[kk][1], __fmul2_rn(__fmul2_rn(oc, a23), a23));
+                        }
+                    } else {
+                        #pragma unroll
+                        for (int kk = 0; kk < RP; ++kk)
+                            #pragma unroll
+                            for (int q = 0; q < VEC; ++q) racc[kk][q].add(occ * acc[kk][q] * acc[kk][q]);
+                    }
                     #pragma unroll
-                    for (int w = 0; w < NW; ++w) t += epw[threadIdx.x * NW + w];
-                    S.part[(long long)(o - j + (int)threadIdx.x) * S.ptiles + S.poff + ptile] = t;
+                    for (int kk = 0; kk < RP; ++kk) {
+                        const int off = (r0 + kk) * RS + cv * VEC;
+                        if (pot) {
+                            const Vec<T> vv = ldv(Z + off);
+                            T y[VEC];
+                            #pragma unroll
+                            for (int q = 0; q < VEC; ++q) {
+                                y[q] = vv.v[q] * acc[kk][q];
+                                ei = fma(y[q], acc[kk][q], ei);
+                            }
+                            if (full) stv(Y + off, y);
+                        }
+                    }
+                }
+                __syncthreads();
+                // X is free: fetch the next orbital's tile during the MFT pass
+                if (o + 1 < o1) load_tile(X, S.in + (long long)(o + 1) * S.P + col0);
+                if (mine && full) {
+                    col_item<T, K_MFT, RP>(Y, rowoff, r0, cv, p.tap[1], acc);
+                    T* const ob = S.out + (long long)o * S.P + col0;
+                    #pragma unroll
+                    for (int kk = 0; kk < RP; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
+                }
+                // the warp's sum of the threads' terms: FP64 in the FP64 form; in the
+                // FP32 form a compensated FP32 pair (about 48 bits) through the
+                // shuffle tree, FP64 from the warp on -- a tree of FP64 additions
+                // per orbital kept the FP64 pipe of GB300 80 % busy
+                double ew;
+                if constexpr (PK) {
+                    FF f{ei, 0.f};
+                    #pragma unroll
+                    for (int sh = 16; sh > 0; sh >>= 1) {
+                        const float oh = __shfl_down_sync(0xffffffffu, f.hi, sh);
+                        const float ol = __shfl_down_sync(0xffffffffu, f.lo, sh);
+                        ff_add(f, oh);
+                        f.lo += ol;
+                    }
+                    ew = (double)f.hi + (double)f.lo;
+                } else {
+                    ew = ei;
+                    #pragma unroll
+                    for (int sh = 16; sh > 0; sh >>= 1) ew += __shfl_down_sync(0xffffffffu, ew, sh);
+                }
+                const int j = (o - o0) % FZ_EPW;
+                if ((threadIdx.x & 31) == 0) epw[j * NW + (threadIdx.x >> 5)] = ew;
+                if (j == FZ_EPW - 1 || o + 1 == o1) {
+                    // orbitals o - j .. o: warp partials in a fixed order
+                    __syncthreads();
+                    if ((int)threadIdx.x <= j && S.part != nullptr) {
+                        double t = 0.0;
+                        #pragma unroll
+                        for (int w = 0; w < NW; ++w) t += epw[threadIdx.x * NW + w];
+                        S.part[(long long)(o - j + (int)threadIdx.x) * S.ptiles + S.poff + ptile] = t;
+                    }
                 }
             }
-        }
-        if (mine && S.rho != nullptr) {
-            double* const rb = S.rho + (long long)u * S.rho_gstride;
-            #pragma unroll
-            for (int kk = 0; kk < RC; ++kk)
+            if (mine && S.rho != nullptr) {
+                double* const rb = S.rho + (long long)u * S.rho_gstride;
                 #pragma unroll
-                for (int q = 0; q < VEC; ++q) {
-                    const long long g = (long long)(r0 + kk) * plane + col0 + cv * VEC + q;
-                    double v;
-                    if constexpr (PK) v = ff2_get(rp[kk][q >> 1], q & 1);
-                    else v = racc[kk][q].get();
-                    if (S.rho_gstride == 0) rb[g] += v;
-                    else rb[g] = v;
-                }
-        }
+                for (int kk = 0; kk < RP; ++kk)
+                    #pragma unroll
+                    for (int q = 0; q < VEC; ++q) {
+                        const long long g = (long long)(r0 + kk) * plane + col0 + cv * VEC + q;
+                        double v;
+                        if constexpr (PK) v = ff2_get(rp[kk][q >> 1], q & 1);
+                        else v = racc[kk][q].get();
+                        if (S.rho_gstride == 0) rb[g] += v;
+                        else rb[g] = v;
+                    }
+            }
+        };
+        const int rp = (sizeof(T) == 4 && N3 % 16 == 0 && N3 >= 64) ? N3 / 16 : FZ_RC;
+        if (rp == 4) pot3(std::integral_constant<int, 4>{});
+        else if (rp == 5) pot3(std::integral_constant<int, 5>{});
+        else if (rp == 6) pot3(std::integral_constant<int, 6>{});
+        else if (rp == 7) pot3(std::integral_constant<int, 7>{});
+        else pot3(std::integral_constant<int, FZ_RC>{});
     }
 }
 
