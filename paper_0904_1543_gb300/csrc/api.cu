@@ -950,7 +950,17 @@ static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, c
                 T* const C = r.buf[2];
                 T* const D = r.buf[3];
                 switch (prog) {
-                case FZ_SYN3: s.in = r.in; s.out = A; break;
+                case FZ_SYN3: {
+                    s.in = r.in; s.out = A;
+                    // orbital groups of about four jobs per SM: each job walks
+                    // its group on one tile, the next orbital's gather under
+                    // this one's filter
+                    long long G = (4LL * num_sms() + ctiles - 1) / ctiles;
+                    G = std::max(1LL, std::min<long long>(G, std::max(r.norb, 1)));
+                    s.opg = (int)((r.norb + G - 1) / G);
+                    units = (r.norb + s.opg - 1) / s.opg;
+                    break;
+                }
                 case FZ_SKM12:
                     s.in = A; s.out2 = hpsi ? C : nullptr; s.out3 = D;
                     s.part = energy ? r.kpart : nullptr; s.ptiles = ktiles; s.poff = 0;

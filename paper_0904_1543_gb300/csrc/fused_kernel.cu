@@ -485,40 +485,51 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
 
     if constexpr (PROG == FZ_SYN3) {
         // gather: tile element (I3, I1) is c^mu at coarse point
-        // (I1/2, I2/2, I3/2), mu = a1 + 2 a2 + 4 a3 (the interleaved layout)
-        const T* cc = S.in + (long long)u * S.P;
-        const T* cf = cc + S.P / 8;
+        // (I1/2, I2/2, I3/2), mu = a1 + 2 a2 + 4 a3 (the interleaved layout).
+        // The job walks the orbitals of group u on this tile; the next
+        // orbital's gather goes into the other buffer while this one is
+        // filtered
         const int ncols = ncv * VEC;
         const int a2 = 2 * (I2 & 1);
         const int x = threadIdx.x & (LTC - 1);
         const int I1 = c0 + x;
         const long long cxy = (long long)(I2 >> 1) * S.n1 + (I1 >> 1);
         const long long nxy = (long long)S.n2 * S.n1;
-        // the thread's rows r0, r0 + RSTEP, ... share the parity of r0 (RSTEP
+        // the thread's rows rg, rg + RSTEP, ... share the parity of rg (RSTEP
         // is even), so mu is fixed and the source advances by RSTEP / 2 coarse
         // planes per row: one pointer step per element
         constexpr int RSTEP = NT / LTC;
         static_assert(RSTEP % 2 == 0, "rows of one parity per thread");
-        const int r0 = threadIdx.x / LTC;
-        const int mu = (I1 & 1) + a2 + 4 * (r0 & 1);
-        const long long ci0 = (long long)(r0 >> 1) * nxy + cxy;
-        const T* src = (mu == 0) ? cc + ci0 : cf + ci0 * 7 + mu - 1;
+        const int rg = threadIdx.x / LTC;
+        const int mu = (I1 & 1) + a2 + 4 * (rg & 1);
+        const long long ci0 = (long long)(rg >> 1) * nxy + cxy;
+        const long long soff = (mu == 0) ? ci0 : S.P / 8 + ci0 * 7 + mu - 1;
         const long long step = (mu == 0 ? 1 : 7) * (RSTEP / 2) * nxy;
-        if (x < ncols)
-            #pragma unroll 1
-            for (int r = r0; r < N3; r += RSTEP, src += step) cp_async(X + r * RS + x, src);
-        cp_commit();
-        cp_wait<0>();
-        __syncthreads();
-        T* const ob = S.out + (long long)u * S.P + col0;
+        auto gather = [&](T* dst, int o) {
+            const T* src = S.in + (long long)o * S.P + soff;
+            if (x < ncols)
+                #pragma unroll 1
+                for (int r = rg; r < N3; r += RSTEP, src += step) cp_async(dst + r * RS + x, src);
+            cp_commit();
+        };
+        const int o0 = u * S.opg, o1 = min(S.norb, o0 + S.opg);
+        gather(X, o0);
         #pragma unroll 1
-        for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
-            const int k = it >> 3, cv = it & 7, r0 = k * RC;
-            if (cv >= ncv) continue;
-            T acc[RC][VEC];
-            col_item<T, K_SYN>(X, rowoff, r0, cv, p.tap[0], acc);
-            #pragma unroll
-            for (int kk = 0; kk < RC; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
+        for (int o = o0; o < o1; ++o) {
+            T* const cur = ((o - o0) & 1) ? Y : X;
+            cp_wait<0>();
+            __syncthreads();   // every thread also left the previous orbital's buffer
+            if (o + 1 < o1) gather(((o - o0) & 1) ? X : Y, o + 1);
+            T* const ob = S.out + (long long)o * S.P + col0;
+            #pragma unroll 1
+            for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+                const int k = it >> 3, cv = it & 7, r0 = k * RC;
+                if (cv >= ncv) continue;
+                T acc[RC][VEC];
+                col_item<T, K_SYN>(cur, rowoff, r0, cv, p.tap[0], acc);
+                #pragma unroll
+                for (int kk = 0; kk < RC; ++kk) stv(ob + (long long)(r0 + kk) * plane + cv * VEC, acc[kk]);
+            }
         }
     } else if constexpr (PROG == FZ_TA3) {
         // H psi = A_3 (w' + T_3 a) on both I2 rows; Ekin part <a, T_3 a>
@@ -632,8 +643,8 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RP;
             const bool mine = (int)threadIdx.x < (N3 / RP) * CV && cv < ncv;
             constexpr bool PK = sizeof(T) == 4;   // FP32: compensated pairs, two columns at once
-            FF2 rp[PK ? RP : 1][PK ? 2 : 1];
-            RhoAcc<T> racc[PK ? 1 : RP][PK ? 1 : VEC];
+            [[maybe_unused]] FF2 rp[PK ? RP : 1][PK ? 2 : 1];
+            [[maybe_unused]] RhoAcc<T> racc[PK ? 1 : RP][PK ? 1 : VEC];
             const bool pot = S.V != nullptr, full = S.out != nullptr;
             if (pot) load_tile(Z, S.V + col0);
             load_tile(X, S.in + (long long)o0 * S.P + col0);
