@@ -12,7 +12,9 @@ Sizes: fine extents 32 to 128 in steps of 8 with uneven axes (N1 = 40, 48,
 80, 112 leave a partial last column tile), cells of different spacings (one
 launch per spacing), more orbitals than density groups (the potential kernel
 walks the orbitals of a group), no density target, the largest planes
-(FP32 128 x 128, FP64 112 x 112) and the bench's cells on sampled orbitals.
+(FP32 128 x 128, FP64 112 x 112), FP32 tiles of 64 to 112 rows (the
+potential kernel's items of 4 to 7 rows) and the bench's cells on sampled
+orbitals.
 """
 import numpy as np
 import pytest
@@ -207,6 +209,24 @@ def test_fused_largest_planes(W):
         occ = np.array([2.0, 2.0])
         out = run_plan(W, cells, [0, 0], np.concatenate(psis), Vs, occ, prec, "fused")
         check_against_oracle(cells, [0, 0], psis, Vs, occ, out, tol, tol_e, orbitals={1})
+
+
+def test_fused_f32_potential_item_rows(W):
+    """FP32 tiles of 64, 80, 96 and 112 rows, where the potential kernel's
+    items are N3 / 16 = 4 .. 7 rows so that they fill its 128 threads, with
+    more orbitals than density groups: each potential-kernel job walks
+    several orbitals, and the first column kernel gathers the next orbital
+    of its group while it filters the current one.  Every orbital and the
+    density of each cell against the oracle."""
+    cells = [W.Grid((16, 16, n3)) for n3 in (32, 40, 48, 56)]
+    per = 24
+    cell_of_orb = [c for c in range(len(cells)) for _ in range(per)]
+    psis = [inputs.orbital(57, o, cells[c].n).astype(np.float32) for o, c in enumerate(cell_of_orb)]
+    Vs = [inputs.gaussian_potential(57, c, cells[c].n).astype(np.float32) for c in range(len(cells))]
+    occ = np.linspace(0.5, 2.0, len(cell_of_orb))
+    out = run_plan(W, cells, cell_of_orb, np.concatenate(psis), Vs, occ, W.WVL_F32, "fused")
+    check_against_oracle(cells, cell_of_orb, psis, Vs, occ, out, RTOL32, RTOL32_E,
+                         rtol_rho=RTOL32_RHO)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
