@@ -87,15 +87,53 @@ __device__ __forceinline__ void static_for(F&& f) {
     static_for_impl(f, std::make_integer_sequence<int, N>{});
 }
 
-__device__ __forceinline__ double fz_block_sum(double v, double* red) {
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+// Energy accumulator of an energy partial (one CTA's share of Ekin): FP64
+// in the FP64 form; in the FP32 form a compensated FP32 pair (two-sum,
+// about 48 bits) of the item chains of at most 32 products, carried through
+// the warp's shuffle tree and formed in FP64 from the warp on, as the
+// potential kernel does for Epot -- FP64 additions through the tree took
+// about 12 % of the last column kernel on GB300's narrow FP64 pipe.
+template <typename T> struct EAcc;
+template <> struct EAcc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double warp_sum() {
+        double t = v;
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        return t;
+    }
+};
+template <> struct EAcc<float> {
+    FF f{0.f, 0.f};
+    __device__ __forceinline__ void add(float x) { ff_add(f, x); }
+    __device__ __forceinline__ double warp_sum() {
+        FF g = f;
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, g.hi, o);
+            const float ol = __shfl_down_sync(0xffffffffu, g.lo, o);
+            ff_add(g, oh);
+            g.lo += ol;
+        }
+        return (double)g.hi + (double)g.lo;
+    }
+};
+// the CTA's sum: the warps' sums, then warp 0 adds them in a fixed tree
+template <typename T>
+__device__ __forceinline__ double fz_block_sum(EAcc<T>& e, double* red) {
+    const double w = e.warp_sum();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = v;
+    const int nw = (int)(blockDim.x >> 5);
+    if (lane == 0) red[warp] = w;
     __syncthreads();
     double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    if (warp == 0) {
+        t = lane < nw ? red[lane] : 0.0;
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            if (o < nw) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
     __syncthreads();
     return t;
 }
@@ -324,7 +362,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
     }
 
     if constexpr (PROG == FZ_SKM12) {
-        Acc<T> e;
+        EAcc<T> e;
         // s = S_1 S_2 a -> X
         row_pass<T, K_SYN>(X, Y, N2, N1, RS, p.tap[0], p.tp[0]);
         __syncthreads();
@@ -378,7 +416,7 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
                 stv(S.out3 + pbase + (long long)(r0 + kk) * N1 + cv * VEC, acc[kk]);
         }
         if (S.part != nullptr) {
-            const double tot = fz_block_sum(e.get(), red);
+            const double tot = fz_block_sum(e, red);
             if (threadIdx.x == 0) S.part[(long long)o * S.ptiles + S.poff + I3] = tot;
         }
     } else {
@@ -540,7 +578,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
         load_tile(Y, S.in2 + ob);             // a
         cp_wait<0>();
         __syncthreads();
-        Acc<T> e;
+        EAcc<T> e;
         #pragma unroll 1
         for (int it = threadIdx.x; it < NSUB * nitems; it += blockDim.x) {
             const int sub = it >= nitems, r = it - sub * nitems;
@@ -621,7 +659,7 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                 }
         }
         }
-        const double tot = fz_block_sum(e.get(), red);
+        const double tot = fz_block_sum(e, red);
         if (threadIdx.x == 0) S.part[(long long)u * S.ptiles + S.poff + ptile] = tot;
     } else {
         // FZ_POT3: the orbitals of group u in order; each thread owns one
