@@ -121,15 +121,14 @@ __host__ __device__ inline long long quantize(double x, int E) {
     const unsigned long long b = dbits(x);
     const int e = (int)((b >> 52) & 0x7FF);
     if (e == 0) return 0;
-    const long long m = (long long)((b & ((1ULL << 52) - 1)) | (1ULL << 52));
-    // x = m 2^(e - 1075) -> X = m 2^-(sh)
-    const int sh = E + 1075 - QBITS - e;
-    // left shift by -sh <= 6 (e <= E + 1022), or round off sh bits (none
-    // survive once sh >= 54); select rather than branch
-    const int lsh = sh < 0 ? -sh : 0;
-    const int rsh = sh > 63 ? 63 : (sh > 0 ? sh : 0);
-    const long long half = rsh > 0 ? (1LL << (rsh - 1)) : 0;
-    const long long X = ((m << lsh) + half) >> rsh;
+    // x = m 2^(e - 1075), m < 2^53 -> X = m 2^-(sh), sh = E + 1075 - QBITS - e
+    // >= -6 (e <= E + 1022).  With the mantissa shifted left by 6 first
+    // (m6 < 2^59), X is one right shift by r = sh + 6 >= 0, rounded half up
+    // on the magnitude (none of m survives once r >= 60)
+    const unsigned long long m6 = ((b & ((1ULL << 52) - 1)) | (1ULL << 52)) << 6;
+    int r = E + 1081 - QBITS - e;
+    r = r < 0 ? 0 : (r > 63 ? 63 : r);
+    const long long X = (long long)((m6 + ((1ULL << r) >> 1)) >> r);   // m6 + half < 2^63
     return (b >> 63) ? -X : X;
 }
 

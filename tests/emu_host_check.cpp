@@ -86,6 +86,30 @@ int main() {
         CHECK(std::fabs((long double)x - back) <= std::ldexp(1.0L, E - QBITS - 1), "rounding");
     }
     CHECK(quantize(0.0, 5) == 0, "zero");
+    // quantize exactly: the magnitude m 2^(e - 1075 + QBITS - E) rounded half
+    // up, in 128-bit integers from the bit pattern (every binade offset from
+    // the scale, and the ties)
+    {
+        std::uniform_int_distribution<int> sh(-6, 70);
+        for (int it = 0; it < 2000000; ++it) {
+            const int E = (int)(rng() % 200) - 100;
+            const int s = sh(rng);                 // x's binade below the scale
+            unsigned long long mant = rng() & ((1ULL << 52) - 1);
+            if (it % 7 == 0) mant &= ~((1ULL << (rng() % 52)) - 1);   // many trailing zeros: ties
+            const double x0 = std::ldexp((double)((1ULL << 52) | mant), E + 1075 - QBITS - s - 1075);
+            const double x = (it & 1) ? -x0 : x0;
+            if (!(std::fabs(x) < std::ldexp(1.0, E)) || bexp(x) == 0) continue;
+            const unsigned long long m = (1ULL << 52) | mant;
+            const int r = s;                       // X = m 2^-r
+            __int128 ref;
+            if (r <= 0) ref = (__int128)m << (-r);
+            else if (r >= 100) ref = 0;
+            else ref = ((__int128)m + (((__int128)1 << r) >> 1)) >> r;
+            const long long got = quantize(x, E);
+            CHECK((__int128)(got < 0 ? -got : got) == ref && ((got < 0) == (x < 0) || ref == 0),
+                  "quantize exact x %a E %d", x, E);
+        }
+    }
 
     // ---------------------------------------------------- 2. schedules
     double h[16], g[16], w[16], a[29];
