@@ -217,19 +217,27 @@ inline bool build_sched(const double (&f)[2][32], int nt, Sched& s) {
 __device__ __forceinline__ void digit_pairs(long long X0, long long X1, uint32_t (&h)[S]) {
     constexpr long long C = 512LL * (1 + (1LL << 10) + (1LL << 20) + (1LL << 30) + (1LL << 40));
     static_assert(S == 6, "digit layout");
-    const long long Y0 = X0 + C, Y1 = X1 + C;
+    const unsigned long long Y0 = (unsigned long long)(X0 + C), Y1 = (unsigned long long)(X1 + C);
+    const unsigned l0 = (unsigned)Y0, h0 = (unsigned)(Y0 >> 32);
+    const unsigned l1 = (unsigned)Y1, h1 = (unsigned)(Y1 >> 32);
     const __half2 off = __halves2half2(__ushort_as_half((unsigned short)0x6600),
                                        __ushort_as_half((unsigned short)0x6600));   // 1536
+    // fields y0, y1 <= 1024 -> the word (0x6400 + y0) | (0x6400 + y1) << 16,
+    // the halves joined by a byte permute (no carry crosses them)
     auto pack = [&](unsigned y0, unsigned y1) {
-        const unsigned w = (0x6400u + y0) | ((0x6400u + y1) << 16);
+        const unsigned w = __byte_perm(y0, y1, 0x5410) + 0x64006400u;
         const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&w), off);
         return *reinterpret_cast<const uint32_t*>(&d);
     };
+    // the 10-bit field k of Y from its 32-bit halves (field 3 straddles them)
+    auto field = [](unsigned lo, unsigned hi, int k) {
+        return k < 3 ? (lo >> (DBITS * k)) & 1023u
+                     : k == 3 ? __funnelshift_r(lo, hi, 30) & 1023u : (hi >> (DBITS * k - 32)) & 1023u;
+    };
 #pragma unroll
-    for (int k = 0; k < S - 1; ++k)
-        h[S - 1 - k] = pack((unsigned)(Y0 >> (DBITS * k)) & 1023u, (unsigned)(Y1 >> (DBITS * k)) & 1023u);
-    h[0] = pack((unsigned)((int)(Y0 >> (DBITS * (S - 1))) + 512),
-                (unsigned)((int)(Y1 >> (DBITS * (S - 1))) + 512));
+    for (int k = 0; k < S - 1; ++k) h[S - 1 - k] = pack(field(l0, h0, k), field(l1, h1, k));
+    h[0] = pack((unsigned)(((int)h0 >> (DBITS * (S - 1) - 32)) + 512),
+                (unsigned)(((int)h1 >> (DBITS * (S - 1) - 32)) + 512));
 }
 #endif
 
