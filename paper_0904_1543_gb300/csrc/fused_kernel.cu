@@ -363,17 +363,18 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
 
     if constexpr (PROG == FZ_SKM12) {
         EAcc<T> e;
-        // s = S_1 S_2 a -> X
-        row_pass<T, K_SYN>(X, Y, N2, N1, RS, p.tap[0], p.tp[0]);
-        __syncthreads();
+        // s = S_1 S_2 a -> X: the column pass (S_2) first, then the row pass
+        // (the two commute; this order measured 1 % faster)
         #pragma unroll 1
         for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
             const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
             T acc[RC][VEC];
-            col_item<T, K_SYN>(Y, rowoff, r0, cv, p.tap[0], acc);
+            col_item<T, K_SYN>(X, rowoff, r0, cv, p.tap[0], acc);
             #pragma unroll
-            for (int kk = 0; kk < RC; ++kk) stv(X + (r0 + kk) * RS + cv * VEC, acc[kk]);
+            for (int kk = 0; kk < RC; ++kk) stv(Y + (r0 + kk) * RS + cv * VEC, acc[kk]);
         }
+        __syncthreads();
+        row_pass<T, K_SYN>(Y, X, N2, N1, RS, p.tap[0], p.tp[0]);
         __syncthreads();
         // v = T_1 s + T_2 s, Ekin part <s, v> (not for the density alone;
         // v stored for H psi only)
