@@ -771,6 +771,18 @@ static wvl_status exec_reductions(int op, std::vector<CellRun<T>>& runs,
         if (c.mode == M_POT) pot = &c;
         if (c.mode == M_KLAST) kl = &c;
     }
+    // the energy sums of every cell in as few launches as the task table allows
+    PartTasks tasks;
+    auto add_task = [&](const double* part, int tiles, const double* mpart, int mtiles, double* out,
+                        int norb) -> cudaError_t {
+        if (!tasks.add(part, tiles, mpart, mtiles, out, norb)) {
+            cudaError_t e = launch_reduce_parts_multi(tasks, st);
+            if (e != cudaSuccess) return e;
+            tasks = PartTasks();
+            tasks.add(part, tiles, mpart, mtiles, out, norb);
+        }
+        return cudaSuccess;
+    };
     for (size_t i = 0; i < runs.size(); ++i) {
         CellRun<T>& r = runs[i];
         cudaError_t e = cudaSuccess;
@@ -781,18 +793,22 @@ static wvl_status exec_reductions(int op, std::vector<CellRun<T>>& runs,
                 if (e != cudaSuccess) return cuda_fail(e, "density reduction");
             }
             if ((op == OP_HPSI || op == OP_ENERGY) && r.epot) {
-                e = launch_reduce_parts(r.epart, nullptr, d.s.tiles, r.norb, r.epot, st);
-                if (e != cudaSuccess) return cuda_fail(e, "epot reduction");
+                e = add_task(r.epart, d.s.tiles, nullptr, 0, r.epot, r.norb);
+                if (e != cudaSuccess) return cuda_fail(e, "energy reduction");
             }
         }
         if (kl && r.ekin) {
             const SegDesc<T>& d = kl->segs[i];
-            // OP_HPSI accumulates <s, z> = Ekin + Epot; subtract Epot
-            const double* minus = (op == OP_HPSI) ? r.epot : nullptr;
-            e = launch_reduce_parts(r.kpart, minus, d.s.tiles, r.norb, r.ekin, st);
-            if (e != cudaSuccess) return cuda_fail(e, "ekin reduction");
+            // OP_HPSI accumulates <s, z> = Ekin + Epot; subtract Epot, formed
+            // again from its partials in the order of its own reduction
+            const bool sub = op == OP_HPSI && pot != nullptr;
+            e = add_task(r.kpart, d.s.tiles, sub ? r.epart : nullptr, sub ? pot->segs[i].s.tiles : 0,
+                         r.ekin, r.norb);
+            if (e != cudaSuccess) return cuda_fail(e, "energy reduction");
         }
     }
+    cudaError_t e = launch_reduce_parts_multi(tasks, st);
+    if (e != cudaSuccess) return cuda_fail(e, "energy reduction");
     return WVL_OK;
 }
 
@@ -1010,6 +1026,18 @@ static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, c
         }
     }
     clk.begin(ST_RED);
+    // the energy sums of every cell in as few launches as the task table allows
+    PartTasks tasks;
+    auto add_task = [&](const double* part, int tiles, const double* mpart, int mtiles, double* out,
+                        int norb) -> cudaError_t {
+        if (!tasks.add(part, tiles, mpart, mtiles, out, norb)) {
+            cudaError_t e = launch_reduce_parts_multi(tasks, st);
+            if (e != cudaSuccess) return e;
+            tasks = PartTasks();
+            tasks.add(part, tiles, mpart, mtiles, out, norb);
+        }
+        return cudaSuccess;
+    };
     for (size_t i = 0; i < runs.size(); ++i) {
         CellRun<T>& r = runs[i];
         const int ctiles = r.Nf[1] * ((r.Nf[0] + LTC - 1) / LTC);
@@ -1019,13 +1047,17 @@ static wvl_status run_fused(int op, std::vector<CellRun<T>>& runs, Prof* prof, c
             if (e != cudaSuccess) return cuda_fail(e, "density reduction");
         }
         if (r.epot && energy) {
-            e = launch_reduce_parts(r.epart, nullptr, ctiles, r.norb, r.epot, st);
-            if (e != cudaSuccess) return cuda_fail(e, "epot reduction");
+            e = add_task(r.epart, ctiles, nullptr, 0, r.epot, r.norb);
+            if (e != cudaSuccess) return cuda_fail(e, "energy reduction");
         }
         if (r.ekin && energy) {
-            e = launch_reduce_parts(r.kpart, nullptr, r.Nf[2] + ctiles / 2, r.norb, r.ekin, st);
-            if (e != cudaSuccess) return cuda_fail(e, "ekin reduction");
+            e = add_task(r.kpart, r.Nf[2] + ctiles / 2, nullptr, 0, r.ekin, r.norb);
+            if (e != cudaSuccess) return cuda_fail(e, "energy reduction");
         }
+    }
+    {
+        cudaError_t e = launch_reduce_parts_multi(tasks, st);
+        if (e != cudaSuccess) return cuda_fail(e, "energy reduction");
     }
     clk.end();
     return WVL_OK;

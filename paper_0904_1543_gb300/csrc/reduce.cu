@@ -22,6 +22,31 @@ __global__ void reduce_parts_kernel(const double* __restrict__ part,
     if (lane == 0) out[warp] = s - (minus ? minus[warp] : 0.0);
 }
 
+// Several of those sums in one launch, one warp per (task, orbital):
+// out[o] = sum_t part[o][t] - sum_t mpart[o][t] (the second sum where mpart
+// is set, formed by the same warp in the same order as its own task forms
+// it, so the result equals the two launches' bit for bit).
+__device__ __forceinline__ double warp_row_sum(const double* __restrict__ p, int tiles, int lane) {
+    double s = 0.0;
+    for (int t = lane; t < tiles; t += 32) s += p[t];
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+__global__ void reduce_parts_multi_kernel(const __grid_constant__ PartTasks T) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= T.nwarps) return;
+    int k = 0;
+    while (k + 1 < T.ntask && warp >= T.t[k + 1].warp0) ++k;
+    const PartTask& q = T.t[k];
+    const int o = warp - q.warp0;
+    double s = warp_row_sum(q.part + (long long)o * q.tiles, q.tiles, lane);
+    if (q.mpart != nullptr) s = s - warp_row_sum(q.mpart + (long long)o * q.mtiles, q.mtiles, lane);
+    else s = s - 0.0;
+    if (lane == 0) q.out[o] = s;
+}
+
 // rho[i] += sum_g parts[g * P + i], g in increasing order.
 __global__ void rho_reduce_kernel(const double* __restrict__ parts, long long P,
                                   int ngroups, double* __restrict__ rho) {
@@ -93,6 +118,15 @@ cudaError_t launch_reduce_parts(const double* part, const double* minus, int til
     const int threads = 128;
     const int blocks = (norb * 32 + threads - 1) / threads;
     reduce_parts_kernel<<<blocks, threads, 0, st>>>(part, minus, tiles, norb, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_parts_multi(const PartTasks& t, cudaStream_t st) {
+    if (t.ntask <= 0 || t.nwarps <= 0) return cudaSuccess;
+    const int threads = 128;
+    const int blocks = (t.nwarps * 32 + threads - 1) / threads;
+    reduce_parts_multi_kernel<<<blocks, threads, 0, st>>>(t);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -226,6 +226,29 @@ cudaError_t launch_reduce_parts(const double* part, const double* minus, int til
                                 int norb, double* out, cudaStream_t st);
 cudaError_t launch_rho_reduce(const double* parts, long long P, int ngroups,
                               double* rho, cudaStream_t st);
+// several reduce_parts sums in one launch: task k covers warps
+// warp0 .. warp0 + norb - 1, out[o] = sum part[o][*] - sum mpart[o][*]
+struct PartTask {
+    const double* part;
+    const double* mpart;  // null: nothing subtracted
+    double* out;
+    int tiles, mtiles, norb, warp0;
+};
+constexpr int MAXTASK = 2 * MAXSEG;
+struct PartTasks {
+    PartTask t[MAXTASK];
+    int ntask = 0;
+    int nwarps = 0;
+    // append a task; false when the table is full
+    bool add(const double* part, int tiles, const double* mpart, int mtiles, double* out, int norb) {
+        if (ntask >= MAXTASK) return false;
+        t[ntask] = PartTask{part, mpart, out, tiles, mtiles, norb, nwarps};
+        ++ntask;
+        nwarps += norb;
+        return true;
+    }
+};
+cudaError_t launch_reduce_parts_multi(const PartTasks& t, cudaStream_t st);
 // E_loc = sum_o occ (ekin + epot) into *out (one fixed-order CTA), and
 // dV = gbar rho in the potential's precision (the adjoint of E_loc in V).
 cudaError_t launch_eloc_total(const double* occ, const double* ekin, const double* epot,
