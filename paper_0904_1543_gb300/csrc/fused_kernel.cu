@@ -686,10 +686,13 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             constexpr int RP = decltype(rpc)::value;
             T* const Z = Y + N3 * RS;
             const int o0 = u * S.opg, o1 = min(S.norb, o0 + S.opg);
-            // Epot partial of orbital o0 + j from warp w: epw[(j % FZ_EPW) * 4 + w],
-            // written out every FZ_EPW orbitals
+            // Epot partial of orbital o0 + j from warp w: epw[(j % FZ_EPW) * 4 + w]
+            // (FP32: the compensated pair, epf), written out every FZ_EPW
+            // orbitals; occf holds the FP32 occupations of the current FZ_EPW
             constexpr int NW = NT / 32;
             double* const epw = reinterpret_cast<double*>(Z + N3 * RS);
+            [[maybe_unused]] float2* const epf = reinterpret_cast<float2*>(epw);
+            [[maybe_unused]] float* const occf = reinterpret_cast<float*>(epw + FZ_EPW * NW);
             const int k = (int)threadIdx.x >> 3, cv = (int)threadIdx.x & 7, r0 = k * RP;
             const bool mine = (int)threadIdx.x < (N3 / RP) * CV && cv < ncv;
             constexpr bool PK = sizeof(T) == 4;   // FP32: compensated pairs, two columns at once
@@ -700,10 +703,19 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
             load_tile(X, S.in + (long long)o0 * S.P + col0);
             #pragma unroll 1
             for (int o = o0; o < o1; ++o) {
+                const int j = (o - o0) % FZ_EPW;
+                if constexpr (PK) {
+                    // the occupations of the next FZ_EPW orbitals as floats, so
+                    // that the orbital loop itself runs no FP64 instruction
+                    if (j == 0 && (int)threadIdx.x < min(FZ_EPW, o1 - o))
+                        occf[threadIdx.x] = (float)(S.occ ? S.occ[o + threadIdx.x] : 1.0);
+                }
                 cp_wait<0>();
                 __syncthreads();
                 T ei = T(0);   // this thread's Epot terms of the orbital (at most 32 products)
-                const T occ = (T)(S.occ ? S.occ[o] : 1.0);
+                T occ;
+                if constexpr (PK) occ = occf[j];
+                else occ = (T)(S.occ ? S.occ[o] : 1.0);
                 T acc[RP][VEC];
                 if (mine) {
                     col_item<T, K_MF, RP>(X, rowoff, r0, cv, p.tap[0], acc);
@@ -748,9 +760,10 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                 }
                 // the warp's sum of the threads' terms: FP64 in the FP64 form; in the
                 // FP32 form a compensated FP32 pair (about 48 bits) through the
-                // shuffle tree, FP64 from the warp on -- a tree of FP64 additions
-                // per orbital kept the FP64 pipe of GB300 80 % busy
-                double ew;
+                // shuffle tree, kept as a pair until the flush adds the warps' pairs
+                // in FP64 (a tree of FP64 additions per orbital kept the FP64 pipe
+                // of GB300 80 % busy; converting each warp's pair per orbital cost
+                // 0.007 ms per headline step against converting at the flush)
                 if constexpr (PK) {
                     FF f{ei, 0.f};
                     #pragma unroll
@@ -760,21 +773,29 @@ fz_col_kernel(const __grid_constant__ FzParams<T> p) {
                         ff_add(f, oh);
                         f.lo += ol;
                     }
-                    ew = (double)f.hi + (double)f.lo;
+                    if ((threadIdx.x & 31) == 0) epf[j * NW + (threadIdx.x >> 5)] = make_float2(f.hi, f.lo);
                 } else {
-                    ew = ei;
+                    double ew = ei;
                     #pragma unroll
                     for (int sh = 16; sh > 0; sh >>= 1) ew += __shfl_down_sync(0xffffffffu, ew, sh);
+                    if ((threadIdx.x & 31) == 0) epw[j * NW + (threadIdx.x >> 5)] = ew;
                 }
-                const int j = (o - o0) % FZ_EPW;
-                if ((threadIdx.x & 31) == 0) epw[j * NW + (threadIdx.x >> 5)] = ew;
                 if (j == FZ_EPW - 1 || o + 1 == o1) {
                     // orbitals o - j .. o: warp partials in a fixed order
                     __syncthreads();
                     if ((int)threadIdx.x <= j && S.part != nullptr) {
                         double t = 0.0;
                         #pragma unroll
-                        for (int w = 0; w < NW; ++w) t += epw[threadIdx.x * NW + w];
+                        for (int w = 0; w < NW; ++w) {
+                            double ew;
+                            if constexpr (PK) {
+                                const float2 e = epf[threadIdx.x * NW + w];
+                                ew = (double)e.x + (double)e.y;
+                            } else {
+                                ew = epw[threadIdx.x * NW + w];
+                            }
+                            t += ew;
+                        }
                         S.part[(long long)(o - j + (int)threadIdx.x) * S.ptiles + S.poff + ptile] = t;
                     }
                 }
@@ -862,10 +883,12 @@ template <typename T>
 size_t fz_smem(int prog, int N1, int N2, int N3) {
     if (prog == FZ_SKM12 || prog == FZ_MFTA12)
         return 2 * (size_t)N2 * fz_plane_rs<T>(N1) * sizeof(T);
-    // FZ_POT3 also stages the potential tile and keeps per-warp Epot partials;
+    // FZ_POT3 also stages the potential tile and keeps per-warp Epot partials
+    // and FP32 occupations;
     // FZ_TA3 holds two sub-tiles in each of its two buffers
     if (prog == FZ_POT3)
-        return 3 * (size_t)N3 * fz_ltc<T>() * sizeof(T) + (size_t)FZ_EPW * (FZ_CTHREADS / 32) * 8;
+        return 3 * (size_t)N3 * fz_ltc<T>() * sizeof(T) + (size_t)FZ_EPW * (FZ_CTHREADS / 32) * 8 +
+               (size_t)FZ_EPW * sizeof(float);
     if (prog == FZ_TA3) return 4 * (size_t)N3 * fz_ltc<T>() * sizeof(T);
     return 2 * (size_t)N3 * fz_ltc<T>() * sizeof(T);
 }
