@@ -178,6 +178,33 @@ __device__ __forceinline__ void fir(const T (&win)[NW], const T (&f)[2][32],
     }
 }
 
+// WV 16-byte vectors of a periodic row from position p0 (a multiple of the
+// vector width, possibly negative) into win, wrapped at ncols
+template <typename T, int WV>
+__device__ __forceinline__ void row_window(const T* __restrict__ row, int p0, int ncols,
+                                           T (&win)[WV * (16 / sizeof(T))]) {
+    constexpr int VEC = 16 / (int)sizeof(T);
+    if (p0 >= 0 && p0 + WV * VEC <= ncols) {
+        #pragma unroll
+        for (int q = 0; q < WV; ++q) {
+            const Vec<T> v = ldv(row + p0 + q * VEC);
+            #pragma unroll
+            for (int e = 0; e < VEC; ++e) win[q * VEC + e] = v.v[e];
+        }
+    } else {
+        int pq = p0;
+        while (pq < 0) pq += ncols;
+        #pragma unroll
+        for (int q = 0; q < WV; ++q) {
+            const Vec<T> v = ldv(row + pq);
+            #pragma unroll
+            for (int e = 0; e < VEC; ++e) win[q * VEC + e] = v.v[e];
+            pq += VEC;
+            if (pq >= ncols) pq -= ncols;
+        }
+    }
+}
+
 // Row pass over a plane in shared memory:
 //   dst(r, c) = sum_t f[c & 1][t] src(r, (c - HL + off(c & 1) + t) mod ncols)
 // (the 1D filter of Eq. 1dconvtrans along the row, periodic)
@@ -200,28 +227,8 @@ __device__ __forceinline__ void row_pass_r(const T* __restrict__ src, T* __restr
         const int r = rb * 32 + lane;
         if (r >= nrows) continue;
         const int c0 = ch * RR;
-        const T* row = src + r * RS;
         T win[WV * VEC];
-        const int p0 = c0 - HLR;
-        if (p0 >= 0 && p0 + WV * VEC <= ncols) {
-            #pragma unroll
-            for (int q = 0; q < WV; ++q) {
-                const Vec<T> v = ldv(row + p0 + q * VEC);
-                #pragma unroll
-                for (int e = 0; e < VEC; ++e) win[q * VEC + e] = v.v[e];
-            }
-        } else {
-            int pq = p0;
-            while (pq < 0) pq += ncols;
-            #pragma unroll
-            for (int q = 0; q < WV; ++q) {
-                const Vec<T> v = ldv(row + pq);
-                #pragma unroll
-                for (int e = 0; e < VEC; ++e) win[q * VEC + e] = v.v[e];
-                pq += VEC;
-                if (pq >= ncols) pq -= ncols;
-            }
-        }
+        row_window<T, WV>(src + r * RS, c0 - HLR, ncols, win);
         T acc[RR];
         #pragma unroll
         for (int k = 0; k < RR; ++k) acc[k] = T(0);
@@ -255,6 +262,58 @@ __device__ __forceinline__ void row_pass(const T* __restrict__ src, T* __restric
                                          const float2 (&tp)[32]) {
     if (ncols % 16 == 0) row_pass_r<T, KIND, 16>(src, dst, nrows, ncols, RS, f, tp);
     else row_pass_r<T, KIND, FZ_RR>(src, dst, nrows, ncols, RS, f, tp);
+}
+
+// FP32 row passes T_1 and MF_1 of the same plane from one window per chunk
+// of 16 outputs: MF_1 src -> dst (shared memory), T_1 src -> vg (global, row
+// stride ncols).  The kinetic window holds the magic filter's, so each
+// filter's FMAs are those of its own row pass, in the same order.
+template <typename T>
+__device__ __forceinline__ void row_pass_kin_mf(const T* __restrict__ src, T* __restrict__ dst,
+                                                T* __restrict__ vg, int nrows, int ncols, int RS,
+                                                const FzParams<T>& p) {
+    constexpr int RR = 16, VEC = 16 / (int)sizeof(T);
+    constexpr int HLR = (KT<K_KIN>::HL + VEC - 1) / VEC * VEC;
+    constexpr int DK = HLR - KT<K_KIN>::HL, DM = HLR - KT<K_MF>::HL;
+    constexpr int WK = RR + KT<K_KIN>::NT - 1, WM = RR + KT<K_MF>::NT - 1;
+    constexpr int WV = (WK + DK + VEC - 1) / VEC;
+    static_assert(KT<K_KIN>::EXTRA == 0 && KT<K_MF>::EXTRA == 0 && DM >= 0 && WM + DM <= WV * VEC,
+                  "the kinetic window holds the magic filter's");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);
+    const int nrb = (nrows + 31) >> 5, nch = ncols / RR;
+    #pragma unroll 1
+    for (int it = warp; it < nrb * nch; it += nwarps) {
+        const int ch = it / nrb, rb = it - ch * nrb;
+        const int r = rb * 32 + lane;
+        if (r >= nrows) continue;
+        const int c0 = ch * RR;
+        T win[WV * VEC];
+        row_window<T, WV>(src + r * RS, c0 - HLR, ncols, win);
+        T acc[RR];
+        #pragma unroll
+        for (int k = 0; k < RR; ++k) acc[k] = T(0);
+        fir<T, K_KIN, RR, DK>(win, p.tap[1], p.tp[1], acc);
+        T* const o = vg + (long long)r * ncols + c0;
+        #pragma unroll
+        for (int q = 0; q < RR / VEC; ++q) {
+            T u[VEC];
+            #pragma unroll
+            for (int e = 0; e < VEC; ++e) u[e] = acc[q * VEC + e];
+            stv(o + q * VEC, u);
+        }
+        #pragma unroll
+        for (int k = 0; k < RR; ++k) acc[k] = T(0);
+        fir<T, K_MF, RR, DM>(win, p.tap[3], p.tp[3], acc);
+        T* const od = dst + r * RS + c0;
+        #pragma unroll
+        for (int q = 0; q < RR / VEC; ++q) {
+            T u[VEC];
+            #pragma unroll
+            for (int e = 0; e < VEC; ++e) u[e] = acc[q * VEC + e];
+            stv(od + q * VEC, u);
+        }
+    }
 }
 
 // One column-pass item: rows r0 .. r0 + FZ_RC - 1 of the 16-byte column
@@ -376,6 +435,46 @@ fz_plane_kernel(const __grid_constant__ FzParams<T> p) {
         __syncthreads();
         row_pass<T, K_SYN>(Y, X, N2, N1, RS, p.tap[0], p.tp[0]);
         __syncthreads();
+        if (sizeof(T) == 4 && N1 % 16 == 0 && S.part != nullptr && S.out2 != nullptr) {
+            // H psi, FP32: T_1 s -> v and MF_1 s -> Y in one row pass (one
+            // window per chunk, two fewer phases); then per column item
+            // t = MF_2 Y and v += T_2 s with the Ekin part <s, v>, the same
+            // operations in the same order as the phases below (bit-identical
+            // results; 1.414 -> 1.404 ms per headline step for SYN3 + SKM12).
+            // The FP32 kernel fits 128 registers (two CTAs per SM).
+            T* const vg = S.out2 + pbase;
+            row_pass_kin_mf<T>(X, Y, vg, N2, N1, RS, p);
+            __syncthreads();
+            #pragma unroll 1
+            for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+                const int k = it / ncv, cv = it - k * ncv, r0 = k * RC;
+                T acc[RC][VEC];
+                col_item<T, K_MF>(Y, rowoff, r0, cv, p.tap[3], acc);
+                #pragma unroll
+                for (int kk = 0; kk < RC; ++kk)
+                    stv(S.out3 + pbase + (long long)(r0 + kk) * N1 + cv * VEC, acc[kk]);
+                Vec<T> t1[RC];
+                #pragma unroll
+                for (int kk = 0; kk < RC; ++kk) t1[kk] = ldv(vg + (long long)(r0 + kk) * N1 + cv * VEC);
+                col_item<T, K_KIN>(X, rowoff, r0, cv, p.tap[2], acc);
+                T ei = T(0);
+                #pragma unroll
+                for (int kk = 0; kk < RC; ++kk) {
+                    const Vec<T> sv = ldv(X + (r0 + kk) * RS + cv * VEC);
+                    T v[VEC];
+                    #pragma unroll
+                    for (int q = 0; q < VEC; ++q) {
+                        v[q] = acc[kk][q] + t1[kk].v[q];
+                        ei = fma(sv.v[q], v[q], ei);
+                    }
+                    stv(vg + (long long)(r0 + kk) * N1 + cv * VEC, v);
+                }
+                e.add(ei);
+            }
+            const double tot = fz_block_sum(e, red);
+            if (threadIdx.x == 0) S.part[(long long)o * S.ptiles + S.poff + I3] = tot;
+            return;
+        }
         // v = T_1 s + T_2 s, Ekin part <s, v> (not for the density alone;
         // v stored for H psi only)
         if (S.part != nullptr) {
